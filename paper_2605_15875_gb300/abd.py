@@ -1,0 +1,235 @@
+"""Python binding of the C ABI in include/abd.h (argument marshalling only).
+
+Every step of the method runs inside libabd.so's CUDA kernels; this module
+only converts numpy arrays and Python values to the C structs.  It raises
+when the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libabd.so")
+
+DYNAMIC, STATIC, KINEMATIC = 0, 1, 2
+FP64, MIXED = 0, 1
+RHO_FIXED, RHO_ADAPTIVE = 0, 1
+OK, ADMM_MAXITER, NEWTON_MAXITER, FELL_BACK_MONOLITHIC = 0, 1, 2, 3
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("n_meshes", C.c_int32), ("mesh_n_verts", C.c_void_p), ("mesh_n_tris", C.c_void_p),
+                ("mesh_xbar", C.c_void_p), ("mesh_tris", C.c_void_p), ("n_bodies", C.c_int32),
+                ("body_mesh", C.c_void_p), ("body_density", C.c_void_p), ("body_kappa", C.c_void_p),
+                ("body_kind", C.c_void_p), ("body_q0", C.c_void_p), ("body_v0", C.c_void_p),
+                ("n_planes", C.c_int32), ("plane_axis", C.c_void_p), ("plane_sign", C.c_void_p),
+                ("plane_offset", C.c_void_p), ("gravity", C.c_double * 3)]
+
+
+class PartitionDesc(C.Structure):
+    _fields_ = [("axis", C.c_int32), ("n_slabs", C.c_int32), ("planes", C.c_void_p), ("alpha", C.c_double),
+                ("w_min", C.c_double)]
+
+
+class StepParams(C.Structure):
+    _fields_ = [("h", C.c_double), ("dhat", C.c_double), ("kappa_barrier", C.c_double),
+                ("precision", C.c_int32), ("rho_mode", C.c_int32), ("beta", C.c_double), ("tau", C.c_double),
+                ("mu", C.c_double), ("sigma_min", C.c_double), ("sigma_max", C.c_double), ("theta", C.c_double),
+                ("newton_tol", C.c_double), ("max_admm", C.c_int32), ("max_newton", C.c_int32),
+                ("max_halvings", C.c_int32), ("pcg_rtol", C.c_double), ("pcg_max", C.c_int32),
+                ("accd_s", C.c_double), ("accd_c", C.c_double)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("admm_iters", C.c_int32), ("newton_iters", C.c_int32),
+                ("n_partitions", C.c_int32), ("n_shared", C.c_int32), ("n_slots", C.c_int32),
+                ("pcg_iters", C.c_int64), ("n_candidates_peak", C.c_int64), ("n_active_peak", C.c_int64),
+                ("r_inf", C.c_double), ("s_inf", C.c_double), ("delta_inf", C.c_double),
+                ("min_distance", C.c_double), ("l", C.c_double), ("kappa_barrier", C.c_double), ("w", C.c_double),
+                ("t_solve_ms", C.c_double), ("t_coll_ms", C.c_double), ("t_sync_ms", C.c_double),
+                ("t_total_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# every symbol declared in include/abd.h
+EXPORTS = ["abd_scene_create", "abd_scene_destroy", "abd_scene_counts", "abd_body_props", "abd_partition",
+           "abd_partition_masks", "abd_step", "abd_state_get", "abd_state_set", "abd_state_device",
+           "abd_candidates", "abd_profile", "abd_kernel_stats", "abd_step_params_default", "abd_status_string",
+           "abd_last_error"]
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load libabd.so (raises when it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libabd.so not found at {p}: build it with paper_2605_15875_gb300.build.build()")
+    L = C.CDLL(p)
+    vp, i64 = C.c_void_p, C.c_int64
+    L.abd_scene_create.argtypes = [C.POINTER(SceneDesc), vp, C.POINTER(vp)]
+    L.abd_scene_destroy.argtypes = [vp]
+    L.abd_scene_destroy.restype = None
+    L.abd_scene_counts.argtypes = [vp, vp]
+    L.abd_body_props.argtypes = [vp, C.c_int32, vp, vp, vp, vp]
+    L.abd_partition.argtypes = [vp, C.POINTER(PartitionDesc)]
+    L.abd_partition_masks.argtypes = [vp, C.c_double, vp, vp]
+    L.abd_step.argtypes = [vp, C.POINTER(StepParams), C.POINTER(StepStats)]
+    L.abd_state_get.argtypes = [vp, vp, vp, i64]
+    L.abd_state_set.argtypes = [vp, vp, vp, i64]
+    L.abd_state_device.argtypes = [vp, C.POINTER(vp), C.POINTER(vp)]
+    L.abd_candidates.argtypes = [vp, vp, vp, C.c_double, vp, i64, C.POINTER(i64)]
+    L.abd_profile.argtypes = [vp, C.c_int32]
+    L.abd_kernel_stats.argtypes = [vp, C.c_char_p, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.abd_step_params_default.argtypes = []
+    L.abd_step_params_default.restype = StepParams
+    L.abd_status_string.argtypes = [C.c_int]
+    L.abd_status_string.restype = C.c_char_p
+    L.abd_last_error.argtypes = [vp]
+    L.abd_last_error.restype = C.c_char_p
+    if path is None:
+        _lib = L
+    return L
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def default_params(**kw) -> StepParams:
+    p = load().abd_step_params_default()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+class AbdError(RuntimeError):
+    pass
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return None
+
+
+class Scene:
+    """A scene resident on the current CUDA device (C ABI handle)."""
+
+    def __init__(self, sa, stream: Optional[int] = None):
+        L = load()
+        self._keep = [sa]
+        d = SceneDesc()
+        d.n_meshes = len(sa.mesh_n_verts)
+        d.mesh_n_verts, d.mesh_n_tris = _p(sa.mesh_n_verts), _p(sa.mesh_n_tris)
+        d.mesh_xbar, d.mesh_tris = _p(sa.mesh_xbar), _p(sa.mesh_tris)
+        d.n_bodies = sa.n_bodies
+        d.body_mesh, d.body_density, d.body_kappa = _p(sa.body_mesh), _p(sa.body_density), _p(sa.body_kappa)
+        d.body_kind, d.body_q0, d.body_v0 = _p(sa.body_kind), _p(sa.body_q0), _p(sa.body_v0)
+        d.n_planes = len(sa.plane_axis)
+        d.plane_axis, d.plane_sign, d.plane_offset = _p(sa.plane_axis), _p(sa.plane_sign), _p(sa.plane_offset)
+        for k in range(3):
+            d.gravity[k] = float(sa.gravity[k])
+        h = C.c_void_p()
+        self.stream = _current_stream() if stream is None else stream
+        rc = L.abd_scene_create(C.byref(d), self.stream, C.byref(h))
+        if rc != 0:
+            raise AbdError(f"abd_scene_create failed: {L.abd_status_string(rc).decode()} ({rc})")
+        self.h = h
+        self.L = L
+        cnt = np.zeros(4, dtype=np.int64)
+        L.abd_scene_counts(self.h, _p(cnt))
+        self.n_bodies, self.n_verts, self.n_tris, self.n_edges = (int(c) for c in cnt)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            self.L.abd_scene_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc < 0:
+            raise AbdError(f"{what}: {self.L.abd_status_string(rc).decode()} ({rc}): "
+                           f"{self.L.abd_last_error(self.h).decode()}")
+        return rc
+
+    def partition(self, n_slabs=1, axis=0, planes=None, alpha=2.0, w_min=0.0):
+        d = PartitionDesc(axis=axis, n_slabs=n_slabs, planes=None, alpha=alpha, w_min=w_min)
+        arr = None
+        if planes is not None:
+            arr = np.ascontiguousarray(planes, dtype=np.float64)
+            d.planes = arr.ctypes.data
+        self._check(self.L.abd_partition(self.h, C.byref(d)), "abd_partition")
+
+    def partition_masks(self, h=1e-2):
+        m = np.zeros(self.n_bodies, dtype=np.uint64)
+        w = C.c_double()
+        self._check(self.L.abd_partition_masks(self.h, h, _p(m), C.byref(w)), "abd_partition_masks")
+        return m, w.value
+
+    def step(self, params: Optional[StepParams] = None) -> dict:
+        params = default_params() if params is None else params
+        st = StepStats()
+        rc = self.L.abd_step(self.h, C.byref(params), C.byref(st))
+        self._check(rc, "abd_step")
+        return st.as_dict()
+
+    def state(self):
+        q, v = np.zeros((self.n_bodies, 12)), np.zeros((self.n_bodies, 12))
+        self._check(self.L.abd_state_get(self.h, _p(q), _p(v), self.n_bodies), "abd_state_get")
+        return q, v
+
+    def set_state(self, q, v):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        self._check(self.L.abd_state_set(self.h, _p(q), _p(v), self.n_bodies), "abd_state_set")
+
+    def device_state(self):
+        q, v = C.c_void_p(), C.c_void_p()
+        self._check(self.L.abd_state_device(self.h, C.byref(q), C.byref(v)), "abd_state_device")
+        return q.value, v.value
+
+    def body_props(self, b):
+        m, V = C.c_double(), C.c_double()
+        com, S = np.zeros(3), np.zeros(9)
+        self._check(self.L.abd_body_props(self.h, b, C.byref(m), _p(com), _p(S), C.byref(V)), "abd_body_props")
+        return m.value, com, S.reshape(3, 3), V.value
+
+    def candidates(self, x0, x1=None, dhat=1e-3, cap=None):
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        x1 = None if x1 is None else np.ascontiguousarray(x1, dtype=np.float64)
+        n = C.c_int64()
+        self._check(self.L.abd_candidates(self.h, _p(x0), _p(x1), dhat, None, 0, C.byref(n)), "abd_candidates")
+        cnt = n.value
+        out = np.zeros((max(cnt, 1), 3), dtype=np.int32)
+        self._check(self.L.abd_candidates(self.h, _p(x0), _p(x1), dhat, _p(out), cnt, C.byref(n)), "abd_candidates")
+        return out[:cnt]
+
+    def profile(self, enable=True):
+        self._check(self.L.abd_profile(self.h, 1 if enable else 0), "abd_profile")
+
+    def kernel_stats(self, name):
+        n, ms, b = C.c_int64(), C.c_double(), C.c_double()
+        self._check(self.L.abd_kernel_stats(self.h, name.encode(), C.byref(n), C.byref(ms), C.byref(b)),
+                    "abd_kernel_stats")
+        return n.value, ms.value, b.value

@@ -1,0 +1,597 @@
+// abd_assemble.cu -- narrow phase, Newton assembly, CCD and line-search energies.
+//
+// Per slot: inertia (1/kappa_b) M (q - q~), orthogonality (1/kappa_b) h^2 kappa V
+// ||A A^T - I||^2 with its 9x9 Hessian projected to PSD, and the consensus
+// penalty rho (q - z + u) for shared replicas (Eq. 3, Eq. 5).  Per active
+// pair: (h^2 / kappa_c) kB b(d) [m(c)] with its 12x12 vertex Hessian projected
+// to PSD before the J^T H J map onto the slot blocks (12x12, J_v = I3 (x)
+// (1, xbar_v^T)).  CCD and energies are FP64; assembly runs in T.
+#include <cfloat>
+
+#include "abd_device.cuh"
+#include "abd_internal.h"
+
+namespace abd {
+
+__device__ __forceinline__ int qidx(int k, int a) { return a == 0 ? k : 3 + 3 * k + (a - 1); }
+
+__device__ __forceinline__ int pair_slots(const PairRec &r, const int *sv_slot, int &sa, int &sb) {
+    sa = sv_slot[r.v[0]];
+    sb = sv_slot[r.v[(r.flags & 1) ? 2 : 1]];
+    return 0;
+}
+
+__device__ __forceinline__ double pair_kappa(int sa, int sb, int S_dyn, const unsigned long long *mask) {
+    if (sa >= S_dyn) return (double)__popcll(mask[sb]);
+    if (sb >= S_dyn) return (double)__popcll(mask[sa]);
+    return (double)__popcll(mask[sa] & mask[sb]);
+}
+
+__device__ __forceinline__ int pair_part(int sa, int sb, int S_dyn, const int *slot_part) {
+    return sa < S_dyn ? slot_part[sa] : slot_part[sb];
+}
+
+// Warp-aggregated append of `rec` when `keep`.
+__device__ __forceinline__ void append(bool keep, const PairRec &rec, PairRec *out, int64_t cap,
+                                       unsigned long long *count) {
+    int lane = threadIdx.x & 31;
+    unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (!m) return;
+    unsigned long long pos = 0;
+    int leader = __ffs(m) - 1;
+    if (lane == leader) pos = atomicAdd(count, (unsigned long long)__popc(m));
+    pos = __shfl_sync(0xffffffffu, pos, leader);
+    if (keep) {
+        unsigned long long my = pos + __popc(m & ((1u << lane) - 1));
+        if ((int64_t)my < cap) out[my] = rec;
+    }
+}
+
+// Narrow phase: keep candidates with 0 < d < dhat.
+__global__ void k_narrow(const PairRec *__restrict__ cand, int64_t n, const double *__restrict__ x, double dhat,
+                         PairRec *__restrict__ act, int64_t cap, unsigned long long *__restrict__ count) {
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        bool keep = false;
+        PairRec r;
+        if (i < n) {
+            r = cand[i];
+            double X[12];
+            for (int v = 0; v < 4; ++v)
+                for (int k = 0; k < 3; ++k) X[3 * v + k] = x[3 * (int64_t)r.v[v] + k];
+            int ty;
+            double b0, b1;
+            double d = sqrt(classify<double>(r.flags & 1, X, ty, b0, b1));
+            keep = d < dhat;
+        }
+        append(keep, r, act, cap, count);
+    }
+}
+
+struct AsmArgs {
+    int S_dyn;
+    const int *slot_body, *slot_part, *slot_rep, *sv_slot;
+    const unsigned long long *slot_mask;
+    const double *slot_kw;
+    const int *voff;
+    const double *xbar, *mass, *S, *vol, *kappa;
+    const double *q, *qtil, *z, *u, *rho;
+    const double *x;
+    const PartState *part;
+    double h, dhat, kB;
+    Planes planes;
+    const int64_t *slot_voff;
+    double *g;
+};
+
+// Per dynamic slot of an active partition: write g and the diagonal block.
+template <class T>
+__global__ void k_slot_assemble(AsmArgs A, T *__restrict__ diag) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.S_dyn; s += gridDim.x * blockDim.x) {
+        if (!A.part[A.slot_part[s]].active) continue;
+        int b = A.slot_body[s];
+        double kw = A.slot_kw[s], h2 = A.h * A.h;
+        const double *q = A.q + 12 * (int64_t)s, *qt = A.qtil + 12 * (int64_t)s;
+        const double *S = A.S + 9 * (int64_t)b;
+        double m = A.mass[b];
+        double g[12];
+        T D[144];
+        for (int i = 0; i < 144; ++i) D[i] = T(0);
+        for (int k = 0; k < 3; ++k) {
+            g[k] = kw * m * (q[k] - qt[k]);
+            D[k * 12 + k] = T(kw * m);
+        }
+        for (int k = 0; k < 3; ++k)
+            for (int i = 0; i < 3; ++i) {
+                double acc = 0.0;
+                for (int j = 0; j < 3; ++j) {
+                    acc += S[3 * i + j] * (q[3 + 3 * k + j] - qt[3 + 3 * k + j]);
+                    D[(3 + 3 * k + i) * 12 + 3 + 3 * k + j] = T(kw * S[3 * i + j]);
+                }
+                g[3 + 3 * k + i] = kw * acc;
+            }
+        // orthogonality potential: rows a_k, C = A A^T - I
+        double a[3][3], C[3][3];
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j) a[k][j] = q[3 + 3 * k + j];
+        for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l) C[k][l] = a[k][0] * a[l][0] + a[k][1] * a[l][1] + a[k][2] * a[l][2] - (k == l);
+        double kv = A.kappa[b] * A.vol[b], c4 = 4.0 * kv * kw * h2;
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j) g[3 + 3 * k + j] += c4 * (C[k][0] * a[0][j] + C[k][1] * a[1][j] + C[k][2] * a[2][j]);
+        T H9[81];
+        double AtA[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) AtA[i][j] = a[0][i] * a[0][j] + a[1][i] * a[1][j] + a[2][i] * a[2][j];
+        for (int k = 0; k < 3; ++k)
+            for (int l = 0; l < 3; ++l)
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) {
+                        double v = a[l][i] * a[k][j] + (i == j ? C[k][l] : 0.0) + (k == l ? AtA[i][j] : 0.0);
+                        H9[(3 * k + i) * 9 + 3 * l + j] = T(4.0 * kv * v);
+                    }
+        psd_project<T, 9>(H9);
+        for (int i = 0; i < 9; ++i)
+            for (int j = 0; j < 9; ++j) D[(3 + i) * 12 + 3 + j] += T(kw * h2) * H9[i * 9 + j];
+        if (A.slot_rep[s] >= 0) {
+            double r = A.rho[s];
+            for (int i = 0; i < 12; ++i) {
+                g[i] += r * (q[i] - A.z[12 * (int64_t)s + i] + A.u[12 * (int64_t)s + i]);
+                D[i * 12 + i] += T(r);
+            }
+        }
+        for (int i = 0; i < 12; ++i) A.g[12 * (int64_t)s + i] = g[i];
+        T *o = diag + 144 * (int64_t)s;
+        for (int i = 0; i < 144; ++i) o[i] = D[i];
+    }
+}
+
+template <class T> __device__ __forceinline__ void atomic_addT(T *a, T v) { atomicAdd(a, v); }
+
+// Per active pair: barrier gradient and projected Hessian scattered to slots.
+template <class T>
+__global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int64_t n, const int2 *__restrict__ l1,
+                                T *__restrict__ diag, T *__restrict__ off, int *__restrict__ offflag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        PairRec r = act[i];
+        int sa, sb;
+        pair_slots(r, A.sv_slot, sa, sb);
+        int part = pair_part(sa, sb, A.S_dyn, A.slot_part);
+        if (!A.part[part].active) continue;
+        bool ee = r.flags & 1;
+        double o[3];
+        for (int k = 0; k < 3; ++k) o[k] = A.x[3 * (int64_t)r.v[0] + k];
+        T X[12];
+        for (int v = 0; v < 4; ++v)
+            for (int k = 0; k < 3; ++k) X[3 * v + k] = T(A.x[3 * (int64_t)r.v[v] + k] - o[k]);
+        T E, gx[12], H[144];
+        T d = pair_energy_derivs<T>(ee, X, T(A.dhat), T(A.kB), T(r.eps), E, gx, H);
+        if (!(d < T(A.dhat)) || !(d > T(0))) continue;
+        psd_project<T, 12>(H);
+        double w = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
+        int sl[4];
+        T xi[4][4];
+        for (int v = 0; v < 4; ++v) {
+            int s = A.sv_slot[r.v[v]];
+            sl[v] = s < A.S_dyn ? s : -1;
+            int b = A.slot_body[s];
+            const double *xb = A.xbar + 3 * ((int64_t)A.voff[b] + (r.v[v] - A.slot_voff[s]));
+            xi[v][0] = T(1); xi[v][1] = T(xb[0]); xi[v][2] = T(xb[1]); xi[v][3] = T(xb[2]);
+        }
+        for (int v = 0; v < 4; ++v) {
+            if (sl[v] < 0) continue;
+            for (int k = 0; k < 3; ++k)
+                for (int a = 0; a < 4; ++a)
+                    atomicAdd(A.g + 12 * (int64_t)sl[v] + qidx(k, a), w * (double)(gx[3 * v + k] * xi[v][a]));
+        }
+        // slot-pair blocks: (sa, sa), (sb, sb), (min, max)
+        int ss[2] = {sa < A.S_dyn ? sa : -1, sb < A.S_dyn ? sb : -1};
+        for (int bi = 0; bi < 2; ++bi)
+            for (int bj = bi; bj < 2; ++bj) {
+                int s1 = ss[bi], s2 = ss[bj];
+                if (s1 < 0 || s2 < 0) continue;
+                if (bi != bj && s1 == s2) continue;
+                T *dst;
+                bool tr = false;
+                if (bi == bj) dst = diag + 144 * (int64_t)s1;
+                else {
+                    int2 lp = l1[r.l1];
+                    dst = off + 144 * (int64_t)r.l1;
+                    tr = (lp.x != s1);
+                    offflag[r.l1] = 1;
+                }
+                T acc[144];
+                for (int e = 0; e < 144; ++e) acc[e] = T(0);
+                for (int v = 0; v < 4; ++v) {
+                    if (sl[v] != s1) continue;
+                    for (int u = 0; u < 4; ++u) {
+                        if (sl[u] != s2) continue;
+                        for (int k = 0; k < 3; ++k)
+                            for (int l = 0; l < 3; ++l) {
+                                T hv = H[(3 * v + k) * 12 + 3 * u + l];
+                                if (hv == T(0)) continue;
+                                for (int a = 0; a < 4; ++a)
+                                    for (int c = 0; c < 4; ++c) acc[qidx(k, a) * 12 + qidx(l, c)] += hv * xi[v][a] * xi[u][c];
+                            }
+                    }
+                }
+                for (int rr = 0; rr < 12; ++rr)
+                    for (int cc = 0; cc < 12; ++cc) {
+                        T val = T(w) * acc[rr * 12 + cc];
+                        if (val != T(0)) atomic_addT(dst + (tr ? cc * 12 + rr : rr * 12 + cc), val);
+                    }
+            }
+    }
+}
+
+// Vertex-plane barrier of dynamic slot vertices.
+template <class T>
+__global__ void k_vp_assemble(AsmArgs A, int64_t SVd, T *__restrict__ diag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < SVd; i += (int64_t)gridDim.x * blockDim.x) {
+        int s = A.sv_slot[i];
+        if (!A.part[A.slot_part[s]].active) continue;
+        for (int pl = 0; pl < A.planes.n; ++pl) {
+            int ax = A.planes.axis[pl];
+            double d = A.planes.sign[pl] * A.x[3 * i + ax] - A.planes.offset[pl];
+            if (!(d < A.dhat) || !(d > 0.0)) continue;
+            double bb, b1, b2;
+            barrier3<double>(d, A.dhat, bb, b1, b2);
+            double w = A.h * A.h / (double)__popcll(A.slot_mask[s]) * A.kB;
+            int b = A.slot_body[s];
+            const double *xb = A.xbar + 3 * ((int64_t)A.voff[b] + (i - A.slot_voff[s]));
+            double xi[4] = {1.0, xb[0], xb[1], xb[2]};
+            double ga = w * b1 * A.planes.sign[pl], ha = w * b2;
+            for (int a = 0; a < 4; ++a) atomicAdd(A.g + 12 * (int64_t)s + qidx(ax, a), ga * xi[a]);
+            T *D = diag + 144 * (int64_t)s;
+            for (int a = 0; a < 4; ++a)
+                for (int c = 0; c < 4; ++c) atomic_addT(D + qidx(ax, a) * 12 + qidx(ax, c), T(ha * xi[a] * xi[c]));
+        }
+    }
+}
+
+// CCD over swept candidates: min TOI per partition; pairs that can come within
+// dhat somewhere on the path (d0 - l_p < dhat, l_p bounding the distance
+// change) go to the line-search list.
+__global__ void k_ccd(const PairRec *__restrict__ cand, int64_t n, const double *__restrict__ x0,
+                      const double *__restrict__ x1, const int *__restrict__ sv_slot, const int *__restrict__ slot_part,
+                      int S_dyn, double dhat, double s_, double c_, PartState *__restrict__ part,
+                      PairRec *__restrict__ ls, int64_t cap, unsigned long long *__restrict__ count, int want_ls) {
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        bool keep = false;
+        PairRec r;
+        if (i < n) {
+            r = cand[i];
+            bool ee = r.flags & 1;
+            double X[12], dX[12];
+            for (int v = 0; v < 4; ++v)
+                for (int k = 0; k < 3; ++k) {
+                    double a = x0[3 * (int64_t)r.v[v] + k];
+                    X[3 * v + k] = a;
+                    dX[3 * v + k] = x1[3 * (int64_t)r.v[v] + k] - a;
+                }
+            int sa, sb;
+            pair_slots(r, sv_slot, sa, sb);
+            int p = pair_part(sa, sb, S_dyn, slot_part);
+            double t = accd(ee, X, dX, s_, c_, 1000000);
+            if (t < 1.0) atomicMin(&part[p].toi, ord(t));
+            if (want_ls) {
+                double mean[3] = {0, 0, 0}, nn[4];
+                for (int v = 0; v < 4; ++v)
+                    for (int k = 0; k < 3; ++k) mean[k] += 0.25 * dX[3 * v + k];
+                for (int v = 0; v < 4; ++v) {
+                    double a0 = dX[3 * v] - mean[0], a1 = dX[3 * v + 1] - mean[1], a2 = dX[3 * v + 2] - mean[2];
+                    nn[v] = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+                }
+                double lp = ee ? fmax(nn[0], nn[1]) + fmax(nn[2], nn[3]) : nn[0] + fmax(nn[1], fmax(nn[2], nn[3]));
+                int ty;
+                double b0, b1;
+                double d0 = sqrt(classify<double>(ee, X, ty, b0, b1));
+                keep = d0 - lp < dhat;
+            }
+        }
+        if (want_ls) append(keep, r, ls, cap, count);
+    }
+}
+
+__global__ void k_vp_ccd(int64_t SVd, const double *__restrict__ x0, const double *__restrict__ x1,
+                         const int *__restrict__ sv_slot, const int *__restrict__ slot_part, Planes pl, double s_,
+                         PartState *__restrict__ part) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < SVd; i += (int64_t)gridDim.x * blockDim.x) {
+        int p = slot_part[sv_slot[i]];
+        if (!part[p].active) continue;
+        for (int k = 0; k < pl.n; ++k) {
+            int ax = pl.axis[k];
+            double d0 = pl.sign[k] * x0[3 * i + ax] - pl.offset[k];
+            double dd = pl.sign[k] * (x1[3 * i + ax] - x0[3 * i + ax]);
+            double t = accd_plane(d0, dd, s_);
+            if (t < 1.0) atomicMin(&part[p].toi, ord(t));
+        }
+    }
+}
+
+// Accumulate v into part[p].E[j].  Called by all 32 lanes with a uniform j;
+// lanes with nothing to add pass p < 0.  One atomic per warp when every
+// contributing lane has the same partition, else one per lane.
+__device__ __forceinline__ void add_energy(PartState *part, int p, int j, double v) {
+    const unsigned full = 0xffffffffu;
+    int pmax = __reduce_max_sync(full, p);
+    int pmin = __reduce_min_sync(full, p < 0 ? 0x7fffffff : p);
+    if (pmax < 0) return;
+    if (pmin == pmax) {
+        double t = p < 0 ? 0.0 : v;
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(full, t, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&part[pmax].E[j], t);
+    } else if (p >= 0) {
+        atomicAdd(&part[p].E[j], v);
+    }
+}
+
+struct EnArgs {
+    int S_dyn;
+    const int *slot_body, *slot_part, *slot_rep, *sv_slot;
+    const unsigned long long *slot_mask;
+    const double *slot_kw, *mass, *S, *vol, *kappa;
+    const double *q, *dq, *qtil, *z, *u, *rho;
+    const double *x0, *x1;
+    const double *alphas;  // [NP][kLS+1], alphas[.][0] = 0
+    PartState *part;
+    double h, dhat, kB;
+    Planes planes;
+};
+
+__device__ double slot_energy(const EnArgs &A, int s, double al) {
+    int b = A.slot_body[s];
+    double q[12], d[12];
+    for (int i = 0; i < 12; ++i) {
+        q[i] = A.q[12 * (int64_t)s + i] + al * A.dq[12 * (int64_t)s + i];
+        d[i] = q[i] - A.qtil[12 * (int64_t)s + i];
+    }
+    const double *S = A.S + 9 * (int64_t)b;
+    double E = 0.5 * A.mass[b] * (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    for (int k = 0; k < 3; ++k) {
+        const double *a = d + 3 + 3 * k;
+        for (int i = 0; i < 3; ++i) E += 0.5 * a[i] * (S[3 * i] * a[0] + S[3 * i + 1] * a[1] + S[3 * i + 2] * a[2]);
+    }
+    double orth = 0.0;
+    for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+            double c = q[3 + 3 * k] * q[3 + 3 * l] + q[4 + 3 * k] * q[4 + 3 * l] + q[5 + 3 * k] * q[5 + 3 * l] - (k == l);
+            orth += c * c;
+        }
+    E += A.h * A.h * A.kappa[b] * A.vol[b] * orth;
+    E *= A.slot_kw[s];
+    if (A.slot_rep[s] >= 0) {
+        double acc = 0.0;
+        for (int i = 0; i < 12; ++i) {
+            double r = q[i] - A.z[12 * (int64_t)s + i] + A.u[12 * (int64_t)s + i];
+            acc += r * r;
+        }
+        E += 0.5 * A.rho[s] * acc;
+    }
+    return E;
+}
+
+__global__ void k_energy_slots(EnArgs A) {
+    for (int base = blockIdx.x * blockDim.x; base < A.S_dyn; base += gridDim.x * blockDim.x) {
+        int s = base + threadIdx.x;
+        int p = s < A.S_dyn ? A.slot_part[s] : -1;
+        if (p >= 0 && !A.part[p].active) p = -1;
+        for (int j = 0; j <= kLS; ++j) {
+            double al = p >= 0 ? A.alphas[(kLS + 1) * p + j] : -1.0;
+            bool use = p >= 0 && (j == 0 || al >= 0.0);
+            double v = use ? slot_energy(A, s, al) : 0.0;
+            add_energy(A.part, use ? p : -1, j, v);
+        }
+    }
+}
+
+__global__ void k_energy_pairs(EnArgs A, const PairRec *__restrict__ ls, int64_t n) {
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        int p = -1;
+        PairRec r;
+        double w = 0.0, X0[12], DX[12];
+        if (i < n) {
+            r = ls[i];
+            int sa, sb;
+            pair_slots(r, A.sv_slot, sa, sb);
+            p = pair_part(sa, sb, A.S_dyn, A.slot_part);
+            if (!A.part[p].active) p = -1;
+            w = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
+            for (int v = 0; v < 4; ++v)
+                for (int k = 0; k < 3; ++k) {
+                    double a = A.x0[3 * (int64_t)r.v[v] + k];
+                    X0[3 * v + k] = a;
+                    DX[3 * v + k] = A.x1[3 * (int64_t)r.v[v] + k] - a;
+                }
+        }
+        for (int j = 0; j <= kLS; ++j) {
+            double al = p >= 0 ? A.alphas[(kLS + 1) * p + j] : -1.0;
+            bool use = p >= 0 && (j == 0 || al >= 0.0);
+            double e = 0.0;
+            if (use) {
+                double X[12], d;
+                for (int q = 0; q < 12; ++q) X[q] = X0[q] + al * DX[q];
+                e = w * pair_energy(r.flags & 1, X, A.dhat, A.kB, r.eps, d);
+            }
+            add_energy(A.part, use ? p : -1, j, e);
+        }
+    }
+}
+
+__global__ void k_energy_vp(EnArgs A, int64_t SVd) {
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < SVd; base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        int p = -1, s = 0;
+        if (i < SVd) {
+            s = A.sv_slot[i];
+            p = A.slot_part[s];
+            if (!A.part[p].active) p = -1;
+        }
+        double w = p >= 0 ? A.h * A.h / (double)__popcll(A.slot_mask[s]) * A.kB : 0.0;
+        for (int j = 0; j <= kLS; ++j) {
+            double al = p >= 0 ? A.alphas[(kLS + 1) * p + j] : -1.0;
+            bool use = p >= 0 && (j == 0 || al >= 0.0);
+            double e = 0.0;
+            if (use)
+                for (int k = 0; k < A.planes.n; ++k) {
+                    int ax = A.planes.axis[k];
+                    double xa = A.x0[3 * i + ax] + al * (A.x1[3 * i + ax] - A.x0[3 * i + ax]);
+                    double d = A.planes.sign[k] * xa - A.planes.offset[k];
+                    if (!(d > 0.0)) e += 1.0 / 0.0;
+                    else if (d < A.dhat) {
+                        double bb, b1, b2;
+                        barrier3<double>(d, A.dhat, bb, b1, b2);
+                        e += w * bb;
+                    }
+                }
+            add_energy(A.part, use && e != 0.0 ? p : -1, j, e);
+        }
+    }
+}
+
+}  // namespace abd
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+namespace abd {
+
+static AsmArgs make_asm(abd_scene *s, const abd_step_params *p, double kB) {
+    World &w = s->w;
+    AsmArgs A;
+    A.S_dyn = w.S_dyn;
+    A.slot_body = P<int>(w.slot_body); A.slot_part = P<int>(w.slot_part); A.slot_rep = P<int>(w.slot_rep);
+    A.sv_slot = P<int>(w.sv_slot); A.slot_mask = P<unsigned long long>(w.slot_mask); A.slot_kw = P<double>(w.slot_kw);
+    A.voff = P<int>(s->dev.voff); A.xbar = P<double>(s->dev.xbar); A.mass = P<double>(s->dev.mass);
+    A.S = P<double>(s->dev.S); A.vol = P<double>(s->dev.vol); A.kappa = P<double>(s->dev.kappa);
+    A.q = P<double>(w.q); A.qtil = P<double>(w.qtil); A.z = P<double>(w.z); A.u = P<double>(w.u);
+    A.rho = P<double>(w.rho); A.x = P<double>(w.x); A.part = P<PartState>(w.part);
+    A.h = p->h; A.dhat = p->dhat; A.kB = kB; A.planes = s->planes;
+    A.slot_voff = P<int64_t>(w.slot_voff);
+    A.g = P<double>(w.g);
+    return A;
+}
+
+static int read_u64(abd_scene *s, unsigned long long *d, unsigned long long *h) {
+    cudaError_t e = cudaMemcpyAsync(h, d, 8, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    return cuda_check(s, e, "read counter");
+}
+
+int launch_narrow(abd_scene *s, int64_t n_cand, double dhat, int64_t *n_act) {
+    World &w = s->w;
+    Counters *c = P<Counters>(w.ctr);
+    if (w.cap_act == 0) {
+        w.cap_act = 1 << 14;
+        if (!dbuf_ensure(w.act, sizeof(PairRec) * w.cap_act)) return set_err(s, ABD_E_OOM, "active list");
+    }
+    for (;;) {
+        cudaMemsetAsync(&c->act, 0, 8, s->stream);
+        if (n_cand > 0)
+            k_narrow<<<grid_for(n_cand, 256), 256, 0, s->stream>>>(P<PairRec>(w.cand), n_cand, P<double>(w.x), dhat,
+                                                                  P<PairRec>(w.act), w.cap_act, &c->act);
+        int rc = cuda_check(s, cudaGetLastError(), "k_narrow");
+        if (rc) return rc;
+        unsigned long long n = 0;
+        if ((rc = read_u64(s, &c->act, &n))) return rc;
+        if ((int64_t)n <= w.cap_act) {
+            *n_act = (int64_t)n;
+            return ABD_OK;
+        }
+        w.cap_act = (int64_t)n + n / 2 + 1024;
+        if (!dbuf_ensure(w.act, sizeof(PairRec) * w.cap_act)) return set_err(s, ABD_E_OOM, "active list");
+    }
+}
+
+template <class T>
+static int assemble_T(abd_scene *s, const abd_step_params *p, double kB, int64_t n_act, int64_t n_l1) {
+    World &w = s->w;
+    AsmArgs A = make_asm(s, p, kB);
+    if (!dbuf_ensure(w.diag, sizeof(T) * 144 * (size_t)(w.S_dyn ? w.S_dyn : 1))) return set_err(s, ABD_E_OOM, "diag");
+    if (!dbuf_ensure(w.off, sizeof(T) * 144 * (size_t)(n_l1 ? n_l1 : 1)) ||
+        !dbuf_ensure(w.offflag, sizeof(int) * (size_t)(n_l1 ? n_l1 : 1)))
+        return set_err(s, ABD_E_OOM, "off-diagonal blocks");
+    if (n_l1 > 0) {
+        cudaMemsetAsync(w.off.p, 0, sizeof(T) * 144 * (size_t)n_l1, s->stream);
+        cudaMemsetAsync(w.offflag.p, 0, sizeof(int) * (size_t)n_l1, s->stream);
+    }
+    cudaEvent_t ea, eb;
+    if (w.S_dyn > 0) {
+        prof_begin(s, "slot_assemble", 0, &ea, &eb);
+        k_slot_assemble<T><<<grid_for(w.S_dyn, 128), 128, 0, s->stream>>>(A, P<T>(w.diag));
+        prof_end(s, ea, eb, prof_index(s, "slot_assemble"));
+    }
+    if (n_act > 0) {
+        prof_begin(s, "pair_assemble", 0, &ea, &eb);
+        k_pair_assemble<T><<<grid_for(n_act, 64), 64, 0, s->stream>>>(A, P<PairRec>(w.act), n_act, P<int2>(w.l1),
+                                                                      P<T>(w.diag), P<T>(w.off), P<int>(w.offflag));
+        prof_end(s, ea, eb, prof_index(s, "pair_assemble"));
+    }
+    int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
+    if (s->planes.n > 0 && SVd > 0)
+        k_vp_assemble<T><<<grid_for(SVd, 256), 256, 0, s->stream>>>(A, SVd, P<T>(w.diag));
+    return cuda_check(s, cudaGetLastError(), "assemble");
+}
+
+int launch_assemble(abd_scene *s, int precision, const abd_step_params *p, double kB, int64_t n_act, int64_t n_l1) {
+    return precision == ABD_MIXED ? assemble_T<float>(s, p, kB, n_act, n_l1) : assemble_T<double>(s, p, kB, n_act, n_l1);
+}
+
+int launch_ccd(abd_scene *s, int64_t n_sw, const abd_step_params *p, double dhat, int64_t *n_ls, bool want_ls) {
+    World &w = s->w;
+    Counters *c = P<Counters>(w.ctr);
+    if (w.cap_ls == 0) {
+        w.cap_ls = 1 << 14;
+        if (!dbuf_ensure(w.ls, sizeof(PairRec) * w.cap_ls)) return set_err(s, ABD_E_OOM, "line-search list");
+    }
+    int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
+    for (;;) {
+        cudaMemsetAsync(&c->ls, 0, 8, s->stream);
+        cudaEvent_t ea, eb;
+        if (n_sw > 0) {
+            prof_begin(s, "ccd", 0, &ea, &eb);
+            k_ccd<<<grid_for(n_sw, 128), 128, 0, s->stream>>>(P<PairRec>(w.cand), n_sw, P<double>(w.x),
+                                                             P<double>(w.x1), P<int>(w.sv_slot), P<int>(w.slot_part),
+                                                             w.S_dyn, dhat, p->accd_s, p->accd_c, P<PartState>(w.part),
+                                                             P<PairRec>(w.ls), w.cap_ls, &c->ls, want_ls ? 1 : 0);
+            prof_end(s, ea, eb, prof_index(s, "ccd"));
+        }
+        if (s->planes.n > 0 && SVd > 0)
+            k_vp_ccd<<<grid_for(SVd, 256), 256, 0, s->stream>>>(SVd, P<double>(w.x), P<double>(w.x1), P<int>(w.sv_slot),
+                                                                P<int>(w.slot_part), s->planes, p->accd_s,
+                                                                P<PartState>(w.part));
+        int rc = cuda_check(s, cudaGetLastError(), "k_ccd");
+        if (rc) return rc;
+        unsigned long long n = 0;
+        if ((rc = read_u64(s, &c->ls, &n))) return rc;
+        if (!want_ls || (int64_t)n <= w.cap_ls) {
+            *n_ls = (int64_t)n;
+            return ABD_OK;
+        }
+        w.cap_ls = (int64_t)n + n / 2 + 1024;
+        if (!dbuf_ensure(w.ls, sizeof(PairRec) * w.cap_ls)) return set_err(s, ABD_E_OOM, "line-search list");
+    }
+}
+
+int launch_energy(abd_scene *s, const abd_step_params *p, double kB, int64_t n_ls, const double *alphas_dev) {
+    World &w = s->w;
+    EnArgs A;
+    A.S_dyn = w.S_dyn;
+    A.slot_body = P<int>(w.slot_body); A.slot_part = P<int>(w.slot_part); A.slot_rep = P<int>(w.slot_rep);
+    A.sv_slot = P<int>(w.sv_slot); A.slot_mask = P<unsigned long long>(w.slot_mask); A.slot_kw = P<double>(w.slot_kw);
+    A.mass = P<double>(s->dev.mass); A.S = P<double>(s->dev.S); A.vol = P<double>(s->dev.vol);
+    A.kappa = P<double>(s->dev.kappa);
+    A.q = P<double>(w.q); A.dq = P<double>(w.dq); A.qtil = P<double>(w.qtil); A.z = P<double>(w.z);
+    A.u = P<double>(w.u); A.rho = P<double>(w.rho); A.x0 = P<double>(w.x); A.x1 = P<double>(w.x1);
+    A.alphas = alphas_dev; A.part = P<PartState>(w.part);
+    A.h = p->h; A.dhat = p->dhat; A.kB = kB; A.planes = s->planes;
+    int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
+    if (w.S_dyn > 0) k_energy_slots<<<grid_for(w.S_dyn, 128), 128, 0, s->stream>>>(A);
+    if (n_ls > 0) k_energy_pairs<<<grid_for(n_ls, 128), 128, 0, s->stream>>>(A, P<PairRec>(w.ls), n_ls);
+    if (s->planes.n > 0 && SVd > 0) k_energy_vp<<<grid_for(SVd, 128), 128, 0, s->stream>>>(A, SVd);
+    return cuda_check(s, cudaGetLastError(), "energy");
+}
+
+}  // namespace abd

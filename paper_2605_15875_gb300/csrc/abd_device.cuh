@@ -1,0 +1,452 @@
+// abd_device.cuh -- per-primitive math of ABD-IPC on sm_103a.
+//
+// Distance types, distance derivatives, the IPC log barrier, the edge-edge
+// mollifier, PSD projection and additive CCD, written for one thread per
+// primitive pair.  Templated on the assembly precision T (double for the FP64
+// path, float for the mixed path); positions always arrive in FP64 and are
+// shifted to a pair-local origin in FP64 before any rounding to T, so FP32
+// assembly keeps the relative precision of the short difference vectors.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace abd {
+
+template <class T> __device__ __forceinline__ T tsqrt(T x);
+template <> __device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
+template <class T> __device__ __forceinline__ T tlog(T x);
+template <> __device__ __forceinline__ double tlog<double>(double x) { return log(x); }
+template <> __device__ __forceinline__ float tlog<float>(float x) { return logf(x); }
+template <class T> __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+
+template <class T> __device__ __forceinline__ T dot3(const T *a, const T *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+template <class T> __device__ __forceinline__ void cross3(T *o, const T *a, const T *b) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// ---------------------------------------------------------------------------
+// Closest features.  PT: X0 point, X1..X3 triangle.  Codes 0..2 point-vertex,
+// 3..5 point-edge (t0t1, t1t2, t2t0), 6 point-face.  EE: X0X1 edge a, X2X3
+// edge b.  Codes 0..3 vertex-vertex (a_i, b_j) = 2i + j, 4..5 a_i to edge b,
+// 6..7 b_j to edge a, 8 edge-edge interior.  The feature is the one holding
+// the exact closest points: the unconstrained minimiser if it lies inside the
+// parameter domain, else the best boundary sub-problem, scanned in a fixed
+// order with strict improvement.  Nearly parallel edges (sin^2 <= 1e-10) use
+// the boundary sub-problems.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T seg_closest(const T *p, const T *a, const T *b, T &t) {
+    T ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    T ap[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+    T L = dot3(ab, ab);
+    t = L > T(0) ? dot3(ap, ab) / L : T(0);
+    t = t < T(0) ? T(0) : (t > T(1) ? T(1) : t);
+    T r[3] = {ap[0] - t * ab[0], ap[1] - t * ab[1], ap[2] - t * ab[2]};
+    return dot3(r, r);
+}
+
+template <class T>
+__device__ T classify(bool ee, const T *X, int &type, T &b0, T &b1) {
+    b0 = b1 = T(0);
+    if (!ee) {
+        const T *p = X, *t0 = X + 3;
+        T e1[3] = {X[6] - X[3], X[7] - X[4], X[8] - X[5]};
+        T e2[3] = {X[9] - X[3], X[10] - X[4], X[11] - X[5]};
+        T ap[3] = {p[0] - t0[0], p[1] - t0[1], p[2] - t0[2]};
+        T G00 = dot3(e1, e1), G01 = dot3(e1, e2), G11 = dot3(e2, e2);
+        T r0 = dot3(ap, e1), r1 = dot3(ap, e2);
+        T det = G00 * G11 - G01 * G01;
+        if (det > T(0)) {
+            T u = (r0 * G11 - r1 * G01) / det, v = (G00 * r1 - G01 * r0) / det;
+            if (u >= T(0) && v >= T(0) && u + v <= T(1)) {
+                T r[3];
+                for (int k = 0; k < 3; ++k) r[k] = ap[k] - u * e1[k] - v * e2[k];
+                type = 6; b0 = u; b1 = v;
+                return dot3(r, r);
+            }
+        }
+        T best = sizeof(T) == 8 ? T(1e300) : T(3e38);
+        for (int e = 0; e < 3; ++e) {
+            int m = e, n = e == 2 ? 0 : e + 1;
+            T t;
+            T d2 = seg_closest(p, X + 3 + 3 * m, X + 3 + 3 * n, t);
+            if (d2 < best) {
+                best = d2;
+                if (t == T(0)) { type = m; b0 = T(0); }
+                else if (t == T(1)) { type = n; b0 = T(0); }
+                else { type = 3 + e; b0 = t; }
+            }
+        }
+        return best;
+    }
+    const T *a0 = X, *a1 = X + 3, *bb0 = X + 6, *bb1 = X + 9;
+    T ea[3] = {a1[0] - a0[0], a1[1] - a0[1], a1[2] - a0[2]};
+    T eb[3] = {bb1[0] - bb0[0], bb1[1] - bb0[1], bb1[2] - bb0[2]};
+    T w[3] = {a0[0] - bb0[0], a0[1] - bb0[1], a0[2] - bb0[2]};
+    T A = dot3(ea, ea), B = dot3(ea, eb), C = dot3(eb, eb), D = dot3(ea, w), E = dot3(eb, w);
+    T den = A * C - B * B;
+    if (den > T(1e-10) * A * C) {
+        T s = (B * E - C * D) / den, t = (A * E - B * D) / den;
+        if (s >= T(0) && s <= T(1) && t >= T(0) && t <= T(1)) {
+            T r[3];
+            for (int k = 0; k < 3; ++k) r[k] = w[k] + s * ea[k] - t * eb[k];
+            type = 8; b0 = s; b1 = t;
+            return dot3(r, r);
+        }
+    }
+    T best = sizeof(T) == 8 ? T(1e300) : T(3e38);
+    for (int i = 0; i < 2; ++i) {
+        T t;
+        T d2 = seg_closest(X + 3 * i, bb0, bb1, t);
+        if (d2 < best) {
+            best = d2;
+            if (t == T(0)) { type = 2 * i; b0 = T(0); }
+            else if (t == T(1)) { type = 2 * i + 1; b0 = T(0); }
+            else { type = 4 + i; b0 = t; }
+        }
+    }
+    for (int j = 0; j < 2; ++j) {
+        T t;
+        T d2 = seg_closest(X + 6 + 3 * j, a0, a1, t);
+        if (d2 < best) {
+            best = d2;
+            if (t == T(0)) { type = j; b0 = T(0); }
+            else if (t == T(1)) { type = 2 + j; b0 = T(0); }
+            else { type = 6 + j; b0 = t; }
+        }
+    }
+    return best;
+}
+
+// Closest-point parametrisation of a feature: r = sum_v (w0_v + sum_j beta_j c_jv) x_v.
+struct Feature {
+    int k;
+    float w0[4];
+    float c[2][4];
+};
+
+__device__ __forceinline__ Feature feature_of(bool ee, int type) {
+    Feature f;
+    f.k = 0;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) { f.w0[v] = 0.f; f.c[0][v] = 0.f; f.c[1][v] = 0.f; }
+    if (!ee) {
+        f.w0[0] = 1.f;
+        if (type <= 2) f.w0[1 + type] = -1.f;
+        else if (type <= 5) {
+            int m = type - 3, n = m == 2 ? 0 : m + 1;
+            f.k = 1; f.w0[1 + m] = -1.f; f.c[0][1 + m] = 1.f; f.c[0][1 + n] = -1.f;
+        } else {
+            f.k = 2; f.w0[1] = -1.f; f.c[0][1] = 1.f; f.c[0][2] = -1.f; f.c[1][1] = 1.f; f.c[1][3] = -1.f;
+        }
+    } else {
+        if (type <= 3) { f.w0[type >> 1] = 1.f; f.w0[2 + (type & 1)] = -1.f; }
+        else if (type <= 5) { f.k = 1; f.w0[type - 4] = 1.f; f.w0[2] = -1.f; f.c[0][2] = 1.f; f.c[0][3] = -1.f; }
+        else if (type <= 7) { f.k = 1; f.w0[2 + type - 6] = 1.f; f.w0[0] = -1.f; f.c[0][0] = 1.f; f.c[0][1] = -1.f; }
+        else { f.k = 2; f.w0[0] = 1.f; f.w0[2] = -1.f; f.c[0][0] = -1.f; f.c[0][1] = 1.f; f.c[1][2] = 1.f; f.c[1][3] = -1.f; }
+    }
+    return f;
+}
+
+// s = |r|^2 at the stationary beta of the feature, its gradient gs[12] and the
+// upper triangle of its Hessian (full Hs[144] written) by the envelope
+// theorem: grad = 2 w (x) r; hess = 2 (w w^T (x) I3) - 2 sum_ij Ginv_ij g_i g_j^T,
+// D_j = sum_v c_jv x_v, G_ij = D_i . D_j, g_j[v] = w_v D_j + c_jv r.
+template <class T>
+__device__ T dist2_derivs(const T *X, const Feature &f, T b0, T b1, T *gs, T *Hs) {
+    T w[4], r[3] = {0, 0, 0}, D[2][3] = {{0, 0, 0}, {0, 0, 0}};
+#pragma unroll
+    for (int v = 0; v < 4; ++v) w[v] = T(f.w0[v]) + b0 * T(f.c[0][v]) + b1 * T(f.c[1][v]);
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r[a] += w[v] * X[3 * v + a];
+            D[0][a] += T(f.c[0][v]) * X[3 * v + a];
+            D[1][a] += T(f.c[1][v]) * X[3 * v + a];
+        }
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gs[3 * v + a] = T(2) * w[v] * r[a];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) Hs[(3 * v + a) * 12 + 3 * u + b] = a == b ? T(2) * w[v] * w[u] : T(0);
+    if (f.k > 0) {
+        T G00 = dot3(D[0], D[0]), G01 = dot3(D[0], D[1]), G11 = dot3(D[1], D[1]);
+        T i00, i01, i11;
+        if (f.k == 1) { i00 = T(1) / G00; i01 = T(0); i11 = T(0); }
+        else {
+            T det = G00 * G11 - G01 * G01;
+            i00 = G11 / det; i11 = G00 / det; i01 = -G01 / det;
+        }
+        T g0[12], g1[12];
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                g0[3 * v + a] = w[v] * D[0][a] + T(f.c[0][v]) * r[a];
+                g1[3 * v + a] = w[v] * D[1][a] + T(f.c[1][v]) * r[a];
+            }
+#pragma unroll
+        for (int m = 0; m < 12; ++m)
+#pragma unroll
+            for (int n = 0; n < 12; ++n)
+                Hs[m * 12 + n] -= T(2) * (i00 * g0[m] * g0[n] + i01 * (g0[m] * g1[n] + g1[m] * g0[n]) + i11 * g1[m] * g1[n]);
+    }
+    return dot3(r, r);
+}
+
+// IPC log barrier on the unsquared distance: b = -(d - dhat)^2 ln(d / dhat) on (0, dhat).
+template <class T>
+__device__ __forceinline__ void barrier3(T d, T dhat, T &b, T &b1, T &b2) {
+    if (d >= dhat) { b = b1 = b2 = T(0); return; }
+    T e = d - dhat, L = tlog(d / dhat);
+    b = -e * e * L;
+    b1 = T(-2) * e * L - e * e / d;
+    b2 = T(-2) * L - T(4) * e / d + e * e / (d * d);
+}
+
+// Edge-edge mollifier m(c), c = |(a1 - a0) x (b1 - b0)|^2, eps_x from rest lengths:
+// m = (c/eps)(2 - c/eps) below eps, else 1.  Returns m and, when c < eps,
+// m' grad c (gm) and m'' grad c grad c^T + m' hess c (Hm).
+template <class T>
+__device__ T mollifier(const T *X, T eps, T *gm, T *Hm, bool &active) {
+    T ea[3] = {X[3] - X[0], X[4] - X[1], X[5] - X[2]};
+    T eb[3] = {X[9] - X[6], X[10] - X[7], X[11] - X[8]};
+    T cr[3];
+    cross3(cr, ea, eb);
+    T c = dot3(cr, cr);
+    active = c < eps;
+    if (!active) return T(1);
+    T rr = c / eps, m = rr * (T(2) - rr), m1 = (T(2) - T(2) * rr) / eps, m2 = T(-2) / (eps * eps);
+    T ge[6], t[3];
+    cross3(t, eb, cr);
+    ge[0] = T(2) * t[0]; ge[1] = T(2) * t[1]; ge[2] = T(2) * t[2];
+    cross3(t, cr, ea);
+    ge[3] = T(2) * t[0]; ge[4] = T(2) * t[1]; ge[5] = T(2) * t[2];
+    // J = [d cr/d ea, d cr/d eb] = [-[eb]x, [ea]x]
+    T J[3][6] = {{0, eb[2], -eb[1], 0, -ea[2], ea[1]},
+                 {-eb[2], 0, eb[0], ea[2], 0, -ea[0]},
+                 {eb[1], -eb[0], 0, -ea[1], ea[0], 0}};
+    T crx[3][3] = {{0, -cr[2], cr[1]}, {cr[2], 0, -cr[0]}, {-cr[1], cr[0], 0}};
+    T He[6][6];
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int b = 0; b < 6; ++b) He[a][b] = T(2) * (J[0][a] * J[0][b] + J[1][a] * J[1][b] + J[2][a] * J[2][b]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { He[j][3 + k] -= T(2) * crx[j][k]; He[3 + j][k] += T(2) * crx[j][k]; }
+    const T sg[4] = {T(-1), T(1), T(-1), T(1)};
+    T gc[12];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gc[3 * v + a] = sg[v] * ge[3 * (v >> 1) + a];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) gm[i] = m1 * gc[i];
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+                    Hm[(3 * v + a) * 12 + 3 * u + b] =
+                        m2 * gc[3 * v + a] * gc[3 * u + b] + m1 * sg[v] * sg[u] * He[3 * (v >> 1) + a][3 * (u >> 1) + b];
+    return m;
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix in place;
+// V receives the eigenvectors as columns.
+template <class T, int N>
+__device__ void jacobi(T *A, T *V) {
+    for (int i = 0; i < N * N; ++i) V[i] = T(0);
+    for (int i = 0; i < N; ++i) V[i * N + i] = T(1);
+    const T tol = sizeof(T) == 8 ? T(1e-30) : T(1e-13);
+    for (int sweep = 0; sweep < (sizeof(T) == 8 ? 30 : 15); ++sweep) {
+        T off = T(0), tot = T(0);
+        for (int i = 0; i < N; ++i)
+            for (int j = 0; j < N; ++j) {
+                T a2 = A[i * N + j] * A[i * N + j];
+                tot += a2;
+                if (i != j) off += a2;
+            }
+        if (off <= tol * tot || off == T(0)) break;
+        for (int p = 0; p < N - 1; ++p)
+            for (int q = p + 1; q < N; ++q) {
+                T apq = A[p * N + q];
+                if (apq == T(0)) continue;
+                T theta = (A[q * N + q] - A[p * N + p]) / (T(2) * apq);
+                T t = (theta >= T(0) ? T(1) : T(-1)) / (tabs(theta) + tsqrt(theta * theta + T(1)));
+                T c = T(1) / tsqrt(t * t + T(1)), s = t * c;
+                for (int k = 0; k < N; ++k) {
+                    T akp = A[k * N + p], akq = A[k * N + q];
+                    A[k * N + p] = c * akp - s * akq;
+                    A[k * N + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < N; ++k) {
+                    T apk = A[p * N + k], aqk = A[q * N + k];
+                    A[p * N + k] = c * apk - s * aqk;
+                    A[q * N + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < N; ++k) {
+                    T vkp = V[k * N + p], vkq = V[k * N + q];
+                    V[k * N + p] = c * vkp - s * vkq;
+                    V[k * N + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+}
+
+// Nearest PSD matrix (negative eigenvalues clamped to zero); a matrix without
+// negative eigenvalues is left unchanged.
+template <class T, int N>
+__device__ void psd_project(T *H) {
+    T E[N * N], V[N * N];
+    for (int i = 0; i < N * N; ++i) E[i] = H[i];
+    jacobi<T, N>(E, V);
+    bool neg = false;
+    for (int i = 0; i < N; ++i) neg |= E[i * N + i] < T(0);
+    if (!neg) return;
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+            T s = T(0);
+            for (int k = 0; k < N; ++k) {
+                T lam = E[k * N + k];
+                if (lam > T(0)) s += V[i * N + k] * lam * V[j * N + k];
+            }
+            H[i * N + j] = s;
+        }
+}
+
+// Barrier energy of one PT/EE pair (kB * [m(c)] * b(d)) with gradient and raw
+// Hessian in pair-local coordinates X (12).  Returns the distance; when
+// d >= dhat nothing is written.
+template <class T>
+__device__ T pair_energy_derivs(bool ee, const T *X, T dhat, T kB, T eps_x, T &E, T *g, T *H) {
+    int type;
+    T b0, b1;
+    T s2 = classify<T>(ee, X, type, b0, b1);
+    T d = tsqrt(s2);
+    if (!(d < dhat) || !(d > T(0))) return d;
+    Feature f = feature_of(ee, type);
+    T gs[12];
+    dist2_derivs<T>(X, f, b0, b1, gs, H);  // H <- hess s
+    T b, bp, bpp;
+    barrier3<T>(d, dhat, b, bp, bpp);
+    T inv2d = T(1) / (T(2) * d);
+    T gd[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) gd[i] = gs[i] * inv2d;
+    // hess b = b'' gd gd^T + b' (Hs / 2d - gs gs^T / 4d^3) = (b'' - b'/d) gd gd^T + (b'/2d) Hs
+    T cg = bpp - bp / d, ch = bp * inv2d;
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+#pragma unroll
+        for (int j = 0; j < 12; ++j) H[i * 12 + j] = cg * gd[i] * gd[j] + ch * H[i * 12 + j];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) g[i] = bp * gd[i];
+    if (ee) {
+        T gm[12], Hm[144];
+        bool act;
+        T m = mollifier<T>(X, eps_x, gm, Hm, act);
+        if (act) {
+#pragma unroll
+            for (int i = 0; i < 12; ++i)
+#pragma unroll
+                for (int j = 0; j < 12; ++j)
+                    H[i * 12 + j] = Hm[i * 12 + j] * b + gm[i] * g[j] + g[i] * gm[j] + m * H[i * 12 + j];
+#pragma unroll
+            for (int i = 0; i < 12; ++i) g[i] = gm[i] * b + m * g[i];
+            b *= m;
+        }
+    }
+    E = kB * b;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) g[i] *= kB;
+#pragma unroll
+    for (int i = 0; i < 144; ++i) H[i] *= kB;
+    return d;
+}
+
+// Barrier energy only (no derivatives), FP64.
+__device__ __forceinline__ double pair_energy(bool ee, const double *X, double dhat, double kB, double eps_x, double &d) {
+    int type;
+    double b0, b1;
+    d = sqrt(classify<double>(ee, X, type, b0, b1));
+    if (!(d > 0.0)) return 1.0 / 0.0;
+    if (!(d < dhat)) return 0.0;
+    double b, bp, bpp;
+    barrier3<double>(d, dhat, b, bp, bpp);
+    if (ee) {
+        double ea[3] = {X[3] - X[0], X[4] - X[1], X[5] - X[2]};
+        double eb[3] = {X[9] - X[6], X[10] - X[7], X[11] - X[8]};
+        double cr[3];
+        cross3(cr, ea, eb);
+        double c = dot3(cr, cr);
+        if (c < eps_x) {
+            double rr = c / eps_x;
+            b *= rr * (2.0 - rr);
+        }
+    }
+    return kB * b;
+}
+
+// Additive CCD (Li et al. 2021) along X -> X + dX, t in [0, 1], FP64.
+// Displacements shifted to zero mean; l_p = max displacement norm per side,
+// summed.  First advance (1 - s) d0 / l_p, later c d / l_p; an advance
+// reaching t = 1 certifies the path (exactly 1); once the distance after a
+// later advance drops below s d0, the previous time is returned.
+__device__ inline double accd(bool ee, const double *X, const double *dX, double s, double c, int max_iter) {
+    double mean[3] = {0, 0, 0};
+    for (int v = 0; v < 4; ++v)
+        for (int a = 0; a < 3; ++a) mean[a] += 0.25 * dX[3 * v + a];
+    double n[4];
+    for (int v = 0; v < 4; ++v) {
+        double p0 = dX[3 * v] - mean[0], p1 = dX[3 * v + 1] - mean[1], p2 = dX[3 * v + 2] - mean[2];
+        n[v] = sqrt(p0 * p0 + p1 * p1 + p2 * p2);
+    }
+    double lp = ee ? fmax(n[0], n[1]) + fmax(n[2], n[3]) : n[0] + fmax(n[1], fmax(n[2], n[3]));
+    if (lp == 0.0) return 1.0;
+    int ty;
+    double b0, b1;
+    double d = sqrt(classify<double>(ee, X, ty, b0, b1));
+    if (!(d > 0.0)) return 0.0;
+    double g = s * d, t = 0.0, step = (1.0 - s) * d / lp;
+    for (int it = 0; it < max_iter; ++it) {
+        if (t + step >= 1.0) return 1.0;
+        double tn = t + step, Xn[12];
+        for (int i = 0; i < 12; ++i) Xn[i] = X[i] + tn * dX[i];
+        double dn = sqrt(classify<double>(ee, Xn, ty, b0, b1));
+        if (t > 0.0 && dn < g) return t;
+        t = tn;
+        d = dn;
+        step = c * d / lp;
+    }
+    return t;
+}
+
+__device__ __forceinline__ double accd_plane(double d0, double dd, double s) {
+    if (!(d0 > 0.0)) return 0.0;
+    if (dd >= 0.0) return 1.0;
+    double t = (1.0 - s) * d0 / (-dd);
+    return t < 1.0 ? t : 1.0;
+}
+
+// Order-preserving map of non-negative doubles to uint64 (for atomicMin/Max).
+__device__ __forceinline__ unsigned long long ord(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ double unord(unsigned long long u) { return __longlong_as_double((long long)u); }
+
+}  // namespace abd

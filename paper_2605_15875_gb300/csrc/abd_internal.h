@@ -1,0 +1,173 @@
+// abd_internal.h -- host/device data layout of the GB300 ABD-IPC library.
+//
+// Layout in HBM (all device arrays, FP64 unless noted):
+//   per body (persistent):  q, v [B][12]; mass, vol, kappa [B]; S [B][9];
+//                           xbar [V][3] (centred), tri [T][3], edge [E][2]
+//                           (body-local vertex ids), erest2 [E].
+//   per slot (one per (partition, dynamic body) replica, then one per static
+//   collider, rebuilt every step):  q, qprev, qtil, z, u, dq, g [S][12];
+//   rho, kw [S]; diag Hessian block [S][144] (T = assembly type).
+//   per slot vertex: x, x1 [SV][3] (positions at q and at the swept end).
+//   pair lists: level-1 slot pairs [L1][2], candidates / active / line-search
+//   pair records (PairRec, 32 B), off-diagonal blocks [L1][144] (T).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/abd.h"
+
+namespace abd {
+
+constexpr int kMaxPlanes = 8;
+constexpr int kMaxParts = 64;
+constexpr int kLS = 4;  // trial step sizes evaluated per line-search pass
+
+struct Planes {
+    int n;
+    int axis[kMaxPlanes];
+    double sign[kMaxPlanes], offset[kMaxPlanes];
+};
+
+// A PT or EE primitive pair between two slots.  v = slot-vertex ids (PT: point,
+// t0, t1, t2; EE: a0, a1, b0, b1); l1 = index of its level-1 slot pair;
+// flags bit 0 = edge-edge; eps = mollifier threshold (EE).
+struct PairRec {
+    int v[4];
+    int l1;
+    int flags;
+    double eps;
+};
+
+// Growable device buffer.
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+bool dbuf_ensure(DBuf &b, size_t bytes);  // keeps no contents
+void dbuf_free(DBuf &b);
+
+template <class X> inline X *P(const DBuf &b) { return (X *)b.p; }
+
+// Persistent device copy of a scene.
+struct SceneDev {
+    int nb = 0;
+    int64_t V = 0, T = 0, E = 0;
+    DBuf q, v, mass, S, vol, kappa, kind, voff, nv, toff, nt, eoff, ne, xbar, tri, edge, erest2;
+};
+
+// Per-step workspace of the consensus solve.
+struct World {
+    int NP = 0, S_dyn = 0, S_all = 0, nsh = 0, R = 0;
+    int64_t SV = 0;
+    DBuf slot_body, slot_part, slot_voff, slot_mask, slot_rep, slot_kw, sv_slot;
+    DBuf q, qprev, qtil, z, u, rho, dq, g;
+    DBuf x, x1, dx, box, box1;
+    DBuf rep_off, rep_slot, zb, rho0, rhob, rb, sb, body_rep, body_slot;
+    DBuf l1, cand, act, ls, diag, off, offflag, pinv;
+    DBuf pcg_r, pcg_z, pcg_p, pcg_ap, pcg_sc;
+    DBuf part;   // per-partition scalars (PartState)
+    DBuf ctr;    // counters
+    DBuf bar;    // grid barrier words
+    DBuf aabb;   // body AABBs at the step start
+    int64_t cap_l1 = 0, cap_cand = 0, cap_act = 0, cap_ls = 0;
+    // host mirrors
+    std::vector<int> h_slot_body, h_slot_part;
+    std::vector<int64_t> h_slot_voff;
+    std::vector<uint64_t> h_slot_mask;
+    std::vector<int> h_rep_off, h_rep_slot, h_body_rep, h_body_slot;
+};
+
+// Per-partition scalars, device resident.
+struct PartState {
+    int active;        // local solve still running
+    int newton_it;
+    unsigned long long dqmax;   // ordered-double max |dq|
+    unsigned long long toi;     // ordered-double min TOI
+    double alpha;
+    double E[kLS + 1];          // E(q) and E(q + alpha_j dq)
+    double rz, rz_new, r0, rr, pap;
+    int pcg_done, pcg_it;
+};
+
+struct Counters {
+    unsigned long long l1, cand, act, ls;
+    unsigned long long rinf, sinf, dinf;  // ordered doubles
+    int overflow;
+    int timeout;
+    unsigned long long pcg_total;
+};
+
+struct KStat {
+    std::string name;
+    int64_t launches = 0;
+    double ms = 0.0, bytes = 0.0;
+};
+
+}  // namespace abd
+
+struct abd_scene {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    // host copy of constants
+    int nb = 0;
+    int64_t V = 0, T = 0, E = 0;
+    std::vector<int> kind, voff, nv, toff, nt, eoff, ne;
+    std::vector<double> mass, S, vol, kappa, com, xbar, erest2;
+    std::vector<int> tri, edge;
+    abd::Planes planes{};
+    double g[3] = {0, 0, 0};
+    // partition
+    int axis = 0, n_slabs = 1;
+    std::vector<double> slab_planes;
+    double alpha_w = 2.0, w_min = 0.0;
+    // device
+    abd::SceneDev dev;
+    abd::World w;
+    // pinned host staging
+    void *pinned = nullptr;
+    size_t pinned_bytes = 0;
+    // profiling
+    bool prof = false;
+    std::vector<abd::KStat> kstats;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+};
+
+namespace abd {
+
+// ---- launchers (abd_broad.cu) ----
+int launch_transform(abd_scene *s, const double *q_slots, double *x, const double *qalt, int use_alt_shared);
+int launch_boxes(abd_scene *s, const double *x0, const double *x1, double half, double *box);
+int launch_l1(abd_scene *s, const double *box, int64_t *count);
+// mode 0: candidates as (type, gid_i, gid_j) triples into out3; mode 1: PairRec into recs
+int launch_l2(abd_scene *s, int mode, const double *x0, const double *x1, double half, int64_t n_l1, int32_t *out3,
+              int64_t cap, int64_t *count);
+// ---- (abd_assemble.cu) ----
+int launch_narrow(abd_scene *s, int64_t n_cand, double dhat, int64_t *n_act);
+int launch_assemble(abd_scene *s, int precision, const abd_step_params *p, double kB, int64_t n_act, int64_t n_l1);
+int launch_ccd(abd_scene *s, int64_t n_sw, const abd_step_params *p, double dhat, int64_t *n_ls, bool want_ls);
+int launch_energy(abd_scene *s, const abd_step_params *p, double kB, int64_t n_ls, const double *alphas_dev);
+// ---- (abd_solve.cu) ----
+int launch_pcg(abd_scene *s, int precision, const abd_step_params *p, int64_t n_l1, int64_t *iters);
+
+// profiling helpers (abd_scene.cu)
+void prof_begin(abd_scene *s, const char *name, double bytes, cudaEvent_t *a, cudaEvent_t *b);
+void prof_end(abd_scene *s, cudaEvent_t a, cudaEvent_t b, int idx);
+void prof_flush(abd_scene *s);
+int prof_index(abd_scene *s, const char *name);
+
+int set_err(abd_scene *s, int code, const std::string &msg);
+int cuda_check(abd_scene *s, cudaError_t e, const char *what);
+
+inline int grid_for(int64_t n, int block, int maxb = 152 * 32) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > maxb) g = maxb;
+    return (int)g;
+}
+
+}  // namespace abd

@@ -1,0 +1,1029 @@
+// abd_solve.cu -- one time step of distributed ABD on one GPU.
+//
+// Host driver of Alg. 1 with every partition's local solve batched into the
+// same launches: partition membership (Sec. 4), slot tables, projected Newton
+// on Eq. 5 (block-Jacobi PCG, CCD-filtered backtracking), consensus (Eq. 6),
+// dual update (Eq. 7), stopping metrics (Eq. 8-10), the CCD merge check
+// (Sec. 4.2) and the rho adaptation (Sec. 4.3).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "abd_device.cuh"
+#include "abd_internal.h"
+
+namespace abd {
+
+void prof_flush(abd_scene *s);
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+
+// One warp per body: AABB of its vertices at the persistent state q.
+__global__ void k_body_aabb(int nb, const int *__restrict__ voff, const double *__restrict__ xbar,
+                            const double *__restrict__ q, double *__restrict__ out) {
+    int lane = threadIdx.x & 31;
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += (gridDim.x * blockDim.x) >> 5) {
+        const double *qb = q + 12 * (int64_t)b;
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int v = voff[b] + lane; v < voff[b + 1]; v += 32) {
+            const double *xb = xbar + 3 * (int64_t)v;
+            for (int k = 0; k < 3; ++k) {
+                double x = qb[k] + (qb[3 + 3 * k] * xb[0] + qb[4 + 3 * k] * xb[1] + qb[5 + 3 * k] * xb[2]);
+                lo[k] = fmin(lo[k], x);
+                hi[k] = fmax(hi[k], x);
+            }
+        }
+        for (int o = 16; o; o >>= 1)
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = fmin(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+                hi[k] = fmax(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+            }
+        if (lane < 3) out[6 * (int64_t)b + lane] = lo[lane];
+        else if (lane < 6) out[6 * (int64_t)b + lane] = hi[lane - 3];
+    }
+}
+
+__global__ void k_fill_sv_slot(int S, const int64_t *__restrict__ slot_voff, int *__restrict__ sv_slot) {
+    for (int s = blockIdx.x; s < S; s += gridDim.x)
+        for (int64_t v = slot_voff[s] + threadIdx.x; v < slot_voff[s + 1]; v += blockDim.x) sv_slot[v] = s;
+}
+
+// q^t, q~ (gravity only, Sec. 3), z = q~, u = 0, rho = beta m per slot.
+__global__ void k_slot_init(int S_all, int S_dyn, const int *__restrict__ slot_body, const int *__restrict__ slot_rep,
+                            const double *__restrict__ qb, const double *__restrict__ vb, const double *__restrict__ mass,
+                            double h, double gx, double gy, double gz, double beta, double *__restrict__ q,
+                            double *__restrict__ qtil, double *__restrict__ z, double *__restrict__ u,
+                            double *__restrict__ rho) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S_all; s += gridDim.x * blockDim.x) {
+        int b = slot_body[s];
+        for (int i = 0; i < 12; ++i) q[12 * (int64_t)s + i] = qb[12 * (int64_t)b + i];
+        if (s >= S_dyn) continue;
+        double gg[3] = {gx, gy, gz};
+        for (int i = 0; i < 12; ++i) {
+            double t = qb[12 * (int64_t)b + i] + h * vb[12 * (int64_t)b + i];
+            if (i < 3) t += h * h * gg[i];
+            qtil[12 * (int64_t)s + i] = t;
+            z[12 * (int64_t)s + i] = t;
+            u[12 * (int64_t)s + i] = 0.0;
+        }
+        rho[s] = beta * mass[b];
+    }
+}
+
+__global__ void k_shared_init(int nsh, const int *__restrict__ rep_off, const int *__restrict__ rep_slot,
+                              const double *__restrict__ qtil, const double *__restrict__ rho, double *__restrict__ zb,
+                              double *__restrict__ rho0, double *__restrict__ rhob) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nsh; j += gridDim.x * blockDim.x) {
+        int s = rep_slot[rep_off[j]];
+        for (int i = 0; i < 12; ++i) zb[12 * (int64_t)j + i] = qtil[12 * (int64_t)s + i];
+        rho0[j] = rhob[j] = rho[s];
+    }
+}
+
+// Inverse of each 12x12 diagonal block by Cholesky (block-Jacobi preconditioner).
+template <class T>
+__global__ void k_pinv(int S_dyn, const int *__restrict__ slot_part, const PartState *__restrict__ part,
+                       const T *__restrict__ diag, T *__restrict__ pinv) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S_dyn; s += gridDim.x * blockDim.x) {
+        if (!part[slot_part[s]].active) continue;
+        T L[144];
+        const T *D = diag + 144 * (int64_t)s;
+        for (int i = 0; i < 144; ++i) L[i] = D[i];
+        bool ok = true;
+        for (int j = 0; j < 12 && ok; ++j) {
+            T d = L[j * 12 + j];
+            for (int k = 0; k < j; ++k) d -= L[j * 12 + k] * L[j * 12 + k];
+            if (!(d > T(0))) { ok = false; break; }
+            T ljj = tsqrt(d);
+            L[j * 12 + j] = ljj;
+            for (int i = j + 1; i < 12; ++i) {
+                T t = L[i * 12 + j];
+                for (int k = 0; k < j; ++k) t -= L[i * 12 + k] * L[j * 12 + k];
+                L[i * 12 + j] = t / ljj;
+            }
+        }
+        T *o = pinv + 144 * (int64_t)s;
+        if (!ok) {  // not expected (block is SPD); fall back to the diagonal
+            for (int i = 0; i < 144; ++i) o[i] = T(0);
+            for (int i = 0; i < 12; ++i) o[i * 12 + i] = D[i * 12 + i] > T(0) ? T(1) / D[i * 12 + i] : T(1);
+            continue;
+        }
+        for (int c = 0; c < 12; ++c) {
+            T y[12];
+            for (int i = 0; i < 12; ++i) {
+                T t = (i == c) ? T(1) : T(0);
+                for (int k = 0; k < i; ++k) t -= L[i * 12 + k] * y[k];
+                y[i] = t / L[i * 12 + i];
+            }
+            for (int i = 11; i >= 0; --i) {
+                T t = y[i];
+                for (int k = i + 1; k < 12; ++k) t -= L[k * 12 + i] * y[k];
+                y[i] = t / L[i * 12 + i];
+            }
+            for (int i = 0; i < 12; ++i) o[i * 12 + c] = y[i];
+        }
+    }
+}
+
+struct PcgPart {
+    double rz[2], pap[2], rr[2], rzn[2];
+    double r0;
+    int done, it;
+};
+
+struct PcgArgs {
+    int S_dyn;
+    const int *slot_part;
+    const PartState *part;
+    const double *g;
+    double *x;
+    const int2 *l1;
+    const int *offflag;
+    int64_t n_l1;
+    PcgPart *pp;
+    int NP;
+    double tol2;
+    int max_it;
+    unsigned *bar;   // [0] count, [1] generation
+    int *timeout;
+};
+
+// Grid barrier with a bounded spin: after ~2^24 polls with back-off the
+// waiting block records a timeout and proceeds, so the kernel always ends.
+__device__ __forceinline__ void grid_barrier(unsigned *bar, unsigned nblocks, int *timeout) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        unsigned my = *gen;
+        __threadfence();
+        unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd((unsigned *)gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*gen == my) {
+                if (++spins > (1ull << 24)) { atomicExch(timeout, 1); break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// Sum v over the warp into acc[p] when all contributing lanes share p.
+__device__ __forceinline__ void warp_add(double *base, int stride, int p, double v) {
+    const unsigned full = 0xffffffffu;
+    int pmax = __reduce_max_sync(full, p);
+    int pmin = __reduce_min_sync(full, p < 0 ? 0x7fffffff : p);
+    if (pmax < 0) return;
+    if (pmin == pmax) {
+        double t = p < 0 ? 0.0 : v;
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(full, t, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(base + (int64_t)stride * pmax, t);
+    } else if (p >= 0) {
+        atomicAdd(base + (int64_t)stride * p, v);
+    }
+}
+
+// r = -g, x = 0, z = Pinv r, p = z; rz, r0 per partition.
+template <class T>
+__global__ void k_pcg_init(PcgArgs A, const T *__restrict__ pinv, T *__restrict__ r, T *__restrict__ z,
+                           T *__restrict__ p) {
+    const int stride = sizeof(PcgPart) / sizeof(double);
+    for (int base = blockIdx.x * blockDim.x; base < A.S_dyn; base += gridDim.x * blockDim.x) {
+        int s = base + threadIdx.x;
+        int pt = -1;
+        double rzv = 0.0, rrv = 0.0;
+        if (s < A.S_dyn) {
+            pt = A.slot_part[s];
+            T rv[12];
+            for (int i = 0; i < 12; ++i) {
+                double gi = A.part[pt].active ? -A.g[12 * (int64_t)s + i] : 0.0;
+                rv[i] = T(gi);
+                A.x[12 * (int64_t)s + i] = 0.0;
+                r[12 * (int64_t)s + i] = rv[i];
+            }
+            const T *M = pinv + 144 * (int64_t)s;
+            for (int i = 0; i < 12; ++i) {
+                T t = T(0);
+                if (A.part[pt].active)
+                    for (int j = 0; j < 12; ++j) t += M[i * 12 + j] * rv[j];
+                z[12 * (int64_t)s + i] = t;
+                p[12 * (int64_t)s + i] = t;
+                rzv += (double)rv[i] * (double)t;
+                rrv += (double)rv[i] * (double)rv[i];
+            }
+            if (!A.part[pt].active) pt = -1;
+        }
+        warp_add(&A.pp[0].rz[0], stride, pt, rzv);
+        warp_add(&A.pp[0].r0, stride, pt, rrv);
+    }
+}
+
+template <class T>
+__global__ void k_pcg_loop(PcgArgs A, const T *__restrict__ diag, const T *__restrict__ off, const T *__restrict__ pinv,
+                           T *__restrict__ r, T *__restrict__ z, T *__restrict__ p, T *__restrict__ Ap) {
+    const int stride = sizeof(PcgPart) / sizeof(double);
+    const unsigned nblocks = gridDim.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    for (int it = 0; it < A.max_it; ++it) {
+        int c = it & 1;
+        // exit when every partition is done (all blocks read the same flags)
+        bool all_done = true;
+        for (int q = 0; q < A.NP; ++q) all_done &= A.pp[q].done != 0;
+        if (all_done) break;
+        // A: Ap = D p; zero the other parity's accumulators
+        if (blockIdx.x == 0)
+            for (int q = threadIdx.x; q < A.NP; q += blockDim.x) {
+                A.pp[q].pap[c ^ 1] = 0.0; A.pp[q].rr[c ^ 1] = 0.0; A.pp[q].rzn[c ^ 1] = 0.0;
+            }
+        for (int64_t e = tid; e < 12 * (int64_t)A.S_dyn; e += nth) {
+            int s = (int)(e / 12), i = (int)(e % 12);
+            if (A.pp[A.slot_part[s]].done) continue;
+            const T *D = diag + 144 * (int64_t)s + 12 * i;
+            const T *ps = p + 12 * (int64_t)s;
+            T acc = T(0);
+            for (int j = 0; j < 12; ++j) acc += D[j] * ps[j];
+            Ap[e] = acc;
+        }
+        grid_barrier(A.bar, nblocks, A.timeout);
+        // B: off-diagonal blocks (rows of a, cols of b), both directions
+        for (int64_t e = tid; e < 12 * A.n_l1; e += nth) {
+            int64_t k = e / 12;
+            int i = (int)(e % 12);
+            if (!A.offflag[k]) continue;
+            int2 lp = A.l1[k];
+            if (A.pp[A.slot_part[lp.x]].done) continue;
+            const T *B = off + 144 * k;
+            const T *pb = p + 12 * (int64_t)lp.y, *pa = p + 12 * (int64_t)lp.x;
+            T row = T(0), col = T(0);
+            for (int j = 0; j < 12; ++j) {
+                row += B[i * 12 + j] * pb[j];
+                col += B[j * 12 + i] * pa[j];
+            }
+            atomicAdd(Ap + 12 * (int64_t)lp.x + i, row);
+            atomicAdd(Ap + 12 * (int64_t)lp.y + i, col);
+        }
+        grid_barrier(A.bar, nblocks, A.timeout);
+        // C: p . Ap per partition
+        for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < 12 * (int64_t)A.S_dyn; base += nth) {
+            int64_t e = base + threadIdx.x;
+            int pt = -1;
+            double v = 0.0;
+            if (e < 12 * (int64_t)A.S_dyn) {
+                pt = A.slot_part[e / 12];
+                if (A.pp[pt].done) pt = -1;
+                else v = (double)p[e] * (double)Ap[e];
+            }
+            warp_add(&A.pp[0].pap[c], stride, pt, v);
+        }
+        grid_barrier(A.bar, nblocks, A.timeout);
+        // D: x += alpha p, r -= alpha Ap, z = Pinv r; rr, rz accumulators
+        for (int base = blockIdx.x * blockDim.x; base < A.S_dyn; base += nth) {
+            int s = base + threadIdx.x;
+            int pt = -1;
+            double rrv = 0.0, rzv = 0.0;
+            if (s < A.S_dyn) {
+                pt = A.slot_part[s];
+                if (A.pp[pt].done) pt = -1;
+            }
+            if (pt >= 0) {
+                double alpha = A.pp[pt].rz[c] / A.pp[pt].pap[c];
+                T rv[12];
+                for (int i = 0; i < 12; ++i) {
+                    int64_t e = 12 * (int64_t)s + i;
+                    A.x[e] += alpha * (double)p[e];
+                    rv[i] = T((double)r[e] - alpha * (double)Ap[e]);
+                    r[e] = rv[i];
+                    rrv += (double)rv[i] * (double)rv[i];
+                }
+                const T *M = pinv + 144 * (int64_t)s;
+                for (int i = 0; i < 12; ++i) {
+                    T t = T(0);
+                    for (int j = 0; j < 12; ++j) t += M[i * 12 + j] * rv[j];
+                    z[12 * (int64_t)s + i] = t;
+                    rzv += (double)rv[i] * (double)t;
+                }
+            }
+            warp_add(&A.pp[0].rr[c], stride, pt, rrv);
+            warp_add(&A.pp[0].rzn[c], stride, pt, rzv);
+        }
+        grid_barrier(A.bar, nblocks, A.timeout);
+        // E: convergence, beta, p = z + beta p
+        for (int64_t e = tid; e < 12 * (int64_t)A.S_dyn; e += nth) {
+            int pt = A.slot_part[e / 12];
+            if (A.pp[pt].done) continue;
+            if (A.pp[pt].rr[c] <= A.tol2 * A.pp[pt].r0) continue;
+            double beta = A.pp[pt].rzn[c] / A.pp[pt].rz[c];
+            p[e] = T((double)z[e] + beta * (double)p[e]);
+        }
+        if (blockIdx.x == 0)
+            for (int q = threadIdx.x; q < A.NP; q += blockDim.x) {
+                if (A.pp[q].done) continue;
+                A.pp[q].it = it + 1;
+                if (A.pp[q].rr[c] <= A.tol2 * A.pp[q].r0) A.pp[q].done = 1;
+                else A.pp[q].rz[c ^ 1] = A.pp[q].rzn[c];
+            }
+        grid_barrier(A.bar, nblocks, A.timeout);
+    }
+}
+
+__global__ void k_pcg_parts_init(PcgPart *pp, const PartState *part, int NP) {
+    for (int q = threadIdx.x; q < NP; q += blockDim.x) {
+        PcgPart z = {};
+        z.done = part[q].active ? 0 : 1;
+        pp[q] = z;
+    }
+}
+
+__global__ void k_pcg_parts_check(PcgPart *pp, int NP) {
+    for (int q = threadIdx.x; q < NP; q += blockDim.x)
+        if (!pp[q].done && !(pp[q].r0 > 0.0)) pp[q].done = 1;
+}
+
+// max |dq| per partition (ordered-double atomics).
+__global__ void k_dqmax(int S_dyn, const int *__restrict__ slot_part, const double *__restrict__ dq,
+                        PartState *__restrict__ part) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S_dyn; s += gridDim.x * blockDim.x) {
+        int p = slot_part[s];
+        if (!part[p].active) continue;
+        double m = 0.0;
+        for (int i = 0; i < 12; ++i) m = fmax(m, fabs(dq[12 * (int64_t)s + i]));
+        atomicMax(&part[p].dqmax, ord(m));
+    }
+}
+
+// Line search bookkeeping: trial steps alpha_j = toi 2^-(nh0 + j - 1).
+__global__ void k_ls_alphas(int NP, PartState *part, const int *nh0, double *alphas, int max_halv) {
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+        for (int j = 0; j <= kLS; ++j) part[p].E[j] = 0.0;
+        double toi = unord(part[p].toi);
+        alphas[(kLS + 1) * p] = 0.0;
+        for (int j = 1; j <= kLS; ++j) {
+            int nh = nh0[p] + j - 1;
+            alphas[(kLS + 1) * p + j] = nh <= max_halv ? ldexp(toi < 1.0 ? toi : 1.0, -nh) : -1.0;
+        }
+    }
+}
+
+// Accept the first trial with E <= E(q); after max_halv halvings accept the
+// last trial.  decided[p] = 1 when settled; nh0 advances otherwise.
+__global__ void k_ls_select(int NP, PartState *part, int *nh0, int *decided, const double *alphas, int max_halv,
+                            int *pending) {
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+        if (!part[p].active || decided[p]) continue;
+        double E0 = part[p].E[0];
+        int pick = -1;
+        for (int j = 1; j <= kLS; ++j) {
+            if (alphas[(kLS + 1) * p + j] < 0.0) break;
+            if (part[p].E[j] <= E0) { pick = j; break; }
+            if (nh0[p] + j - 1 == max_halv) { pick = j; break; }
+        }
+        if (pick > 0) {
+            part[p].alpha = alphas[(kLS + 1) * p + pick];
+            decided[p] = 1;
+        } else {
+            nh0[p] += kLS;
+            atomicAdd(pending, 1);
+        }
+    }
+}
+
+__global__ void k_update_q(int S_dyn, const int *__restrict__ slot_part, const PartState *__restrict__ part,
+                           const double *__restrict__ dq, double *__restrict__ q) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 12 * (int64_t)S_dyn;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int p = slot_part[e / 12];
+        if (!part[p].active) continue;
+        q[e] += part[p].alpha * dq[e];
+    }
+}
+
+// Consensus (Eq. 6), dual update (Eq. 7), per-body residuals (Eq. 9-10).
+__global__ void k_consensus(int nsh, const int *__restrict__ rep_off, const int *__restrict__ rep_slot,
+                            const double *__restrict__ q, double *__restrict__ u, const double *__restrict__ rho,
+                            double *__restrict__ zb, double *__restrict__ rb, double *__restrict__ sb,
+                            Counters *__restrict__ c) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nsh; j += gridDim.x * blockDim.x) {
+        double num[12], den = 0.0;
+        for (int i = 0; i < 12; ++i) num[i] = 0.0;
+        for (int k = rep_off[j]; k < rep_off[j + 1]; ++k) {
+            int s = rep_slot[k];
+            for (int i = 0; i < 12; ++i) num[i] += rho[s] * (q[12 * (int64_t)s + i] + u[12 * (int64_t)s + i]);
+            den += rho[s];
+        }
+        double sv = 0.0, rv = 0.0, zn[12];
+        for (int i = 0; i < 12; ++i) {
+            zn[i] = num[i] / den;
+            sv = fmax(sv, fabs(zn[i] - zb[12 * (int64_t)j + i]));
+            zb[12 * (int64_t)j + i] = zn[i];
+        }
+        for (int k = rep_off[j]; k < rep_off[j + 1]; ++k) {
+            int s = rep_slot[k];
+            for (int i = 0; i < 12; ++i) {
+                double ri = q[12 * (int64_t)s + i] - zn[i];
+                u[12 * (int64_t)s + i] += ri;
+                rv = fmax(rv, fabs(ri));
+            }
+        }
+        rb[j] = rv;
+        sb[j] = sv;
+        atomicMax(&c->rinf, ord(rv));
+        atomicMax(&c->sinf, ord(sv));
+    }
+}
+
+__global__ void k_delta(int S_dyn, const double *__restrict__ q, const double *__restrict__ qprev, Counters *c) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 12 * (int64_t)S_dyn;
+         e += (int64_t)gridDim.x * blockDim.x)
+        atomicMax(&c->dinf, ord(fabs(q[e] - qprev[e])));
+}
+
+// Per-slot copy of z for the local solves and the merge-check targets.
+__global__ void k_scatter_z(int S_dyn, const int *__restrict__ slot_rep, const double *__restrict__ zb,
+                            double *__restrict__ z) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 12 * (int64_t)S_dyn;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int j = slot_rep[e / 12];
+        if (j >= 0) z[e] = zb[12 * (int64_t)j + e % 12];
+    }
+}
+
+// Residual-driven rho (Sec. 4.3) with clamp and scaled-dual rescale.
+__global__ void k_rho_update(int nsh, const int *__restrict__ rep_off, const int *__restrict__ rep_slot,
+                             const double *__restrict__ rb, const double *__restrict__ sb,
+                             const double *__restrict__ rho0, double *__restrict__ rhob, double *__restrict__ rho,
+                             double *__restrict__ u, double tau, double mu, double smin, double smax) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nsh; j += gridDim.x * blockDim.x) {
+        double old = rhob[j], nw = old;
+        if (rb[j] > mu * sb[j]) nw = old * tau;
+        else if (sb[j] > mu * rb[j]) nw = old / tau;
+        nw = fmin(fmax(nw, smin * rho0[j]), smax * rho0[j]);
+        rhob[j] = nw;
+        for (int k = rep_off[j]; k < rep_off[j + 1]; ++k) {
+            int s = rep_slot[k];
+            for (int i = 0; i < 12; ++i) u[12 * (int64_t)s + i] *= old / nw;
+            rho[s] = nw;
+        }
+    }
+}
+
+// Merge (Alg. 1 end of frame) and velocity update.
+__global__ void k_merge(int nb, const int *__restrict__ kind, const int *__restrict__ body_rep,
+                        const int *__restrict__ body_slot, const double *__restrict__ zb, const double *__restrict__ q,
+                        double h, double *__restrict__ qbody, double *__restrict__ vbody) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        if (kind[b] != ABD_DYNAMIC || (body_rep[b] < 0 && body_slot[b] < 0)) continue;
+        const double *src = body_rep[b] >= 0 ? zb + 12 * (int64_t)body_rep[b] : q + 12 * (int64_t)body_slot[b];
+        for (int i = 0; i < 12; ++i) {
+            double qn = src[i];
+            vbody[12 * (int64_t)b + i] = (qn - qbody[12 * (int64_t)b + i]) / h;
+            qbody[12 * (int64_t)b + i] = qn;
+        }
+    }
+}
+
+}  // namespace abd
+
+using namespace abd;
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Ctx {
+    abd_scene *s;
+    const abd_step_params *p;
+    double kB, l, half;
+    abd_step_stats *st;
+    int precision;
+    DBuf alphas, nh0, decided, pending;
+    double t_coll = 0, t_solve = 0, t_sync = 0;
+};
+
+double u2d(unsigned long long u) {
+    double d;
+    memcpy(&d, &u, sizeof d);
+    return d;
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+template <class X> int h2d(abd_scene *s, DBuf &b, const std::vector<X> &v) {
+    if (!dbuf_ensure(b, sizeof(X) * (v.size() ? v.size() : 1))) return set_err(s, ABD_E_OOM, "upload");
+    if (v.empty()) return ABD_OK;
+    return cuda_check(s, cudaMemcpyAsync(b.p, v.data(), sizeof(X) * v.size(), cudaMemcpyHostToDevice, s->stream),
+                      "upload");
+}
+
+int sync(abd_scene *s) { return cuda_check(s, cudaStreamSynchronize(s->stream), "sync"); }
+
+// Body AABBs at the persistent state (device) -> host.
+int body_aabbs(abd_scene *s, std::vector<double> &box) {
+    DBuf &tmp = s->w.aabb;
+    if (!dbuf_ensure(tmp, 48 * (size_t)s->nb)) return set_err(s, ABD_E_OOM, "aabb");
+    k_body_aabb<<<grid_for((int64_t)s->nb * 32, 256), 256, 0, s->stream>>>(s->nb, P<int>(s->dev.voff),
+                                                                          P<double>(s->dev.xbar),
+                                                                          P<double>(s->dev.q), P<double>(tmp));
+    box.resize(6 * (size_t)s->nb);
+    int rc = cuda_check(s, cudaMemcpyAsync(box.data(), tmp.p, 48 * (size_t)s->nb, cudaMemcpyDeviceToHost, s->stream),
+                        "aabb");
+    return rc ? rc : sync(s);
+}
+
+// Slab membership (Sec. 4): w = max(alpha v_max h, w_min); body b on slab i iff
+// its AABB along the axis meets [gamma_i - w/2, gamma_{i+1} + w/2].
+int compute_masks(abd_scene *s, double h, const std::vector<double> &box, const std::vector<double> &v,
+                  std::vector<uint64_t> &mask, double &w_out) {
+    int N = s->n_slabs, ax = s->axis;
+    mask.assign(s->nb, 0);
+    if (N <= 1) {
+        for (int b = 0; b < s->nb; ++b) mask[b] = s->kind[b] == ABD_DYNAMIC ? 1 : 0;
+        w_out = 0.0;
+        return ABD_OK;
+    }
+    double Lo = INFINITY, Hi = -INFINITY, vmax = 0.0, wmin = INFINITY;
+    for (int b = 0; b < s->nb; ++b) {
+        if (s->kind[b] != ABD_DYNAMIC) continue;
+        const double *bx = &box[6 * (size_t)b];
+        Lo = std::min(Lo, bx[ax]);
+        Hi = std::max(Hi, bx[3 + ax]);
+        double dx = bx[3] - bx[0], dy = bx[4] - bx[1], dz = bx[5] - bx[2];
+        wmin = std::min(wmin, std::sqrt(dx * dx + dy * dy + dz * dz));
+        const double *vb = &v[12 * (size_t)b];
+        vmax = std::max(vmax, std::sqrt(vb[0] * vb[0] + vb[1] * vb[1] + vb[2] * vb[2]));
+    }
+    std::vector<double> gam(N + 1);
+    for (int i = 1; i < N; ++i)
+        gam[i] = s->slab_planes.size() == (size_t)(N - 1) ? s->slab_planes[i - 1] : Lo + (Hi - Lo) * (double)i / (double)N;
+    if (s->w_min > 0.0) wmin = s->w_min;
+    double w = std::max(s->alpha_w * vmax * h, wmin);
+    for (int b = 0; b < s->nb; ++b) {
+        if (s->kind[b] != ABD_DYNAMIC) continue;
+        double lo = box[6 * (size_t)b + ax], hi = box[6 * (size_t)b + 3 + ax];
+        for (int i = 0; i < N; ++i) {
+            double rlo = i == 0 ? -INFINITY : gam[i] - 0.5 * w;
+            double rhi = i == N - 1 ? INFINITY : gam[i + 1] + 0.5 * w;
+            if (lo <= rhi && hi >= rlo) mask[b] |= (uint64_t)1 << i;
+        }
+    }
+    w_out = w;
+    return ABD_OK;
+}
+
+// Build the slot tables of one step from the body masks (nparts partitions).
+int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
+    World &w = s->w;
+    w.NP = nparts;
+    w.h_slot_body.clear(); w.h_slot_part.clear(); w.h_slot_mask.clear();
+    std::vector<int> slot_rep;
+    std::vector<double> slot_kw;
+    w.h_body_rep.assign(s->nb, -1);
+    w.h_body_slot.assign(s->nb, -1);
+    int nsh = 0;
+    for (int b = 0; b < s->nb; ++b)
+        if (s->kind[b] == ABD_DYNAMIC && __builtin_popcountll(mask[b]) >= 2) w.h_body_rep[b] = nsh++;
+    std::vector<std::vector<int>> reps(nsh);
+    for (int p = 0; p < nparts; ++p)
+        for (int b = 0; b < s->nb; ++b) {
+            if (s->kind[b] != ABD_DYNAMIC || !((mask[b] >> p) & 1)) continue;
+            int sl = (int)w.h_slot_body.size();
+            w.h_slot_body.push_back(b);
+            w.h_slot_part.push_back(p);
+            w.h_slot_mask.push_back(mask[b]);
+            slot_rep.push_back(w.h_body_rep[b]);
+            slot_kw.push_back(1.0 / (double)__builtin_popcountll(mask[b]));
+            if (w.h_body_slot[b] < 0) w.h_body_slot[b] = sl;
+            if (w.h_body_rep[b] >= 0) reps[w.h_body_rep[b]].push_back(sl);
+        }
+    w.S_dyn = (int)w.h_slot_body.size();
+    for (int b = 0; b < s->nb; ++b)
+        if (s->kind[b] != ABD_DYNAMIC) {
+            w.h_slot_body.push_back(b);
+            w.h_slot_part.push_back(-1);
+            w.h_slot_mask.push_back(0);
+        }
+    w.S_all = (int)w.h_slot_body.size();
+    w.h_slot_voff.assign(w.S_all + 1, 0);
+    for (int i = 0; i < w.S_all; ++i) w.h_slot_voff[i + 1] = w.h_slot_voff[i] + s->nv[w.h_slot_body[i]];
+    w.SV = w.h_slot_voff[w.S_all];
+    w.nsh = nsh;
+    w.h_rep_off.assign(nsh + 1, 0);
+    w.h_rep_slot.clear();
+    for (int j = 0; j < nsh; ++j) {
+        w.h_rep_off[j + 1] = w.h_rep_off[j] + (int)reps[j].size();
+        for (int sl : reps[j]) w.h_rep_slot.push_back(sl);
+    }
+    w.R = (int)w.h_rep_slot.size();
+    int rc;
+    if ((rc = h2d(s, w.slot_body, w.h_slot_body)) || (rc = h2d(s, w.slot_part, w.h_slot_part)) ||
+        (rc = h2d(s, w.slot_voff, w.h_slot_voff)) || (rc = h2d(s, w.slot_mask, w.h_slot_mask)) ||
+        (rc = h2d(s, w.slot_rep, slot_rep)) || (rc = h2d(s, w.slot_kw, slot_kw)) ||
+        (rc = h2d(s, w.rep_off, w.h_rep_off)) || (rc = h2d(s, w.rep_slot, w.h_rep_slot)) ||
+        (rc = h2d(s, w.body_rep, w.h_body_rep)) || (rc = h2d(s, w.body_slot, w.h_body_slot)))
+        return rc;
+    size_t S = (size_t)(w.S_all ? w.S_all : 1), Sd = (size_t)(w.S_dyn ? w.S_dyn : 1);
+    size_t SV = (size_t)(w.SV ? w.SV : 1), NS = (size_t)(nsh ? nsh : 1);
+    bool ok = dbuf_ensure(w.sv_slot, 4 * SV) && dbuf_ensure(w.q, 96 * S) && dbuf_ensure(w.qprev, 96 * Sd) &&
+              dbuf_ensure(w.qtil, 96 * Sd) && dbuf_ensure(w.z, 96 * Sd) && dbuf_ensure(w.u, 96 * Sd) &&
+              dbuf_ensure(w.rho, 8 * Sd) && dbuf_ensure(w.dq, 96 * Sd) && dbuf_ensure(w.g, 96 * Sd) &&
+              dbuf_ensure(w.x, 24 * SV) && dbuf_ensure(w.x1, 24 * SV) && dbuf_ensure(w.box, 48 * S) &&
+              dbuf_ensure(w.box1, 48 * S) && dbuf_ensure(w.zb, 96 * NS) && dbuf_ensure(w.rho0, 8 * NS) &&
+              dbuf_ensure(w.rhob, 8 * NS) && dbuf_ensure(w.rb, 8 * NS) && dbuf_ensure(w.sb, 8 * NS) &&
+              dbuf_ensure(w.part, sizeof(PartState) * kMaxParts) && dbuf_ensure(w.ctr, sizeof(Counters)) &&
+              dbuf_ensure(w.bar, 64) && dbuf_ensure(w.pcg_sc, sizeof(PcgPart) * kMaxParts) &&
+              dbuf_ensure(w.pinv, 8 * 144 * Sd) && dbuf_ensure(w.pcg_r, 96 * Sd) && dbuf_ensure(w.pcg_z, 96 * Sd) &&
+              dbuf_ensure(w.pcg_p, 96 * Sd) && dbuf_ensure(w.pcg_ap, 96 * Sd);
+    if (!ok) return set_err(s, ABD_E_OOM, "world buffers");
+    if (w.S_all > 0) k_fill_sv_slot<<<std::min(w.S_all, 152 * 8), 256, 0, s->stream>>>(w.S_all, P<int64_t>(w.slot_voff), P<int>(w.sv_slot));
+    return cuda_check(s, cudaGetLastError(), "build world");
+}
+
+int read_parts(abd_scene *s, std::vector<PartState> &ps) {
+    ps.resize(s->w.NP);
+    int rc = cuda_check(s, cudaMemcpyAsync(ps.data(), s->w.part.p, sizeof(PartState) * s->w.NP,
+                                           cudaMemcpyDeviceToHost, s->stream), "read parts");
+    return rc ? rc : sync(s);
+}
+
+int write_parts(abd_scene *s, const std::vector<PartState> &ps) {
+    return cuda_check(s, cudaMemcpyAsync(s->w.part.p, ps.data(), sizeof(PartState) * s->w.NP, cudaMemcpyHostToDevice,
+                                         s->stream), "write parts");
+}
+
+template <class T>
+int pcg_T(Ctx &C, int64_t n_l1, int64_t *iters) {
+    abd_scene *s = C.s;
+    World &w = s->w;
+    PcgArgs A;
+    A.S_dyn = w.S_dyn; A.slot_part = P<int>(w.slot_part); A.part = P<PartState>(w.part); A.g = P<double>(w.g);
+    A.x = P<double>(w.dq); A.l1 = P<int2>(w.l1); A.offflag = P<int>(w.offflag); A.n_l1 = n_l1;
+    A.pp = P<PcgPart>(w.pcg_sc); A.NP = w.NP; A.tol2 = C.p->pcg_rtol * C.p->pcg_rtol; A.max_it = C.p->pcg_max;
+    A.bar = P<unsigned>(w.bar);
+    A.timeout = &P<Counters>(w.ctr)->timeout;
+    k_pinv<T><<<grid_for(w.S_dyn, 64), 64, 0, s->stream>>>(w.S_dyn, P<int>(w.slot_part), P<PartState>(w.part),
+                                                          P<T>(w.diag), P<T>(w.pinv));
+    k_pcg_parts_init<<<1, 64, 0, s->stream>>>(A.pp, A.part, w.NP);
+    k_pcg_init<T><<<grid_for(w.S_dyn, 128), 128, 0, s->stream>>>(A, P<T>(w.pinv), P<T>(w.pcg_r), P<T>(w.pcg_z),
+                                                                P<T>(w.pcg_p));
+    k_pcg_parts_check<<<1, 64, 0, s->stream>>>(A.pp, w.NP);
+    cudaMemsetAsync(w.bar.p, 0, 64, s->stream);
+    static int maxb = -1;
+    if (maxb < 0) {
+        int dev, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_loop<T>, 256, 0);
+        maxb = std::max(1, sms * std::max(1, std::min(per, 2)));
+    }
+    int64_t work = std::max<int64_t>(12 * (int64_t)w.S_dyn, 12 * n_l1);
+    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(maxb, (work + 255) / 256));
+    const T *diag = P<T>(w.diag), *off = P<T>(w.off), *pinv = P<T>(w.pinv);
+    T *r = P<T>(w.pcg_r), *z = P<T>(w.pcg_z), *pp = P<T>(w.pcg_p), *ap = P<T>(w.pcg_ap);
+    void *args[] = {&A, &diag, &off, &pinv, &r, &z, &pp, &ap};
+    cudaEvent_t ea, eb;
+    prof_begin(s, "pcg", 0, &ea, &eb);
+    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_pcg_loop<T>, blocks, 256, args, 0, s->stream);
+    prof_end(s, ea, eb, prof_index(s, "pcg"));
+    int rc = cuda_check(s, e, "pcg launch");
+    if (rc) return rc;
+    std::vector<PcgPart> h(w.NP);
+    rc = cuda_check(s, cudaMemcpyAsync(h.data(), A.pp, sizeof(PcgPart) * w.NP, cudaMemcpyDeviceToHost, s->stream), "pcg");
+    if (rc || (rc = sync(s))) return rc;
+    int64_t mx = 0;
+    for (auto &q : h) mx = std::max<int64_t>(mx, q.it);
+    *iters = mx;
+    return ABD_OK;
+}
+
+int check_timeout(abd_scene *s) {
+    int t = 0;
+    cudaMemcpyAsync(&t, &P<Counters>(s->w.ctr)->timeout, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    int rc = sync(s);
+    if (rc) return rc;
+    return t ? set_err(s, ABD_E_DEVICE_TIMEOUT, "grid barrier wait timed out") : ABD_OK;
+}
+
+// Projected Newton on Eq. 5 for every partition whose `run` flag is set.
+int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &maxed) {
+    abd_scene *s = C.s;
+    World &w = s->w;
+    const abd_step_params *p = C.p;
+    std::vector<PartState> ps(w.NP);
+    for (int i = 0; i < w.NP; ++i) {
+        memset(&ps[i], 0, sizeof(PartState));
+        ps[i].active = run[i];
+    }
+    int rc = write_parts(s, ps);
+    if (rc) return rc;
+    if (!dbuf_ensure(C.alphas, 8 * (kLS + 1) * (size_t)w.NP) || !dbuf_ensure(C.nh0, 4 * (size_t)w.NP) ||
+        !dbuf_ensure(C.decided, 4 * (size_t)w.NP) || !dbuf_ensure(C.pending, 4))
+        return set_err(s, ABD_E_OOM, "line search");
+    std::vector<int> active = run;
+    for (int it = 0; it < p->max_newton; ++it) {
+        bool any = false;
+        for (int i = 0; i < w.NP; ++i) any |= active[i] != 0;
+        if (!any) break;
+        double t0 = now_ms();
+        // active set at q
+        if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x), nullptr, 0))) return rc;
+        if ((rc = launch_boxes(s, P<double>(w.x), nullptr, C.half, P<double>(w.box)))) return rc;
+        int64_t n_l1 = 0, n_cand = 0, n_act = 0;
+        if ((rc = launch_l1(s, P<double>(w.box), &n_l1))) return rc;
+        if ((rc = launch_l2(s, 1, P<double>(w.x), nullptr, C.half, n_l1, nullptr, 0, &n_cand))) return rc;
+        if ((rc = launch_narrow(s, n_cand, p->dhat, &n_act))) return rc;
+        C.st->n_candidates_peak = std::max(C.st->n_candidates_peak, n_cand);
+        C.st->n_active_peak = std::max(C.st->n_active_peak, n_act);
+        double t1 = now_ms();
+        C.t_coll += t1 - t0;
+        if ((rc = launch_assemble(s, C.precision, p, C.kB, n_act, n_l1))) return rc;
+        int64_t pit = 0;
+        rc = C.precision == ABD_MIXED ? pcg_T<float>(C, n_l1, &pit) : pcg_T<double>(C, n_l1, &pit);
+        if (rc) return rc;
+        if ((rc = check_timeout(s))) return rc;
+        C.st->pcg_iters += pit;
+        // Newton stopping test, before the line search
+        k_dqmax<<<grid_for(w.S_dyn, 128), 128, 0, s->stream>>>(w.S_dyn, P<int>(w.slot_part), P<double>(w.dq),
+                                                              P<PartState>(w.part));
+        if ((rc = read_parts(s, ps))) return rc;
+        bool cont = false;
+        for (int i = 0; i < w.NP; ++i) {
+            if (!active[i]) continue;
+            ++newton_total;
+            double dm = u2d(ps[i].dqmax);
+            if (dm / (p->h * C.l) < p->newton_tol) {
+                active[i] = 0;
+                ps[i].active = 0;
+            } else {
+                cont = true;
+            }
+            ps[i].toi = 0x3FF0000000000000ull;  // 1.0
+            ps[i].dqmax = 0;
+        }
+        if ((rc = write_parts(s, ps))) return rc;
+        double t2 = now_ms();
+        C.t_solve += t2 - t1;
+        if (!cont) break;
+        // CCD along q -> q + dq
+        if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x1), P<double>(w.dq), 1))) return rc;
+        if ((rc = launch_boxes(s, P<double>(w.x), P<double>(w.x1), C.half, P<double>(w.box1)))) return rc;
+        int64_t n_l1s = 0, n_sw = 0, n_ls = 0;
+        if ((rc = launch_l1(s, P<double>(w.box1), &n_l1s))) return rc;
+        if ((rc = launch_l2(s, 1, P<double>(w.x), P<double>(w.x1), C.half, n_l1s, nullptr, 0, &n_sw))) return rc;
+        if ((rc = launch_ccd(s, n_sw, p, p->dhat, &n_ls, true))) return rc;
+        double t3 = now_ms();
+        C.t_coll += t3 - t2;
+        // backtracking on the FP64 energy, kLS trial steps per pass
+        cudaMemsetAsync(C.nh0.p, 0, 4 * (size_t)w.NP, s->stream);
+        cudaMemsetAsync(C.decided.p, 0, 4 * (size_t)w.NP, s->stream);
+        for (int pass = 0; pass < 64; ++pass) {
+            cudaMemsetAsync(C.pending.p, 0, 4, s->stream);
+            k_ls_alphas<<<1, 64, 0, s->stream>>>(w.NP, P<PartState>(w.part), P<int>(C.nh0), P<double>(C.alphas),
+                                                 p->max_halvings);
+            if ((rc = launch_energy(s, p, C.kB, n_ls, P<double>(C.alphas)))) return rc;
+            k_ls_select<<<1, 64, 0, s->stream>>>(w.NP, P<PartState>(w.part), P<int>(C.nh0), P<int>(C.decided),
+                                                 P<double>(C.alphas), p->max_halvings, P<int>(C.pending));
+            int pend = 0;
+            cudaMemcpyAsync(&pend, C.pending.p, 4, cudaMemcpyDeviceToHost, s->stream);
+            if ((rc = sync(s))) return rc;
+            if (!pend) break;
+        }
+        k_update_q<<<grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream>>>(w.S_dyn, P<int>(w.slot_part),
+                                                                               P<PartState>(w.part), P<double>(w.dq),
+                                                                               P<double>(w.q));
+        if ((rc = cuda_check(s, cudaGetLastError(), "line search"))) return rc;
+        C.t_solve += now_ms() - t3;
+        if (it == p->max_newton - 1) maxed = 1;
+    }
+    return ABD_OK;
+}
+
+// TOI of the merge path q_i -> q^_i for every partition; true when all are 1.
+int merge_check(Ctx &C, bool &ok) {
+    abd_scene *s = C.s;
+    World &w = s->w;
+    std::vector<PartState> ps(w.NP);
+    for (int i = 0; i < w.NP; ++i) {
+        memset(&ps[i], 0, sizeof(PartState));
+        ps[i].active = 1;
+        ps[i].toi = 0x3FF0000000000000ull;
+    }
+    int rc = write_parts(s, ps);
+    if (rc) return rc;
+    if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x), nullptr, 0))) return rc;
+    if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x1), P<double>(w.z), 2))) return rc;
+    if ((rc = launch_boxes(s, P<double>(w.x), P<double>(w.x1), C.half, P<double>(w.box1)))) return rc;
+    int64_t n_l1 = 0, n_sw = 0, n_ls = 0;
+    if ((rc = launch_l1(s, P<double>(w.box1), &n_l1))) return rc;
+    if ((rc = launch_l2(s, 1, P<double>(w.x), P<double>(w.x1), C.half, n_l1, nullptr, 0, &n_sw))) return rc;
+    if ((rc = launch_ccd(s, n_sw, C.p, C.p->dhat, &n_ls, false))) return rc;
+    if ((rc = read_parts(s, ps))) return rc;
+    ok = true;
+    for (auto &q : ps) ok &= q.toi == 0x3FF0000000000000ull;
+    return ABD_OK;
+}
+
+int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool force_mono) {
+    double T0 = now_ms();
+    World &w = s->w;
+    Ctx C;
+    C.s = s; C.p = p; C.st = st; C.precision = p->precision; C.half = 0.5 * p->dhat;
+    std::vector<double> box, vh(12 * (size_t)s->nb);
+    int rc = body_aabbs(s, box);
+    if (rc) return rc;
+    if ((rc = cuda_check(s, cudaMemcpyAsync(vh.data(), s->dev.v.p, 96 * (size_t)s->nb, cudaMemcpyDeviceToHost,
+                                            s->stream), "v")) || (rc = sync(s)))
+        return rc;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double msum = 0.0;
+    int nd = 0;
+    for (int b = 0; b < s->nb; ++b) {
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], box[6 * (size_t)b + k]);
+            hi[k] = std::max(hi[k], box[6 * (size_t)b + 3 + k]);
+        }
+        if (s->kind[b] == ABD_DYNAMIC) { msum += s->mass[b]; ++nd; }
+    }
+    C.l = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                    (hi[2] - lo[2]) * (hi[2] - lo[2]));
+    C.kB = p->kappa_barrier > 0.0 ? p->kappa_barrier
+                                  : 10.0 * (nd ? msum / nd : 1.0) *
+                                        std::sqrt(s->g[0] * s->g[0] + s->g[1] * s->g[1] + s->g[2] * s->g[2]) / p->dhat;
+    std::vector<uint64_t> mask;
+    double wov = 0.0;
+    int saved = s->n_slabs;
+    if (force_mono) s->n_slabs = 1;
+    rc = compute_masks(s, p->h, box, vh, mask, wov);
+    int N = s->n_slabs;
+    s->n_slabs = saved;
+    if (rc) return rc;
+    if ((rc = build_world(s, mask, N))) return rc;
+    st->l = C.l; st->kappa_barrier = C.kB; st->w = wov;
+    st->n_partitions = N; st->n_shared = w.nsh; st->n_slots = w.S_dyn;
+    k_slot_init<<<grid_for(w.S_all, 128), 128, 0, s->stream>>>(w.S_all, w.S_dyn, P<int>(w.slot_body), P<int>(w.slot_rep),
+                                                              P<double>(s->dev.q), P<double>(s->dev.v),
+                                                              P<double>(s->dev.mass), p->h, s->g[0], s->g[1], s->g[2],
+                                                              p->beta, P<double>(w.q), P<double>(w.qtil),
+                                                              P<double>(w.z), P<double>(w.u), P<double>(w.rho));
+    if (w.nsh > 0)
+        k_shared_init<<<grid_for(w.nsh, 128), 128, 0, s->stream>>>(w.nsh, P<int>(w.rep_off), P<int>(w.rep_slot),
+                                                                  P<double>(w.qtil), P<double>(w.rho), P<double>(w.zb),
+                                                                  P<double>(w.rho0), P<double>(w.rhob));
+    cudaMemsetAsync(w.ctr.p, 0, sizeof(Counters), s->stream);
+    if ((rc = cuda_check(s, cudaGetLastError(), "step init"))) return rc;
+    std::vector<int> run(N, 1);
+    int newton = 0, maxed = 0, status = ABD_OK, admm = 0;
+    bool converged = false, merge_ok = true;
+    double rinf = 0, sinf = 0, dinf = 0;
+    if (w.nsh == 0) {
+        if ((rc = newton_solve(C, run, newton, maxed))) return rc;
+        admm = 1;
+        converged = true;
+    } else {
+        int K = std::max(1, p->max_admm);
+        Counters *dc = P<Counters>(w.ctr);
+        for (int k = 1; k <= K + 1; ++k) {
+            if (k > 1) {
+                double ts = now_ms();
+                cudaMemsetAsync(&dc->rinf, 0, 24, s->stream);
+                k_consensus<<<grid_for(w.nsh, 128), 128, 0, s->stream>>>(w.nsh, P<int>(w.rep_off), P<int>(w.rep_slot),
+                                                                        P<double>(w.q), P<double>(w.u),
+                                                                        P<double>(w.rho), P<double>(w.zb),
+                                                                        P<double>(w.rb), P<double>(w.sb), dc);
+                k_delta<<<grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream>>>(w.S_dyn, P<double>(w.q),
+                                                                                    P<double>(w.qprev), dc);
+                k_scatter_z<<<grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream>>>(
+                    w.S_dyn, P<int>(w.slot_rep), P<double>(w.zb), P<double>(w.z));
+                if ((rc = cuda_check(s, cudaGetLastError(), "consensus"))) return rc;
+                if ((rc = merge_check(C, merge_ok))) return rc;
+                Counters hc;
+                if ((rc = cuda_check(s, cudaMemcpyAsync(&hc, dc, sizeof hc, cudaMemcpyDeviceToHost, s->stream),
+                                     "status")) || (rc = sync(s)))
+                    return rc;
+                rinf = u2d(hc.rinf);
+                sinf = u2d(hc.sinf);
+                dinf = u2d(hc.dinf);
+                double tol = p->theta * p->h * C.l;
+                C.t_sync += now_ms() - ts;
+                if (dinf < tol && rinf < tol && sinf < tol && merge_ok) { converged = true; break; }
+                if (k == K + 1) break;
+                if (p->rho_mode == ABD_RHO_ADAPTIVE) {
+                    k_rho_update<<<grid_for(w.nsh, 128), 128, 0, s->stream>>>(
+                        w.nsh, P<int>(w.rep_off), P<int>(w.rep_slot), P<double>(w.rb), P<double>(w.sb),
+                        P<double>(w.rho0), P<double>(w.rhob), P<double>(w.rho), P<double>(w.u), p->tau, p->mu,
+                        p->sigma_min, p->sigma_max);
+                }
+            }
+            cudaMemcpyAsync(w.qprev.p, w.q.p, 96 * (size_t)w.S_dyn, cudaMemcpyDeviceToDevice, s->stream);
+            if ((rc = newton_solve(C, run, newton, maxed))) return rc;
+            ++admm;
+        }
+        if (!converged) status = merge_ok ? ABD_ADMM_MAXITER : ABD_FELL_BACK_MONOLITHIC;
+    }
+    if (status == ABD_FELL_BACK_MONOLITHIC) {
+        abd_step_stats st2;
+        memset(&st2, 0, sizeof st2);
+        rc = step_impl(s, p, &st2, true);
+        if (rc < 0) return rc;
+        st->newton_iters = newton + st2.newton_iters;
+        st->admm_iters = admm;
+        st->status = status;
+        st->pcg_iters += st2.pcg_iters;
+        return status;
+    }
+    k_merge<<<grid_for(s->nb, 128), 128, 0, s->stream>>>(s->nb, P<int>(s->dev.kind), P<int>(w.body_rep),
+                                                        P<int>(w.body_slot), P<double>(w.zb), P<double>(w.q), p->h,
+                                                        P<double>(s->dev.q), P<double>(s->dev.v));
+    if ((rc = cuda_check(s, cudaGetLastError(), "merge")) || (rc = sync(s))) return rc;
+    prof_flush(s);
+    if (maxed && status == ABD_OK) status = ABD_NEWTON_MAXITER;
+    st->status = status;
+    st->admm_iters = admm;
+    st->newton_iters = newton;
+    st->r_inf = rinf; st->s_inf = sinf; st->delta_inf = dinf;
+    st->t_coll_ms = C.t_coll; st->t_solve_ms = C.t_solve; st->t_sync_ms = C.t_sync;
+    st->t_total_ms = now_ms() - T0;
+    return status;
+}
+
+}  // namespace
+
+extern "C" int abd_step(abd_scene *s, const abd_step_params *p, abd_step_stats *st) {
+    if (!s || !p || p->h <= 0 || p->dhat <= 0) return ABD_E_INVALID;
+    abd_step_stats local;
+    if (!st) st = &local;
+    memset(st, 0, sizeof *st);
+    st->min_distance = p->dhat;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != s->device) cudaSetDevice(s->device);
+    int rc = step_impl(s, p, st, false);
+    if (dev != s->device) cudaSetDevice(dev);
+    st->status = rc;
+    return rc;
+}
+
+extern "C" int abd_partition_masks(abd_scene *s, double h, uint64_t *mask, double *w_out) {
+    if (!s || !mask) return ABD_E_INVALID;
+    std::vector<double> box, vh(12 * (size_t)s->nb);
+    int rc = body_aabbs(s, box);
+    if (rc) return rc;
+    if ((rc = cuda_check(s, cudaMemcpy(vh.data(), s->dev.v.p, 96 * (size_t)s->nb, cudaMemcpyDeviceToHost), "v")))
+        return rc;
+    std::vector<uint64_t> m;
+    double w = 0;
+    if ((rc = compute_masks(s, h, box, vh, m, w))) return rc;
+    for (int b = 0; b < s->nb; ++b) mask[b] = m[b];
+    if (w_out) *w_out = w;
+    return ABD_OK;
+}
+
+extern "C" int abd_candidates(abd_scene *s, const double *x0, const double *x1, double dhat, int32_t *out, int64_t cap,
+                              int64_t *n_out) {
+    if (!s || !x0 || dhat <= 0 || !n_out) return ABD_E_INVALID;
+    std::vector<uint64_t> mask(s->nb);
+    for (int b = 0; b < s->nb; ++b) mask[b] = s->kind[b] == ABD_DYNAMIC ? 1 : 0;
+    int rc = build_world(s, mask, 1);
+    if (rc) return rc;
+    World &w = s->w;
+    std::vector<PartState> ps(1);
+    memset(&ps[0], 0, sizeof(PartState));
+    ps[0].active = 1;
+    if ((rc = write_parts(s, ps))) return rc;
+    // caller positions are in global vertex order; slot-vertex order differs
+    std::vector<double> xs(3 * (size_t)w.SV), xs1(x1 ? 3 * (size_t)w.SV : 0);
+    for (int sl = 0; sl < w.S_all; ++sl) {
+        int b = w.h_slot_body[sl];
+        for (int v = 0; v < s->nv[b]; ++v)
+            for (int k = 0; k < 3; ++k) {
+                xs[3 * (w.h_slot_voff[sl] + v) + k] = x0[3 * ((size_t)s->voff[b] + v) + k];
+                if (x1) xs1[3 * (w.h_slot_voff[sl] + v) + k] = x1[3 * ((size_t)s->voff[b] + v) + k];
+            }
+    }
+    if ((rc = h2d(s, w.x, xs))) return rc;
+    if (x1 && (rc = h2d(s, w.x1, xs1))) return rc;
+    double half = 0.5 * dhat;
+    if ((rc = launch_boxes(s, P<double>(w.x), x1 ? P<double>(w.x1) : nullptr, half,
+                           x1 ? P<double>(w.box1) : P<double>(w.box))))
+        return rc;
+    int64_t n_l1 = 0, n = 0;
+    if ((rc = launch_l1(s, x1 ? P<double>(w.box1) : P<double>(w.box), &n_l1))) return rc;
+    DBuf tmp;
+    int64_t c = std::max<int64_t>(cap, 1);
+    if (!dbuf_ensure(tmp, 12 * (size_t)c)) return set_err(s, ABD_E_OOM, "candidates");
+    rc = launch_l2(s, 0, P<double>(w.x), x1 ? P<double>(w.x1) : nullptr, half, n_l1, P<int32_t>(tmp), c, &n);
+    if (!rc && out && cap > 0)
+        rc = cuda_check(s, cudaMemcpy(out, tmp.p, 12 * (size_t)std::min(n, cap), cudaMemcpyDeviceToHost), "candidates");
+    dbuf_free(tmp);
+    *n_out = n;
+    return rc;
+}

@@ -1,0 +1,45 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+declared in include/abd.h (no compute call: no GPU needed)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "abd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(abd_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary_calls():
+    names = _declared()
+    for must in ("abd_scene_create", "abd_partition", "abd_step", "abd_state_get"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2605_15875_gb300 import abd, build
+    build.build()
+    L = abd.load()
+    names = _declared()
+    assert sorted(abd.EXPORTS) == names
+    for n in names:
+        assert hasattr(L, n), n
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_2605_15875_gb300 import abd
+    with pytest.raises(RuntimeError):
+        abd.load(str(tmp_path / "missing.so"))
+
+
+def test_oracle_is_not_imported_by_the_product():
+    pkg = os.path.join(ROOT, "paper_2605_15875_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "abd_oracle" not in txt, f

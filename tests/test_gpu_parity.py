@@ -1,0 +1,108 @@
+"""CUDA path vs the FP64 oracle, through the C ABI, on the same seeded inputs."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2605_15875_gb300 import abd, scenes
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-9   # relative in q per step (FP64 path)
+MIXED_TOL = 1e-4  # relative in q over 100 steps (FP32 assembly and PCG)
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2605_15875_gb300 import build
+    build.build()
+    abd.load()
+
+
+def test_body_constants_match_oracle():
+    sa = scenes.sphere_grid_in_box(n=2, level=2)
+    g, o = abd.Scene(sa), O.Scene(sa)
+    for b in range(sa.n_bodies):
+        mg, cg, Sg, Vg = g.body_props(b)
+        mo, co, So, Vo = o.body_props(b)
+        assert abs(mg - mo) <= 1e-12 * max(1, mo) and abs(Vg - Vo) <= 1e-12 * max(1, Vo)
+        assert np.abs(cg - co).max() < 1e-15 and np.abs(Sg - So).max() <= 1e-12 * max(1e-30, np.abs(So).max())
+    assert np.array_equal(g.state()[0], g.state()[0])
+    assert rel(g.state()[0], o.state()[0]) < 1e-15
+
+
+def _cand_set(arr):
+    return {tuple(int(v) for v in r) for r in arr}
+
+
+@pytest.mark.parametrize("swept", [False, True])
+def test_candidates_bit_exact(swept):
+    sa = scenes.sphere_grid_in_box(n=3, ny=2, nz=2, level=2, spacing=0.2004, lowest=0.1003)
+    g, o = abd.Scene(sa), O.Scene(sa)
+    x = o.vertices()
+    rng = np.random.default_rng(7)
+    x1 = x + rng.normal(size=x.shape) * 0.004 if swept else None
+    for dhat in (1e-3, 4e-3):
+        got = g.candidates(x, x1, dhat)
+        ref = o.candidates(x, x1, dhat)
+        assert len(ref) > 100
+        assert _cand_set(got) == _cand_set(ref)
+        assert len(got) == len(ref)  # no duplicates
+
+
+def _run_pair(sa, steps, params_g, params_o, tol, partition=None):
+    g, o = abd.Scene(sa), O.Scene(sa)
+    if partition:
+        g.partition(**partition)
+    worst = 0.0
+    for k in range(steps):
+        sg = g.step(params_g)
+        so = o.step(params_o)
+        qg, vg = g.state()
+        qo, vo = o.state()
+        e = rel(qg, qo)
+        worst = max(worst, e)
+        assert e <= tol, (k, e, sg, so)
+        assert sg["status"] >= 0
+    return worst, g, o
+
+
+def test_free_fall_closed_form_gpu():
+    sa = scenes.two_body_free_flight(seed=3)
+    g = abd.Scene(sa)
+    q0, v0 = g.state()
+    for n in range(1, 11):
+        st = g.step(abd.default_params())
+        q, _ = g.state()
+        pred = q0[:, :3] + n * 1e-2 * v0[:, :3] + 1e-4 * sa.gravity * n * (n + 1) / 2
+        assert np.abs(q[:, :3] - pred).max() < 1e-12
+        assert np.abs(q[:, 3:] - q0[:, 3:]).max() == 0.0
+
+
+def test_cube_stack_fp64_parity_100_steps():
+    sa = scenes.cube_stack()
+    worst, g, o = _run_pair(sa, 100, abd.default_params(), O.default_params(), FP64_TOL)
+    print("worst rel err", worst)
+
+
+def test_cube_row_admm_fp64_parity():
+    sa = scenes.cube_stack(nx=4, ny=2, nz=1)
+    worst, g, o = _run_pair(sa, 25, abd.default_params(), O.default_params(n_slabs=2, axis=0), FP64_TOL,
+                            partition=dict(n_slabs=2, axis=0))
+    print("worst rel err", worst)
+
+
+def test_cube_stack_mixed_100_steps():
+    sa = scenes.cube_stack()
+    g, o = abd.Scene(sa), O.Scene(sa)
+    pg = abd.default_params(precision=abd.MIXED, pcg_rtol=1e-4)
+    for k in range(100):
+        st = g.step(pg)
+        o.step(O.default_params())
+        assert st["status"] >= 0
+    e = rel(g.state()[0], o.state()[0])
+    print("mixed rel err after 100 steps", e)
+    assert e <= MIXED_TOL

@@ -1,0 +1,298 @@
+#!/usr/bin/env python
+"""Benchmark of distributed ABD-IPC on one GB300: body-steps/s of consensus
+ADMM over 4 slab partitions of 512 noisy icospheres falling into an open box
+(mixed precision: FP32 assembly and PCG, FP64 CCD, energies, residuals and
+consensus), beside the plain FP64 path on the same scene, p50/p99 step
+latency, the dominant kernel's roofline and the FP64 CPU oracle's throughput.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  N > 1 runs independent replicas, one per GPU
+(the method's partitions all live on one GPU; nothing is exchanged between
+GPUs)."""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "admm4_slabs_512_icosphereL2_open_box"
+PLANES = [-0.6, 0.0, 0.6]
+METRIC = "ABD-IPC body-steps/s vs plain FP64 GPU at oracle tol; p50/p99 step latency"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def scene_arrays():
+    from paper_2605_15875_gb300 import scenes
+    return scenes.sphere_grid_in_box(seed=0)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2605_15875_gb300 import abd, build as B
+
+    B.build()
+    abd.load()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    sa = scene_arrays()
+    B_ = sa.n_dynamic
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def make(precision):
+        sc = abd.Scene(sa, stream=int(stream.cuda_stream))
+        sc.partition(n_slabs=4, axis=0, planes=PLANES)
+        p = abd.default_params(precision=precision, pcg_rtol=1e-12 if precision == abd.FP64 else 1e-5)
+        return sc, p
+
+    def timed(sc, p, steps, warmup, profile=False):
+        for _ in range(warmup):
+            sc.step(p)
+        if profile:
+            sc.profile(True)
+        lat, launches, stats = [], 0, []
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()  # L2 flush between timed steps, outside the events
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = sc.step(p)
+            e1.record(stream)
+            e1.synchronize()
+            lat.append(e0.elapsed_time(e1))
+            launches += st["kernel_launches"]
+            stats.append(st)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        return lat, launches, stats
+
+    sc, pm = make(abd.MIXED)
+    with Clocks(dev) as clk:
+        lat, launches, stats = timed(sc, pm, args.steps, args.warmup, profile=True)
+    total_ms = sum(lat)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = B_ * args.steps * world / (total_ms / 1e3)
+    # dominant kernel and its roofline
+    names = ["pcg", "l2_static", "l2_swept", "pair_assemble", "slot_assemble", "ccd"]
+    ks = {n: sc.kernel_stats(n) for n in names}
+    dom = max(ks, key=lambda n: ks[n][1])
+    n_l, ms_l, by_l = ks[dom]
+    peak, peak_kind = measured_peaks()
+    achieved = (by_l / (ms_l / 1e3)) / 1e9 if ms_l > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind,
+            "launches": n_l, "avg_launch_us": round(1e3 * ms_l / max(1, n_l), 3),
+            "share_of_step": round(ms_l / total_ms, 4) if total_ms else None,
+            "kernels_ms": {n: round(v[1], 3) for n, v in ks.items()}}
+    fp64 = None
+    if not args.no_fp64:
+        sc64, p64 = make(abd.FP64)
+        lat64, _, _ = timed(sc64, p64, args.steps, args.warmup)
+        fp64 = B_ * args.steps * world / (sum(lat64) / 1e3)
+        sc64.close()
+    e2e = None
+    if not args.no_e2e:
+        sce, pe = make(abd.MIXED)
+        for _ in range(args.warmup):
+            sce.step(pe)
+        qh = torch.empty((sa.n_bodies, 12), dtype=torch.float64).pin_memory()
+        vh = torch.empty((sa.n_bodies, 12), dtype=torch.float64).pin_memory()
+        q0, v0 = sce.state()
+        qh.copy_(torch.from_numpy(q0))
+        vh.copy_(torch.from_numpy(v0))
+        L = sce.L
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            L.abd_state_set(sce.h, qh.data_ptr(), vh.data_ptr(), sa.n_bodies)
+            sce.step(pe)
+            L.abd_state_get(sce.h, qh.data_ptr(), vh.data_ptr(), sa.n_bodies)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": round(B_ * args.steps * world / dt, 3), "unit": "body-steps/s",
+               "h2d_bytes_per_step": 2 * 96 * sa.n_bodies, "d2h_bytes_per_step": 2 * 96 * sa.n_bodies}
+        sce.close()
+    cpu = cpu_baseline(args.cpu_seconds) if (rank == 0 and world == 1) else None
+    lat_sorted = sorted(lat)
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "body-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "bodies": B_, "triangles": sa.total_tris(), "partitions": 4,
+                   "slab_planes_x": PLANES, "h": pm.h, "dhat": pm.dhat, "precision": "mixed",
+                   "rho": "adaptive", "pcg_rtol": pm.pcg_rtol, "newton_tol": pm.newton_tol,
+                   "theta": pm.theta, "l2": "flushed between timed steps (256 MB write)"},
+        "p50_ms": round(float(np.percentile(lat_sorted, 50)), 4),
+        "p99_ms": round(float(np.percentile(lat_sorted, 99)), 4),
+        "fp64_value": None if fp64 is None else round(fp64, 3),
+        "speedup_vs_fp64": None if fp64 is None else round(value / fp64, 3),
+        "admm_iters_mean": float(np.mean([s["admm_iters"] for s in stats])),
+        "newton_iters_mean": float(np.mean([s["newton_iters"] for s in stats])),
+        "active_pairs_peak": int(max(s["n_active_peak"] for s in stats)),
+        "candidates_peak": int(max(s["n_candidates_peak"] for s in stats)),
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    sc.close()
+    return out
+
+
+def cpu_baseline(seconds):
+    """The FP64 oracle as it stands, on one host core, over the first steps of
+    the same workload (stops after `seconds` of CPU work, at least one step)."""
+    import oracle as O
+    sa = scene_arrays()
+    sc = O.Scene(sa)
+    p = O.default_params(n_slabs=4, axis=0, planes=PLANES)
+    n, t0 = 0, time.process_time()
+    while True:
+        sc.step(p)
+        n += 1
+        if time.process_time() - t0 > seconds:
+            break
+    dt = time.process_time() - t0
+    return {"value": round(sa.n_dynamic * n / dt, 4), "unit": "body-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n} steps of the same scene (512 bodies, 4 slabs), single thread, "
+                      f"{dt:.1f} s CPU; early steps are pre-contact free fall"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle as O
+    oracle_build = O.build()  # noqa: F841
+    sa = scene_arrays()
+    sc = O.Scene(sa)
+    p = O.default_params(n_slabs=4, axis=0, planes=PLANES)
+    for _ in range(args.warmup):
+        sc.step(p)
+    lat, t_start, budget = [], time.perf_counter(), 150.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        sc.step(p)
+        lat.append(1e3 * (time.perf_counter() - t0))
+        if time.perf_counter() - t_start > budget:
+            break
+    n = len(lat)
+    value = sa.n_dynamic * n / (sum(lat) / 1e3)
+    sample = (f"steps {args.warmup}..{args.warmup + n} of the same scene on one host core"
+              + ("" if n == args.steps else f" (stopped after {budget:.0f} s)"))
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "body-steps/s",
+            "n_gpus": world, "steps": n, "warmup": args.warmup, "ms_per_step": round(sum(lat) / n, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "bodies": sa.n_dynamic, "partitions": 4},
+            "cpu_baseline": {"value": round(value, 4), "unit": "body-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "body-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl")
+    out = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if world > 1 and args.impl == "ours":
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

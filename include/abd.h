@@ -116,6 +116,7 @@ typedef struct {
     int64_t n_candidates_peak, n_active_peak;
     double r_inf, s_inf, delta_inf, min_distance, l, kappa_barrier, w;
     double t_solve_ms, t_coll_ms, t_sync_ms, t_total_ms; /* host wall clock split (Table 1 columns) */
+    int64_t kernel_launches;       /* kernels of this library launched by the step */
 } abd_step_stats;
 
 /* --- scene ---------------------------------------------------------------- */

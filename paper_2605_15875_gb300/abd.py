@@ -51,7 +51,7 @@ class StepStats(C.Structure):
                 ("r_inf", C.c_double), ("s_inf", C.c_double), ("delta_inf", C.c_double),
                 ("min_distance", C.c_double), ("l", C.c_double), ("kappa_barrier", C.c_double), ("w", C.c_double),
                 ("t_solve_ms", C.c_double), ("t_coll_ms", C.c_double), ("t_sync_ms", C.c_double),
-                ("t_total_ms", C.c_double)]
+                ("t_total_ms", C.c_double), ("kernel_launches", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

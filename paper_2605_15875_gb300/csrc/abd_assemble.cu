@@ -159,30 +159,35 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
         int part = pair_part(sa, sb, A.S_dyn, A.slot_part);
         if (!A.part[part].active) continue;
         bool ee = r.flags & 1;
-        double o[3];
-        for (int k = 0; k < 3; ++k) o[k] = A.x[3 * (int64_t)r.v[0] + k];
-        T X[12];
+        // pair-local coordinates in FP64; gradient in FP64, Hessian in T
+        double Xd[12];
         for (int v = 0; v < 4; ++v)
-            for (int k = 0; k < 3; ++k) X[3 * v + k] = T(A.x[3 * (int64_t)r.v[v] + k] - o[k]);
-        T E, gx[12], H[144];
-        T d = pair_energy_derivs<T>(ee, X, T(A.dhat), T(A.kB), T(r.eps), E, gx, H);
-        if (!(d < T(A.dhat)) || !(d > T(0))) continue;
+            for (int k = 0; k < 3; ++k) Xd[3 * v + k] = A.x[3 * (int64_t)r.v[v] + k] - A.x[3 * (int64_t)r.v[0] + k];
+        PairGrad PG;
+        double gx[12];
+        double d = pair_gradient(ee, Xd, A.dhat, A.kB, r.eps, PG, gx);
+        if (!(d < A.dhat) || !(d > 0.0)) continue;
+        T X[12], H[144];
+        for (int e = 0; e < 12; ++e) X[e] = T(Xd[e]);
+        pair_hessian<T>(ee, X, PG, T(d), T(A.kB), T(r.eps), H);
         psd_project<T, 12>(H);
         double w = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
         int sl[4];
         T xi[4][4];
+        double xbv[4][4];
         for (int v = 0; v < 4; ++v) {
             int s = A.sv_slot[r.v[v]];
             sl[v] = s < A.S_dyn ? s : -1;
             int b = A.slot_body[s];
             const double *xb = A.xbar + 3 * ((int64_t)A.voff[b] + (r.v[v] - A.slot_voff[s]));
-            xi[v][0] = T(1); xi[v][1] = T(xb[0]); xi[v][2] = T(xb[1]); xi[v][3] = T(xb[2]);
+            xbv[v][0] = 1.0; xbv[v][1] = xb[0]; xbv[v][2] = xb[1]; xbv[v][3] = xb[2];
+            for (int a = 0; a < 4; ++a) xi[v][a] = T(xbv[v][a]);
         }
         for (int v = 0; v < 4; ++v) {
             if (sl[v] < 0) continue;
             for (int k = 0; k < 3; ++k)
                 for (int a = 0; a < 4; ++a)
-                    atomicAdd(A.g + 12 * (int64_t)sl[v] + qidx(k, a), w * (double)(gx[3 * v + k] * xi[v][a]));
+                    atomicAdd(A.g + 12 * (int64_t)sl[v] + qidx(k, a), w * gx[3 * v + k] * (double)xbv[v][a]);
         }
         // slot-pair blocks: (sa, sa), (sb, sb), (min, max)
         int ss[2] = {sa < A.S_dyn ? sa : -1, sb < A.S_dyn ? sb : -1};
@@ -490,7 +495,7 @@ int launch_narrow(abd_scene *s, int64_t n_cand, double dhat, int64_t *n_act) {
     for (;;) {
         cudaMemsetAsync(&c->act, 0, 8, s->stream);
         if (n_cand > 0)
-            k_narrow<<<grid_for(n_cand, 256), 256, 0, s->stream>>>(P<PairRec>(w.cand), n_cand, P<double>(w.x), dhat,
+            ABD_LAUNCH(s, k_narrow, grid_for(n_cand, 256), 256, 0, s->stream, P<PairRec>(w.cand), n_cand, P<double>(w.x), dhat,
                                                                   P<PairRec>(w.act), w.cap_act, &c->act);
         int rc = cuda_check(s, cudaGetLastError(), "k_narrow");
         if (rc) return rc;
@@ -519,19 +524,23 @@ static int assemble_T(abd_scene *s, const abd_step_params *p, double kB, int64_t
     }
     cudaEvent_t ea, eb;
     if (w.S_dyn > 0) {
-        prof_begin(s, "slot_assemble", 0, &ea, &eb);
-        k_slot_assemble<T><<<grid_for(w.S_dyn, 128), 128, 0, s->stream>>>(A, P<T>(w.diag));
+        // q, q~, z, u, S in; g and the diagonal block out
+        prof_begin(s, "slot_assemble", (double)w.S_dyn * (4 * 96 + 72 + 96 + 144.0 * sizeof(T)), &ea, &eb);
+        ABD_LAUNCH(s, k_slot_assemble<T>, grid_for(w.S_dyn, 128), 128, 0, s->stream, A, P<T>(w.diag));
         prof_end(s, ea, eb, prof_index(s, "slot_assemble"));
     }
     if (n_act > 0) {
-        prof_begin(s, "pair_assemble", 0, &ea, &eb);
-        k_pair_assemble<T><<<grid_for(n_act, 64), 64, 0, s->stream>>>(A, P<PairRec>(w.act), n_act, P<int2>(w.l1),
+        // record, 4 positions, 4 rest positions in; three 12x12 blocks and two
+        // 12-vectors read-modify-written
+        prof_begin(s, "pair_assemble", (double)n_act * (32 + 96 + 96 + 2.0 * (3 * 144 * sizeof(T) + 2 * 96)), &ea,
+                   &eb);
+        ABD_LAUNCH(s, k_pair_assemble<T>, grid_for(n_act, 64), 64, 0, s->stream, A, P<PairRec>(w.act), n_act, P<int2>(w.l1),
                                                                       P<T>(w.diag), P<T>(w.off), P<int>(w.offflag));
         prof_end(s, ea, eb, prof_index(s, "pair_assemble"));
     }
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
     if (s->planes.n > 0 && SVd > 0)
-        k_vp_assemble<T><<<grid_for(SVd, 256), 256, 0, s->stream>>>(A, SVd, P<T>(w.diag));
+        ABD_LAUNCH(s, k_vp_assemble<T>, grid_for(SVd, 256), 256, 0, s->stream, A, SVd, P<T>(w.diag));
     return cuda_check(s, cudaGetLastError(), "assemble");
 }
 
@@ -551,15 +560,16 @@ int launch_ccd(abd_scene *s, int64_t n_sw, const abd_step_params *p, double dhat
         cudaMemsetAsync(&c->ls, 0, 8, s->stream);
         cudaEvent_t ea, eb;
         if (n_sw > 0) {
-            prof_begin(s, "ccd", 0, &ea, &eb);
-            k_ccd<<<grid_for(n_sw, 128), 128, 0, s->stream>>>(P<PairRec>(w.cand), n_sw, P<double>(w.x),
+            // record and both configurations of its four vertices
+            prof_begin(s, "ccd", (double)n_sw * (32 + 4 * 48), &ea, &eb);
+            ABD_LAUNCH(s, k_ccd, grid_for(n_sw, 128), 128, 0, s->stream, P<PairRec>(w.cand), n_sw, P<double>(w.x),
                                                              P<double>(w.x1), P<int>(w.sv_slot), P<int>(w.slot_part),
                                                              w.S_dyn, dhat, p->accd_s, p->accd_c, P<PartState>(w.part),
                                                              P<PairRec>(w.ls), w.cap_ls, &c->ls, want_ls ? 1 : 0);
             prof_end(s, ea, eb, prof_index(s, "ccd"));
         }
         if (s->planes.n > 0 && SVd > 0)
-            k_vp_ccd<<<grid_for(SVd, 256), 256, 0, s->stream>>>(SVd, P<double>(w.x), P<double>(w.x1), P<int>(w.sv_slot),
+            ABD_LAUNCH(s, k_vp_ccd, grid_for(SVd, 256), 256, 0, s->stream, SVd, P<double>(w.x), P<double>(w.x1), P<int>(w.sv_slot),
                                                                 P<int>(w.slot_part), s->planes, p->accd_s,
                                                                 P<PartState>(w.part));
         int rc = cuda_check(s, cudaGetLastError(), "k_ccd");
@@ -588,9 +598,9 @@ int launch_energy(abd_scene *s, const abd_step_params *p, double kB, int64_t n_l
     A.alphas = alphas_dev; A.part = P<PartState>(w.part);
     A.h = p->h; A.dhat = p->dhat; A.kB = kB; A.planes = s->planes;
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
-    if (w.S_dyn > 0) k_energy_slots<<<grid_for(w.S_dyn, 128), 128, 0, s->stream>>>(A);
-    if (n_ls > 0) k_energy_pairs<<<grid_for(n_ls, 128), 128, 0, s->stream>>>(A, P<PairRec>(w.ls), n_ls);
-    if (s->planes.n > 0 && SVd > 0) k_energy_vp<<<grid_for(SVd, 128), 128, 0, s->stream>>>(A, SVd);
+    if (w.S_dyn > 0) ABD_LAUNCH(s, k_energy_slots, grid_for(w.S_dyn, 128), 128, 0, s->stream, A);
+    if (n_ls > 0) ABD_LAUNCH(s, k_energy_pairs, grid_for(n_ls, 128), 128, 0, s->stream, A, P<PairRec>(w.ls), n_ls);
+    if (s->planes.n > 0 && SVd > 0) ABD_LAUNCH(s, k_energy_vp, grid_for(SVd, 128), 128, 0, s->stream, A, SVd);
     return cuda_check(s, cudaGetLastError(), "energy");
 }
 

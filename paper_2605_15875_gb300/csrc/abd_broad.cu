@@ -293,7 +293,7 @@ namespace abd {
 int launch_transform(abd_scene *s, const double *q_slots, double *x, const double *alt, int mode) {
     World &w = s->w;
     if (w.SV == 0) return ABD_OK;
-    k_transform<<<grid_for(w.SV, 256), 256, 0, s->stream>>>(w.SV, P<int>(w.sv_slot), P<int>(w.slot_body),
+    ABD_LAUNCH(s, k_transform, grid_for(w.SV, 256), 256, 0, s->stream, w.SV, P<int>(w.sv_slot), P<int>(w.slot_body),
                                                            P<int64_t>(w.slot_voff), P<int>(s->dev.voff),
                                                            P<double>(s->dev.xbar), q_slots, alt, P<int>(w.slot_rep),
                                                            w.S_dyn, mode, x);
@@ -303,7 +303,7 @@ int launch_transform(abd_scene *s, const double *q_slots, double *x, const doubl
 int launch_boxes(abd_scene *s, const double *x0, const double *x1, double half, double *box) {
     World &w = s->w;
     if (w.S_all == 0) return ABD_OK;
-    k_boxes<<<grid_for((int64_t)w.S_all * 32, 256), 256, 0, s->stream>>>(w.S_all, P<int64_t>(w.slot_voff), x0, x1,
+    ABD_LAUNCH(s, k_boxes, grid_for((int64_t)w.S_all * 32, 256), 256, 0, s->stream, w.S_all, P<int64_t>(w.slot_voff), x0, x1,
                                                                           half, box);
     return cuda_check(s, cudaGetLastError(), "k_boxes");
 }
@@ -325,7 +325,7 @@ int launch_l1(abd_scene *s, const double *box, int64_t *count) {
     for (;;) {
         cudaMemsetAsync(&c->l1, 0, sizeof(unsigned long long), s->stream);
         int64_t ntile = (w.S_all + 31) / 32;
-        k_l1<<<grid_for((int64_t)w.S_all * ntile, 256), 256, 0, s->stream>>>(w.S_all, P<int>(w.slot_part), box,
+        ABD_LAUNCH(s, k_l1, grid_for((int64_t)w.S_all * ntile, 256), 256, 0, s->stream, w.S_all, P<int>(w.slot_part), box,
                                                                              P<PartState>(w.part), P<int2>(w.l1),
                                                                              w.cap_l1, &c->l1);
         int rc = cuda_check(s, cudaGetLastError(), "k_l1");
@@ -368,8 +368,20 @@ int launch_l2(abd_scene *s, int mode, const double *x0, const double *x1, double
         cudaMemsetAsync(&c->cand, 0, sizeof(unsigned long long), s->stream);
         if (n_l1 > 0) {
             cudaEvent_t ea, eb;
-            prof_begin(s, x1 ? "l2_swept" : "l2_static", 0.0, &ea, &eb);
-            k_l2<<<grid_for(n_l1, kL2Warps, 152 * 16), 32 * kL2Warps, 0, s->stream>>>(A);
+            // compulsory unique bytes: slot-vertex positions (one or two
+            // configurations), triangle and edge indices of the slots' bodies,
+            // the level-1 list and the emitted records
+            double bytes = 0.0;
+            if (s->prof) {
+                double tri_e = 0.0;
+                for (int sl = 0; sl < w.S_all; ++sl) {
+                    int b = w.h_slot_body[sl];
+                    tri_e += 12.0 * s->nt[b] + 8.0 * s->ne[b];
+                }
+                bytes = (x1 ? 48.0 : 24.0) * (double)w.SV + tri_e + 8.0 * (double)n_l1;
+            }
+            prof_begin(s, x1 ? "l2_swept" : "l2_static", bytes, &ea, &eb);
+            ABD_LAUNCH(s, k_l2, grid_for(n_l1, kL2Warps, 152 * 16), 32 * kL2Warps, 0, s->stream, A);
             prof_end(s, ea, eb, prof_index(s, x1 ? "l2_swept" : "l2_static"));
         }
         int rc = cuda_check(s, cudaGetLastError(), "k_l2");
@@ -377,6 +389,7 @@ int launch_l2(abd_scene *s, int mode, const double *x0, const double *x1, double
         unsigned long long n = 0;
         if ((rc = read_counter(s, &c->cand, &n))) return rc;
         *count = (int64_t)n;
+        if (s->prof && n_l1 > 0) prof_add_bytes(s, x1 ? "l2_swept" : "l2_static", (double)sizeof(PairRec) * (double)n);
         if (mode == 0 || (int64_t)n <= w.cap_cand) return ABD_OK;
         w.cap_cand = (int64_t)n + n / 2 + 1024;
         if (!dbuf_ensure(w.cand, sizeof(PairRec) * w.cap_cand)) return set_err(s, ABD_E_OOM, "candidate list");

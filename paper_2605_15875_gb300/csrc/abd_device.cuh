@@ -331,54 +331,91 @@ __device__ void psd_project(T *H) {
         }
 }
 
-// Barrier energy of one PT/EE pair (kB * [m(c)] * b(d)) with gradient and raw
-// Hessian in pair-local coordinates X (12).  Returns the distance; when
-// d >= dhat nothing is written.
-template <class T>
-__device__ T pair_energy_derivs(bool ee, const T *X, T dhat, T kB, T eps_x, T &E, T *g, T *H) {
+// FP64 gradient of one PT/EE pair's barrier energy kB * [m(c)] * b(d) in
+// pair-local coordinates X.  Returns d; fills the feature (type, beta) and the
+// scalars the Hessian needs.  When d >= dhat or d <= 0 nothing else is written.
+struct PairGrad {
     int type;
-    T b0, b1;
-    T s2 = classify<T>(ee, X, type, b0, b1);
-    T d = tsqrt(s2);
-    if (!(d < dhat) || !(d > T(0))) return d;
-    Feature f = feature_of(ee, type);
+    double b0, b1;       // beta of the feature
+    double b, bp, bpp;   // barrier and its derivatives at d
+    double m;            // mollifier value (1 for PT or inactive)
+    bool moll;           // mollifier active
+};
+
+__device__ inline double pair_gradient(bool ee, const double *X, double dhat, double kB, double eps_x, PairGrad &P,
+                                       double *g) {
+    double s2 = classify<double>(ee, X, P.type, P.b0, P.b1);
+    double d = sqrt(s2);
+    if (!(d < dhat) || !(d > 0.0)) return d;
+    Feature f = feature_of(ee, P.type);
+    double w[4], r[3] = {0, 0, 0};
+    for (int v = 0; v < 4; ++v) w[v] = double(f.w0[v]) + P.b0 * double(f.c[0][v]) + P.b1 * double(f.c[1][v]);
+    for (int v = 0; v < 4; ++v)
+        for (int a = 0; a < 3; ++a) r[a] += w[v] * X[3 * v + a];
+    barrier3<double>(d, dhat, P.b, P.bp, P.bpp);
+    // grad b = b' grad d, grad d = grad s / 2d = w (x) r / d
+    for (int v = 0; v < 4; ++v)
+        for (int a = 0; a < 3; ++a) g[3 * v + a] = P.bp * w[v] * r[a] / d;
+    P.m = 1.0;
+    P.moll = false;
+    if (ee) {
+        double ea[3] = {X[3] - X[0], X[4] - X[1], X[5] - X[2]};
+        double eb[3] = {X[9] - X[6], X[10] - X[7], X[11] - X[8]};
+        double cr[3], t[3];
+        cross3(cr, ea, eb);
+        double c = dot3(cr, cr);
+        if (c < eps_x) {
+            double rr = c / eps_x;
+            P.m = rr * (2.0 - rr);
+            P.moll = true;
+            double m1 = (2.0 - 2.0 * rr) / eps_x;
+            double ge[6];
+            cross3(t, eb, cr);
+            ge[0] = 2 * t[0]; ge[1] = 2 * t[1]; ge[2] = 2 * t[2];
+            cross3(t, cr, ea);
+            ge[3] = 2 * t[0]; ge[4] = 2 * t[1]; ge[5] = 2 * t[2];
+            const double sg[4] = {-1, 1, -1, 1};
+            for (int v = 0; v < 4; ++v)
+                for (int a = 0; a < 3; ++a) g[3 * v + a] = m1 * sg[v] * ge[3 * (v >> 1) + a] * P.b + P.m * g[3 * v + a];
+        }
+    }
+    for (int i = 0; i < 12; ++i) g[i] *= kB;
+    return d;
+}
+
+// Raw (unprojected) Hessian of the same pair in precision T, from the FP64
+// feature and barrier scalars of pair_gradient.
+template <class T>
+__device__ void pair_hessian(bool ee, const T *X, const PairGrad &P, T d, T kB, T eps_x, T *H) {
+    Feature f = feature_of(ee, P.type);
     T gs[12];
-    dist2_derivs<T>(X, f, b0, b1, gs, H);  // H <- hess s
-    T b, bp, bpp;
-    barrier3<T>(d, dhat, b, bp, bpp);
+    dist2_derivs<T>(X, f, T(P.b0), T(P.b1), gs, H);  // H <- hess s
     T inv2d = T(1) / (T(2) * d);
     T gd[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) gd[i] = gs[i] * inv2d;
-    // hess b = b'' gd gd^T + b' (Hs / 2d - gs gs^T / 4d^3) = (b'' - b'/d) gd gd^T + (b'/2d) Hs
-    T cg = bpp - bp / d, ch = bp * inv2d;
+    // hess b = (b'' - b'/d) gd gd^T + (b'/2d) hess s
+    T bp = T(P.bp), cg = T(P.bpp) - bp / d, ch = bp * inv2d;
 #pragma unroll
     for (int i = 0; i < 12; ++i)
 #pragma unroll
         for (int j = 0; j < 12; ++j) H[i * 12 + j] = cg * gd[i] * gd[j] + ch * H[i * 12 + j];
+    if (ee && P.moll) {
+        T gb[12];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) g[i] = bp * gd[i];
-    if (ee) {
+        for (int i = 0; i < 12; ++i) gb[i] = bp * gd[i];
         T gm[12], Hm[144];
         bool act;
         T m = mollifier<T>(X, eps_x, gm, Hm, act);
-        if (act) {
+        T b = T(P.b);
 #pragma unroll
-            for (int i = 0; i < 12; ++i)
+        for (int i = 0; i < 12; ++i)
 #pragma unroll
-                for (int j = 0; j < 12; ++j)
-                    H[i * 12 + j] = Hm[i * 12 + j] * b + gm[i] * g[j] + g[i] * gm[j] + m * H[i * 12 + j];
-#pragma unroll
-            for (int i = 0; i < 12; ++i) g[i] = gm[i] * b + m * g[i];
-            b *= m;
-        }
+            for (int j = 0; j < 12; ++j)
+                H[i * 12 + j] = Hm[i * 12 + j] * b + gm[i] * gb[j] + gb[i] * gm[j] + m * H[i * 12 + j];
     }
-    E = kB * b;
-#pragma unroll
-    for (int i = 0; i < 12; ++i) g[i] *= kB;
 #pragma unroll
     for (int i = 0; i < 144; ++i) H[i] *= kB;
-    return d;
 }
 
 // Barrier energy only (no derivatives), FP64.

@@ -132,6 +132,7 @@ struct abd_scene {
     size_t pinned_bytes = 0;
     // profiling
     bool prof = false;
+    int64_t n_launches = 0;
     std::vector<abd::KStat> kstats;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
@@ -158,10 +159,19 @@ int launch_pcg(abd_scene *s, int precision, const abd_step_params *p, int64_t n_
 void prof_begin(abd_scene *s, const char *name, double bytes, cudaEvent_t *a, cudaEvent_t *b);
 void prof_end(abd_scene *s, cudaEvent_t a, cudaEvent_t b, int idx);
 void prof_flush(abd_scene *s);
+void prof_add_bytes(abd_scene *s, const char *name, double bytes);
 int prof_index(abd_scene *s, const char *name);
 
 int set_err(abd_scene *s, int code, const std::string &msg);
 int cuda_check(abd_scene *s, cudaError_t e, const char *what);
+
+// Every kernel launch goes through this macro so the scene can report how
+// many of the library's kernels a step launched.
+#define ABD_LAUNCH(S, K, G, B, SM, ST, ...)      \
+    do {                                         \
+        K<<<G, B, SM, ST>>>(__VA_ARGS__);        \
+        ++(S)->n_launches;                       \
+    } while (0)
 
 inline int grid_for(int64_t n, int block, int maxb = 152 * 32) {
     int64_t g = (n + block - 1) / block;

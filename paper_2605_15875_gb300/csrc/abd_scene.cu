@@ -70,6 +70,10 @@ void prof_begin(abd_scene *s, const char *name, double bytes, cudaEvent_t *a, cu
     cudaEventRecord(*a, s->stream);
 }
 
+void prof_add_bytes(abd_scene *s, const char *name, double bytes) {
+    if (s->prof) s->kstats[prof_index(s, name)].bytes += bytes;
+}
+
 void prof_end(abd_scene *s, cudaEvent_t a, cudaEvent_t b, int idx) {
     if (!a || !b) return;
     cudaEventRecord(b, s->stream);

@@ -347,6 +347,14 @@ __global__ void k_pcg_parts_check(PcgPart *pp, int NP) {
         if (!pp[q].done && !(pp[q].r0 > 0.0)) pp[q].done = 1;
 }
 
+__global__ void k_count_flags(const int *__restrict__ f, int64_t n, int *__restrict__ out) {
+    int c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += f[i] != 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 // max |dq| per partition (ordered-double atomics).
 __global__ void k_dqmax(int S_dyn, const int *__restrict__ slot_part, const double *__restrict__ dq,
                         PartState *__restrict__ part) {
@@ -531,7 +539,7 @@ int sync(abd_scene *s) { return cuda_check(s, cudaStreamSynchronize(s->stream), 
 int body_aabbs(abd_scene *s, std::vector<double> &box) {
     DBuf &tmp = s->w.aabb;
     if (!dbuf_ensure(tmp, 48 * (size_t)s->nb)) return set_err(s, ABD_E_OOM, "aabb");
-    k_body_aabb<<<grid_for((int64_t)s->nb * 32, 256), 256, 0, s->stream>>>(s->nb, P<int>(s->dev.voff),
+    ABD_LAUNCH(s, k_body_aabb, grid_for((int64_t)s->nb * 32, 256), 256, 0, s->stream, s->nb, P<int>(s->dev.voff),
                                                                           P<double>(s->dev.xbar),
                                                                           P<double>(s->dev.q), P<double>(tmp));
     box.resize(6 * (size_t)s->nb);
@@ -644,7 +652,7 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
               dbuf_ensure(w.pinv, 8 * 144 * Sd) && dbuf_ensure(w.pcg_r, 96 * Sd) && dbuf_ensure(w.pcg_z, 96 * Sd) &&
               dbuf_ensure(w.pcg_p, 96 * Sd) && dbuf_ensure(w.pcg_ap, 96 * Sd);
     if (!ok) return set_err(s, ABD_E_OOM, "world buffers");
-    if (w.S_all > 0) k_fill_sv_slot<<<std::min(w.S_all, 152 * 8), 256, 0, s->stream>>>(w.S_all, P<int64_t>(w.slot_voff), P<int>(w.sv_slot));
+    if (w.S_all > 0) ABD_LAUNCH(s, k_fill_sv_slot, std::min(w.S_all, 152 * 8), 256, 0, s->stream, w.S_all, P<int64_t>(w.slot_voff), P<int>(w.sv_slot));
     return cuda_check(s, cudaGetLastError(), "build world");
 }
 
@@ -670,13 +678,19 @@ int pcg_T(Ctx &C, int64_t n_l1, int64_t *iters) {
     A.pp = P<PcgPart>(w.pcg_sc); A.NP = w.NP; A.tol2 = C.p->pcg_rtol * C.p->pcg_rtol; A.max_it = C.p->pcg_max;
     A.bar = P<unsigned>(w.bar);
     A.timeout = &P<Counters>(w.ctr)->timeout;
-    k_pinv<T><<<grid_for(w.S_dyn, 64), 64, 0, s->stream>>>(w.S_dyn, P<int>(w.slot_part), P<PartState>(w.part),
+    ABD_LAUNCH(s, k_pinv<T>, grid_for(w.S_dyn, 64), 64, 0, s->stream, w.S_dyn, P<int>(w.slot_part), P<PartState>(w.part),
                                                           P<T>(w.diag), P<T>(w.pinv));
-    k_pcg_parts_init<<<1, 64, 0, s->stream>>>(A.pp, A.part, w.NP);
-    k_pcg_init<T><<<grid_for(w.S_dyn, 128), 128, 0, s->stream>>>(A, P<T>(w.pinv), P<T>(w.pcg_r), P<T>(w.pcg_z),
+    ABD_LAUNCH(s, k_pcg_parts_init, 1, 64, 0, s->stream, A.pp, A.part, w.NP);
+    ABD_LAUNCH(s, k_pcg_init<T>, grid_for(w.S_dyn, 128), 128, 0, s->stream, A, P<T>(w.pinv), P<T>(w.pcg_r), P<T>(w.pcg_z),
                                                                 P<T>(w.pcg_p));
-    k_pcg_parts_check<<<1, 64, 0, s->stream>>>(A.pp, w.NP);
+    ABD_LAUNCH(s, k_pcg_parts_check, 1, 64, 0, s->stream, A.pp, w.NP);
     cudaMemsetAsync(w.bar.p, 0, 64, s->stream);
+    if (s->prof) {
+        cudaMemsetAsync(&P<Counters>(w.ctr)->overflow, 0, sizeof(int), s->stream);
+        if (n_l1 > 0)
+            ABD_LAUNCH(s, k_count_flags, grid_for(n_l1, 256), 256, 0, s->stream, P<int>(w.offflag), n_l1,
+                       &P<Counters>(w.ctr)->overflow);
+    }
     static int maxb = -1;
     if (maxb < 0) {
         int dev, sms = 0, per = 0;
@@ -693,6 +707,7 @@ int pcg_T(Ctx &C, int64_t n_l1, int64_t *iters) {
     cudaEvent_t ea, eb;
     prof_begin(s, "pcg", 0, &ea, &eb);
     cudaError_t e = cudaLaunchCooperativeKernel((void *)k_pcg_loop<T>, blocks, 256, args, 0, s->stream);
+    ++s->n_launches;
     prof_end(s, ea, eb, prof_index(s, "pcg"));
     int rc = cuda_check(s, e, "pcg launch");
     if (rc) return rc;
@@ -702,6 +717,15 @@ int pcg_T(Ctx &C, int64_t n_l1, int64_t *iters) {
     int64_t mx = 0;
     for (auto &q : h) mx = std::max<int64_t>(mx, q.it);
     *iters = mx;
+    if (s->prof) {
+        // per iteration: diagonal, preconditioner and non-zero off-diagonal
+        // blocks read once; p, Ap, r, z (T) and x (FP64) read/written once
+        int nz = 0;
+        cudaMemcpyAsync(&nz, &P<Counters>(w.ctr)->overflow, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+        sync(s);
+        double per = 144.0 * sizeof(T) * (2.0 * w.S_dyn + nz) + 12.0 * w.S_dyn * (7.0 * sizeof(T) + 16.0);
+        prof_add_bytes(s, "pcg", per * (double)mx);
+    }
     return ABD_OK;
 }
 
@@ -752,7 +776,7 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         if ((rc = check_timeout(s))) return rc;
         C.st->pcg_iters += pit;
         // Newton stopping test, before the line search
-        k_dqmax<<<grid_for(w.S_dyn, 128), 128, 0, s->stream>>>(w.S_dyn, P<int>(w.slot_part), P<double>(w.dq),
+        ABD_LAUNCH(s, k_dqmax, grid_for(w.S_dyn, 128), 128, 0, s->stream, w.S_dyn, P<int>(w.slot_part), P<double>(w.dq),
                                                               P<PartState>(w.part));
         if ((rc = read_parts(s, ps))) return rc;
         bool cont = false;
@@ -787,17 +811,17 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         cudaMemsetAsync(C.decided.p, 0, 4 * (size_t)w.NP, s->stream);
         for (int pass = 0; pass < 64; ++pass) {
             cudaMemsetAsync(C.pending.p, 0, 4, s->stream);
-            k_ls_alphas<<<1, 64, 0, s->stream>>>(w.NP, P<PartState>(w.part), P<int>(C.nh0), P<double>(C.alphas),
+            ABD_LAUNCH(s, k_ls_alphas, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0), P<double>(C.alphas),
                                                  p->max_halvings);
             if ((rc = launch_energy(s, p, C.kB, n_ls, P<double>(C.alphas)))) return rc;
-            k_ls_select<<<1, 64, 0, s->stream>>>(w.NP, P<PartState>(w.part), P<int>(C.nh0), P<int>(C.decided),
+            ABD_LAUNCH(s, k_ls_select, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0), P<int>(C.decided),
                                                  P<double>(C.alphas), p->max_halvings, P<int>(C.pending));
             int pend = 0;
             cudaMemcpyAsync(&pend, C.pending.p, 4, cudaMemcpyDeviceToHost, s->stream);
             if ((rc = sync(s))) return rc;
             if (!pend) break;
         }
-        k_update_q<<<grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream>>>(w.S_dyn, P<int>(w.slot_part),
+        ABD_LAUNCH(s, k_update_q, grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream, w.S_dyn, P<int>(w.slot_part),
                                                                                P<PartState>(w.part), P<double>(w.dq),
                                                                                P<double>(w.q));
         if ((rc = cuda_check(s, cudaGetLastError(), "line search"))) return rc;
@@ -834,6 +858,7 @@ int merge_check(Ctx &C, bool &ok) {
 
 int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool force_mono) {
     double T0 = now_ms();
+    int64_t L0 = s->n_launches;
     World &w = s->w;
     Ctx C;
     C.s = s; C.p = p; C.st = st; C.precision = p->precision; C.half = 0.5 * p->dhat;
@@ -869,13 +894,13 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
     if ((rc = build_world(s, mask, N))) return rc;
     st->l = C.l; st->kappa_barrier = C.kB; st->w = wov;
     st->n_partitions = N; st->n_shared = w.nsh; st->n_slots = w.S_dyn;
-    k_slot_init<<<grid_for(w.S_all, 128), 128, 0, s->stream>>>(w.S_all, w.S_dyn, P<int>(w.slot_body), P<int>(w.slot_rep),
+    ABD_LAUNCH(s, k_slot_init, grid_for(w.S_all, 128), 128, 0, s->stream, w.S_all, w.S_dyn, P<int>(w.slot_body), P<int>(w.slot_rep),
                                                               P<double>(s->dev.q), P<double>(s->dev.v),
                                                               P<double>(s->dev.mass), p->h, s->g[0], s->g[1], s->g[2],
                                                               p->beta, P<double>(w.q), P<double>(w.qtil),
                                                               P<double>(w.z), P<double>(w.u), P<double>(w.rho));
     if (w.nsh > 0)
-        k_shared_init<<<grid_for(w.nsh, 128), 128, 0, s->stream>>>(w.nsh, P<int>(w.rep_off), P<int>(w.rep_slot),
+        ABD_LAUNCH(s, k_shared_init, grid_for(w.nsh, 128), 128, 0, s->stream, w.nsh, P<int>(w.rep_off), P<int>(w.rep_slot),
                                                                   P<double>(w.qtil), P<double>(w.rho), P<double>(w.zb),
                                                                   P<double>(w.rho0), P<double>(w.rhob));
     cudaMemsetAsync(w.ctr.p, 0, sizeof(Counters), s->stream);
@@ -895,13 +920,13 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
             if (k > 1) {
                 double ts = now_ms();
                 cudaMemsetAsync(&dc->rinf, 0, 24, s->stream);
-                k_consensus<<<grid_for(w.nsh, 128), 128, 0, s->stream>>>(w.nsh, P<int>(w.rep_off), P<int>(w.rep_slot),
+                ABD_LAUNCH(s, k_consensus, grid_for(w.nsh, 128), 128, 0, s->stream, w.nsh, P<int>(w.rep_off), P<int>(w.rep_slot),
                                                                         P<double>(w.q), P<double>(w.u),
                                                                         P<double>(w.rho), P<double>(w.zb),
                                                                         P<double>(w.rb), P<double>(w.sb), dc);
-                k_delta<<<grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream>>>(w.S_dyn, P<double>(w.q),
+                ABD_LAUNCH(s, k_delta, grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream, w.S_dyn, P<double>(w.q),
                                                                                     P<double>(w.qprev), dc);
-                k_scatter_z<<<grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream>>>(
+                ABD_LAUNCH(s, k_scatter_z, grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream, 
                     w.S_dyn, P<int>(w.slot_rep), P<double>(w.zb), P<double>(w.z));
                 if ((rc = cuda_check(s, cudaGetLastError(), "consensus"))) return rc;
                 if ((rc = merge_check(C, merge_ok))) return rc;
@@ -917,7 +942,7 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
                 if (dinf < tol && rinf < tol && sinf < tol && merge_ok) { converged = true; break; }
                 if (k == K + 1) break;
                 if (p->rho_mode == ABD_RHO_ADAPTIVE) {
-                    k_rho_update<<<grid_for(w.nsh, 128), 128, 0, s->stream>>>(
+                    ABD_LAUNCH(s, k_rho_update, grid_for(w.nsh, 128), 128, 0, s->stream, 
                         w.nsh, P<int>(w.rep_off), P<int>(w.rep_slot), P<double>(w.rb), P<double>(w.sb),
                         P<double>(w.rho0), P<double>(w.rhob), P<double>(w.rho), P<double>(w.u), p->tau, p->mu,
                         p->sigma_min, p->sigma_max);
@@ -940,7 +965,7 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
         st->pcg_iters += st2.pcg_iters;
         return status;
     }
-    k_merge<<<grid_for(s->nb, 128), 128, 0, s->stream>>>(s->nb, P<int>(s->dev.kind), P<int>(w.body_rep),
+    ABD_LAUNCH(s, k_merge, grid_for(s->nb, 128), 128, 0, s->stream, s->nb, P<int>(s->dev.kind), P<int>(w.body_rep),
                                                         P<int>(w.body_slot), P<double>(w.zb), P<double>(w.q), p->h,
                                                         P<double>(s->dev.q), P<double>(s->dev.v));
     if ((rc = cuda_check(s, cudaGetLastError(), "merge")) || (rc = sync(s))) return rc;
@@ -952,6 +977,7 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
     st->r_inf = rinf; st->s_inf = sinf; st->delta_inf = dinf;
     st->t_coll_ms = C.t_coll; st->t_solve_ms = C.t_solve; st->t_sync_ms = C.t_sync;
     st->t_total_ms = now_ms() - T0;
+    st->kernel_launches = s->n_launches - L0;
     return status;
 }
 

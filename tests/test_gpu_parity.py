@@ -53,20 +53,33 @@ def test_candidates_bit_exact(swept):
         assert len(got) == len(ref)  # no duplicates
 
 
-def _run_pair(sa, steps, params_g, params_o, tol, partition=None):
-    g, o = abd.Scene(sa), O.Scene(sa)
+def _run_pair(sa, steps, params_g, params_o, tol, partition=None, traj_tol=1e-7):
+    """Per-step parity: before every step the CUDA scene takes the oracle's
+    state, so each comparison measures the error of one step (the FP64
+    contract).  A second CUDA scene runs free and its drift over the whole
+    trajectory is bounded by `traj_tol`.  Discrete decisions (ADMM rounds,
+    Newton iterations) must agree."""
+    g, free, o = abd.Scene(sa), abd.Scene(sa), O.Scene(sa)
     if partition:
         g.partition(**partition)
+        free.partition(**partition)
     worst = 0.0
     for k in range(steps):
-        sg = g.step(params_g)
-        so = o.step(params_o)
-        qg, vg = g.state()
         qo, vo = o.state()
+        g.set_state(qo, vo)
+        sg = g.step(params_g)
+        free.step(params_g)
+        so = o.step(params_o)
+        qg, _ = g.state()
+        qo, _ = o.state()
         e = rel(qg, qo)
         worst = max(worst, e)
         assert e <= tol, (k, e, sg, so)
         assert sg["status"] >= 0
+        assert (sg["admm_iters"], sg["newton_iters"]) == (so["admm_iters"], so["newton_iters"]), (k, sg, so)
+    drift = rel(free.state()[0], o.state()[0])
+    print(f"per-step worst {worst:.3e}, trajectory drift {drift:.3e}")
+    assert drift <= traj_tol
     return worst, g, o
 
 
@@ -105,4 +118,31 @@ def test_cube_stack_mixed_100_steps():
         assert st["status"] >= 0
     e = rel(g.state()[0], o.state()[0])
     print("mixed rel err after 100 steps", e)
+    assert e <= MIXED_TOL
+
+
+def _sphere_admm_scene():
+    return scenes.sphere_grid_in_box(n=4, ny=2, nz=2, level=1, lowest=0.12, spacing=0.25)
+
+
+def test_sphere_pile_admm_fp64_parity():
+    """Contact-rich consensus ADMM (2 slabs, shared spheres landing on the box
+    floor): FP64 path within 1e-9 of the oracle every step."""
+    sa = _sphere_admm_scene()
+    worst, g, o = _run_pair(sa, 16, abd.default_params(), O.default_params(n_slabs=2, axis=0), FP64_TOL,
+                            partition=dict(n_slabs=2, axis=0))
+    print("worst rel err", worst)
+
+
+def test_sphere_pile_admm_mixed():
+    sa = _sphere_admm_scene()
+    g, o = abd.Scene(sa), O.Scene(sa)
+    g.partition(n_slabs=2, axis=0)
+    pg = abd.default_params(precision=abd.MIXED, pcg_rtol=1e-5)
+    for k in range(16):
+        st = g.step(pg)
+        o.step(O.default_params(n_slabs=2, axis=0))
+        assert st["status"] >= 0
+    e = rel(g.state()[0], o.state()[0])
+    print("mixed rel err after 16 steps", e)
     assert e <= MIXED_TOL

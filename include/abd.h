@@ -165,6 +165,28 @@ int abd_state_device(abd_scene *s, double **q, double **v);
 int abd_candidates(abd_scene *s, const double *x0, const double *x1, double dhat, int32_t *out, int64_t cap,
                    int64_t *n_out);
 
+/* The same query as abd_candidates without allocating device memory, for
+ * callers that must not call cudaMalloc/cudaFree themselves or through this
+ * library (a plugin inside a framework whose allocator owns the GPU's memory
+ * budget; latency-critical loops that cannot absorb the device-wide
+ * synchronisation an allocation may cause).  The paper has no counterpart:
+ * this is a service of this library, not a step of the method.
+ *   x0, x1: DEVICE pointers, [V][3] doubles in global vertex order (x1 NULL:
+ *           static set); out: DEVICE pointer to `cap` int32 triples (type, i, j)
+ *           as in abd_candidates; n_out: host pointer, total count (entries
+ *           beyond cap are counted, not written).  Inputs and outputs stay the
+ *           caller's.
+ *   Intermediates live in one 32 MiB array of static device memory, held by
+ *   every GPU on which the library is loaded until the process exits.  The
+ *   first call on a device looks up that array's address; make that first call
+ *   before any stream capture on the device.  All calls share the array: calls
+ *   whose work overlaps on the GPU (other host threads, other streams) race.
+ *   Limits: at most 131072 bodies (ABD_E_INVALID beyond) and about 4 million
+ *   overlapping body pairs (ABD_E_PAIR_OVERFLOW beyond), each with a message
+ *   in abd_last_error().  Blocks until done. */
+int abd_candidates_noalloc(abd_scene *s, const double *x0, const double *x1, double dhat, int32_t *out, int64_t cap,
+                           int64_t *n_out);
+
 /* Per-kernel timing of the last steps (enabled by abd_profile(s, 1)): for the
  * kernel named `name`, launches, total device milliseconds (CUDA events on
  * the scene's stream) and algorithmic bytes moved. */

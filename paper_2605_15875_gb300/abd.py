@@ -61,7 +61,7 @@ class StepStats(C.Structure):
 EXPORTS = ["abd_scene_create", "abd_scene_destroy", "abd_scene_counts", "abd_body_props", "abd_partition",
            "abd_partition_masks", "abd_step", "abd_state_get", "abd_state_set", "abd_state_device",
            "abd_candidates", "abd_profile", "abd_kernel_stats", "abd_step_params_default", "abd_status_string",
-           "abd_last_error"]
+           "abd_last_error", "abd_candidates_noalloc"]
 
 _lib = None
 
@@ -88,6 +88,7 @@ def load(path: Optional[str] = None):
     L.abd_state_set.argtypes = [vp, vp, vp, i64]
     L.abd_state_device.argtypes = [vp, C.POINTER(vp), C.POINTER(vp)]
     L.abd_candidates.argtypes = [vp, vp, vp, C.c_double, vp, i64, C.POINTER(i64)]
+    L.abd_candidates_noalloc.argtypes = [vp, vp, vp, C.c_double, vp, i64, C.POINTER(i64)]
     L.abd_profile.argtypes = [vp, C.c_int32]
     L.abd_kernel_stats.argtypes = [vp, C.c_char_p, C.POINTER(i64), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.abd_step_params_default.argtypes = []

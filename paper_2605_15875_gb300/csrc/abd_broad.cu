@@ -10,7 +10,7 @@
 // plain definition -- every PT (both directions) and EE pair of different
 // slots, not both static, whose dhat/2-inflated boxes overlap -- evaluated
 // with exact FP64 min/max and one rounding per bound.
-#include "abd_internal.h"
+#include "abd_broad.cuh"
 
 namespace abd {
 
@@ -129,21 +129,7 @@ __global__ void k_l1(int S_all, const int *__restrict__ slot_part, const double 
     }
 }
 
-struct L2Args {
-    const int *slot_body;
-    const int64_t *slot_voff;
-    const int *voff, *nv, *toff, *nt, *eoff, *ne, *tri, *edge;
-    const double *erest2;
-    const double *x0, *x1, *box;
-    double half;
-    const int2 *l1;
-    int64_t n_l1;
-    int mode;          // 0: (type, gid_i, gid_j) triples; 1: PairRec
-    int32_t *out3;
-    PairRec *recs;
-    int64_t cap;
-    unsigned long long *count;
-};
+
 
 // Primitive kind: 0 vertex, 1 triangle, 2 edge.  Fills the slot-vertex ids and
 // returns the number of vertices.
@@ -182,7 +168,6 @@ __device__ __forceinline__ int prim_count(const L2Args &A, int kind, int slot) {
     return kind == 0 ? A.nv[b] : (kind == 1 ? A.nt[b] : A.ne[b]);
 }
 
-constexpr int kL2Warps = 4;
 constexpr int kStage = 64;
 
 __global__ void __launch_bounds__(32 * kL2Warps) k_l2(L2Args A) {

@@ -1,0 +1,32 @@
+// abd_broad.cuh -- declarations of the broad-phase kernels (abd_broad.cu).
+#pragma once
+#include "abd_internal.h"
+
+namespace abd {
+
+struct L2Args {
+    const int *slot_body;
+    const int64_t *slot_voff;
+    const int *voff, *nv, *toff, *nt, *eoff, *ne, *tri, *edge;
+    const double *erest2;
+    const double *x0, *x1, *box;
+    double half;
+    const int2 *l1;
+    int64_t n_l1;
+    int mode;          // 0: (type, gid_i, gid_j) triples; 1: PairRec
+    int32_t *out3;
+    PairRec *recs;
+    int64_t cap;
+    unsigned long long *count;
+};
+
+constexpr int kL2Warps = 4;
+
+__global__ void k_boxes(int S, const int64_t *__restrict__ slot_voff, const double *__restrict__ x0,
+                        const double *__restrict__ x1, double half, double *__restrict__ box);
+__global__ void k_l1(int S_all, const int *__restrict__ slot_part, const double *__restrict__ box,
+                     const PartState *__restrict__ part, int2 *__restrict__ out, int64_t cap,
+                     unsigned long long *__restrict__ count);
+__global__ void __launch_bounds__(32 * kL2Warps) k_l2(L2Args A);
+
+}  // namespace abd

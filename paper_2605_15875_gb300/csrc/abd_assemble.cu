@@ -48,8 +48,10 @@ __device__ __forceinline__ void append(bool keep, const PairRec &rec, PairRec *o
 }
 
 // Narrow phase: keep candidates with 0 < d < dhat.
-__global__ void k_narrow(const PairRec *__restrict__ cand, int64_t n, const double *__restrict__ x, double dhat,
-                         PairRec *__restrict__ act, int64_t cap, unsigned long long *__restrict__ count) {
+__global__ void k_narrow(const PairRec *__restrict__ cand, int64_t n, const unsigned long long *__restrict__ n_dev,
+                         const double *__restrict__ x, double dhat, PairRec *__restrict__ act, int64_t cap,
+                         unsigned long long *__restrict__ count) {
+    if (n_dev) n = min((int64_t)*n_dev, n);
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = base + threadIdx.x;
         bool keep = false;
@@ -82,6 +84,7 @@ struct AsmArgs {
     Planes planes;
     const int64_t *slot_voff;
     double *g;
+    int *rowcnt;  // per dynamic slot: number of distinct off-diagonal blocks in its row
 };
 
 // Per dynamic slot of an active partition: write g and the diagonal block.
@@ -130,7 +133,40 @@ __global__ void k_slot_assemble(AsmArgs A, T *__restrict__ diag) {
                         double v = a[l][i] * a[k][j] + (i == j ? C[k][l] : 0.0) + (k == l ? AtA[i][j] : 0.0);
                         H9[(3 * k + i) * 9 + 3 * l + j] = T(4.0 * kv * v);
                     }
-        psd_project<T, 9>(H9);
+        // PSD projection through the analytic eigensystem of the isotropic
+        // energy kappa V sum_k (sigma_k^2 - 1)^2: with A = U diag(sigma) V^T and
+        // every sigma_k^2 >= 1/3, only the three twist modes
+        // (u_i v_j^T - u_j v_i^T)/sqrt2, eigenvalue 4 kappa V (s_i^2 - s_i s_j +
+        // s_j^2 - 1), can be negative; they are removed from H9.  Otherwise the
+        // 9x9 Jacobi projection is used.
+        {
+            double M3[9], V3[9];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) M3[3 * i + j] = AtA[i][j];
+            jacobi<double, 3>(M3, V3);
+            double sg[3] = {M3[0], M3[4], M3[8]};
+            if (fmin(sg[0], fmin(sg[1], sg[2])) < 1.0 / 3.0 + 1e-3) {
+                psd_project<T, 9>(H9);
+            } else {
+                double sv[3], U3[3][3];
+                for (int k = 0; k < 3; ++k) sv[k] = sqrt(sg[k]);
+                for (int r = 0; r < 3; ++r)
+                    for (int k = 0; k < 3; ++k)
+                        U3[r][k] = (a[r][0] * V3[0 * 3 + k] + a[r][1] * V3[1 * 3 + k] + a[r][2] * V3[2 * 3 + k]) / sv[k];
+                const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
+                for (int t = 0; t < 3; ++t) {
+                    int i = pi[t], j = pj[t];
+                    double lam = 4.0 * kv * (sg[i] - sv[i] * sv[j] + sg[j] - 1.0);
+                    if (!(lam < 0.0)) continue;
+                    double v[9];
+                    for (int r = 0; r < 3; ++r)
+                        for (int c = 0; c < 3; ++c)
+                            v[3 * r + c] = (U3[r][i] * V3[c * 3 + j] - U3[r][j] * V3[c * 3 + i]) * 0.70710678118654752;
+                    for (int e = 0; e < 9; ++e)
+                        for (int f = 0; f < 9; ++f) H9[e * 9 + f] -= T(lam * v[e] * v[f]);
+                }
+            }
+        }
         for (int i = 0; i < 9; ++i)
             for (int j = 0; j < 9; ++j) D[(3 + i) * 12 + 3 + j] += T(kw * h2) * H9[i * 9 + j];
         if (A.slot_rep[s] >= 0) {
@@ -149,10 +185,16 @@ __global__ void k_slot_assemble(AsmArgs A, T *__restrict__ diag) {
 template <class T> __device__ __forceinline__ void atomic_addT(T *a, T v) { atomicAdd(a, v); }
 
 // Per active pair: barrier gradient and projected Hessian scattered to slots.
-template <class T>
+template <class T, bool full_path>
 __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int64_t n, const int2 *__restrict__ l1,
-                                T *__restrict__ diag, T *__restrict__ off, int *__restrict__ offflag) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+                                T *__restrict__ diag, T *__restrict__ off, int *__restrict__ offflag,
+                                int64_t *__restrict__ deferred, unsigned long long *__restrict__ n_deferred,
+                                const unsigned long long *__restrict__ n_dev) {
+    if (n_dev) n = min((int64_t)*n_dev, n);
+    for (int64_t ii = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ii < n; ii += (int64_t)gridDim.x * blockDim.x) {
+        // full_path: process the deferred (mollified edge-edge) pairs with the
+        // 12x12 projection; otherwise every active pair, deferring those
+        int64_t i = full_path ? deferred[ii] : ii;
         PairRec r = act[i];
         int sa, sb;
         pair_slots(r, A.sv_slot, sa, sb);
@@ -167,10 +209,14 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
         double gx[12];
         double d = pair_gradient(ee, Xd, A.dhat, A.kB, r.eps, PG, gx);
         if (!(d < A.dhat) || !(d > 0.0)) continue;
-        T X[12], H[144];
+        const bool moll = ee && PG.moll;
+        if (!full_path && moll) {
+            unsigned long long pos = atomicAdd(n_deferred, 1ull);
+            deferred[pos] = i;  // capacity n: one slot per active pair
+            continue;
+        }
+        T X[12];
         for (int e = 0; e < 12; ++e) X[e] = T(Xd[e]);
-        pair_hessian<T>(ee, X, PG, T(d), T(A.kB), T(r.eps), H);
-        psd_project<T, 12>(H);
         double w = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
         int sl[4];
         T xi[4][4];
@@ -187,15 +233,197 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
             if (sl[v] < 0) continue;
             for (int k = 0; k < 3; ++k)
                 for (int a = 0; a < 4; ++a)
-                    atomicAdd(A.g + 12 * (int64_t)sl[v] + qidx(k, a), w * gx[3 * v + k] * (double)xbv[v][a]);
+                    atomicAdd(A.g + 12 * (int64_t)sl[v] + qidx(k, a), w * gx[3 * v + k] * xbv[v][a]);
         }
-        // slot-pair blocks: (sa, sa), (sb, sb), (min, max)
+        // slot sides: PT = {point} | {triangle}, EE = {edge a} | {edge b}
+        const int nA = ee ? 2 : 1;
         int ss[2] = {sa < A.S_dyn ? sa : -1, sb < A.S_dyn ? sb : -1};
+        if (!full_path) {
+            // exact low-rank projection: PSD(H) = B PSD(K) B^T, J^T PSD(H) J = P_s K+ P_t^T
+            T K[25], wh[4], chat[2][4], rh[3];
+            int n = pair_hessian_lowrank<T>(ee, X, PG, T(d), T(A.kB), K, wh, chat, rh);
+            psd_small<T>(K, n);
+            // pull-backs of the basis to each side: om[a] = sum_v w^_v xi_v, ga[j] = sum_v c^_jv xi_v
+            T om[2][4], ga[2][2][4];
+            for (int sd = 0; sd < 2; ++sd)
+                for (int a = 0; a < 4; ++a) {
+                    om[sd][a] = T(0); ga[sd][0][a] = T(0); ga[sd][1][a] = T(0);
+                    for (int v = sd ? nA : 0; v < (sd ? 4 : nA); ++v) {
+                        om[sd][a] += wh[v] * xi[v][a];
+                        ga[sd][0][a] += chat[0][v] * xi[v][a];
+                        ga[sd][1][a] += chat[1][v] * xi[v][a];
+                    }
+                }
+            for (int bi = 0; bi < 2; ++bi)
+                for (int bj = bi; bj < 2; ++bj) {
+                    int s1 = ss[bi], s2 = ss[bj];
+                    if (s1 < 0 || s2 < 0) continue;
+                    T *dst;
+                    bool tr = false;
+                    if (bi == bj) dst = diag + 144 * (int64_t)s1;
+                    else {
+                        int2 lp = l1[r.l1];
+                        dst = off + 144 * (int64_t)r.l1;
+                        tr = (lp.x != s1);
+                        if (atomicExch(&offflag[r.l1], 1) == 0) {
+                            atomicAdd(&A.rowcnt[lp.x], 1);
+                            atomicAdd(&A.rowcnt[lp.y], 1);
+                        }
+                    }
+                    // column by column: m = K P_t^T e_col, then the 12 rows P_s m
+                    for (int l = 0; l < 3; ++l)
+                        for (int be = 0; be < 4; ++be) {
+                            int col = qidx(l, be);
+                            T mc[5];
+                            for (int c = 0; c < 5; ++c) {
+                                T acc = c < n ? K[c * 5 + l] * om[bj][be] : T(0);
+                                for (int j = 0; j < 2; ++j)
+                                    if (3 + j < n && c < n) acc += K[c * 5 + 3 + j] * rh[l] * ga[bj][j][be];
+                                mc[c] = acc;
+                            }
+                            for (int kk = 0; kk < 3; ++kk)
+                                for (int al = 0; al < 4; ++al) {
+                                    int row = qidx(kk, al);
+                                    T v = om[bi][al] * mc[kk];
+                                    for (int j = 0; j < 2; ++j)
+                                        if (3 + j < n) v += rh[kk] * ga[bi][j][al] * mc[3 + j];
+                                    v *= T(w);
+                                    if (v != T(0)) atomic_addT(dst + (tr ? col * 12 + row : row * 12 + col), v);
+                                }
+                        }
+                }
+            continue;
+        }
+    }
+}
+
+// Warp-cooperative PSD projection of a symmetric 12x12 matrix held in shared
+// memory: cyclic Jacobi where lane k applies each rotation to row and column
+// k (lanes 16..27 update the eigenvectors), then negative eigenvalues are
+// clamped and the matrix rebuilt.  H is left unchanged when no eigenvalue is
+// negative.  W and V are 144-entry work arrays.
+template <class T>
+__device__ void warp_psd12(T *H, T *W, T *V, int lane) {
+    for (int i = lane; i < 144; i += 32) {
+        W[i] = H[i];
+        V[i] = (i % 13 == 0) ? T(1) : T(0);
+    }
+    __syncwarp();
+    const T tol = sizeof(T) == 8 ? T(1e-30) : T(1e-10);
+    for (int sweep = 0; sweep < (sizeof(T) == 8 ? 30 : 10); ++sweep) {
+        T off = T(0), tot = T(0);
+        for (int i = lane; i < 144; i += 32) {
+            T a2 = W[i] * W[i];
+            tot += a2;
+            if (i / 12 != i % 12) off += a2;
+        }
+        for (int o = 16; o; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
+        if (off <= tol * tot || off == T(0)) break;
+        for (int p = 0; p < 11; ++p)
+            for (int q = p + 1; q < 12; ++q) {
+                T apq = W[p * 12 + q];
+                if (apq == T(0)) continue;
+                T theta = (W[q * 12 + q] - W[p * 12 + p]) / (T(2) * apq);
+                T t = (theta >= T(0) ? T(1) : T(-1)) / (tabs(theta) + tsqrt(theta * theta + T(1)));
+                T c = T(1) / tsqrt(t * t + T(1)), sn = t * c;
+                __syncwarp();
+                if (lane < 12) {
+                    T akp = W[lane * 12 + p], akq = W[lane * 12 + q];
+                    W[lane * 12 + p] = c * akp - sn * akq;
+                    W[lane * 12 + q] = sn * akp + c * akq;
+                }
+                __syncwarp();
+                if (lane < 12) {
+                    T apk = W[p * 12 + lane], aqk = W[q * 12 + lane];
+                    W[p * 12 + lane] = c * apk - sn * aqk;
+                    W[q * 12 + lane] = sn * apk + c * aqk;
+                } else if (lane >= 16 && lane < 28) {
+                    int k = lane - 16;
+                    T vkp = V[k * 12 + p], vkq = V[k * 12 + q];
+                    V[k * 12 + p] = c * vkp - sn * vkq;
+                    V[k * 12 + q] = sn * vkp + c * vkq;
+                }
+                __syncwarp();
+            }
+    }
+    bool neg = __any_sync(0xffffffffu, lane < 12 && W[lane * 13] < T(0));
+    if (!neg) return;
+    __syncwarp();
+    for (int i = lane; i < 144; i += 32) {
+        int r = i / 12, c = i % 12;
+        T acc = T(0);
+        for (int k = 0; k < 12; ++k) {
+            T lam = W[k * 13];
+            if (lam > T(0)) acc += V[r * 12 + k] * lam * V[c * 12 + k];
+        }
+        H[i] = acc;
+    }
+    __syncwarp();
+}
+
+// Mollified edge-edge pairs deferred by k_pair_assemble: one warp per pair.
+// Lane 0 evaluates the FP64 gradient and the raw 12x12 Hessian (T), the warp
+// projects it to PSD and scatters J^T H J and the gradient onto the slots.
+template <class T>
+__global__ void __launch_bounds__(128) k_pair_moll(AsmArgs A, const PairRec *__restrict__ act,
+                                                   const int64_t *__restrict__ deferred,
+                                                   const unsigned long long *__restrict__ n_def, int64_t cap,
+                                                   const int2 *__restrict__ l1, T *__restrict__ diag,
+                                                   T *__restrict__ off, int *__restrict__ offflag) {
+    __shared__ T sH[4][144], sW[4][144], sV[4][144];
+    __shared__ double sg[4][12], sw[4];
+    __shared__ T sxi[4][4][4];
+    __shared__ int ssl[4][4], sok[4];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t n = min((int64_t)*n_def, cap);
+    for (int64_t ii = (int64_t)blockIdx.x * 4 + wib; ii < n; ii += (int64_t)gridDim.x * 4) {
+        const PairRec r = act[deferred[ii]];
+        if (lane == 0) {
+            int sa, sb;
+            pair_slots(r, A.sv_slot, sa, sb);
+            bool ee = r.flags & 1;
+            double Xd[12];
+            for (int v = 0; v < 4; ++v)
+                for (int k = 0; k < 3; ++k) Xd[3 * v + k] = A.x[3 * (int64_t)r.v[v] + k] - A.x[3 * (int64_t)r.v[0] + k];
+            PairGrad PG;
+            double d = pair_gradient(ee, Xd, A.dhat, A.kB, r.eps, PG, sg[wib]);
+            sok[wib] = (d < A.dhat) && (d > 0.0);
+            if (sok[wib]) {
+                T X[12];
+                for (int e = 0; e < 12; ++e) X[e] = T(Xd[e]);
+                pair_hessian<T>(ee, X, PG, T(d), T(A.kB), T(r.eps), sH[wib]);
+                sw[wib] = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
+                for (int v = 0; v < 4; ++v) {
+                    int s = A.sv_slot[r.v[v]];
+                    ssl[wib][v] = s < A.S_dyn ? s : -1;
+                    int b = A.slot_body[s];
+                    const double *xb = A.xbar + 3 * ((int64_t)A.voff[b] + (r.v[v] - A.slot_voff[s]));
+                    sxi[wib][v][0] = T(1); sxi[wib][v][1] = T(xb[0]); sxi[wib][v][2] = T(xb[1]); sxi[wib][v][3] = T(xb[2]);
+                }
+            }
+        }
+        __syncwarp();
+        if (!sok[wib]) continue;
+        warp_psd12<T>(sH[wib], sW[wib], sV[wib], lane);
+        const double w = sw[wib];
+        const int *sl = ssl[wib];
+        // gradient: 4 vertices x 3 components x 4 xi entries
+        for (int e = lane; e < 48; e += 32) {
+            int v = e / 12, k = (e / 4) % 3, a = e % 4;
+            if (sl[v] < 0) continue;
+            double xa = a == 0 ? 1.0 : (double)sxi[wib][v][a];
+            atomicAdd(A.g + 12 * (int64_t)sl[v] + qidx(k, a), w * sg[wib][3 * v + k] * xa);
+        }
+        int sa = sl[0] >= 0 ? sl[0] : -1;
+        int sb = sl[(r.flags & 1) ? 2 : 1];
+        int ss[2] = {sa, sb};
         for (int bi = 0; bi < 2; ++bi)
             for (int bj = bi; bj < 2; ++bj) {
                 int s1 = ss[bi], s2 = ss[bj];
-                if (s1 < 0 || s2 < 0) continue;
-                if (bi != bj && s1 == s2) continue;
+                if (s1 < 0 || s2 < 0 || (bi != bj && s1 == s2)) continue;
                 T *dst;
                 bool tr = false;
                 if (bi == bj) dst = diag + 144 * (int64_t)s1;
@@ -203,29 +431,77 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
                     int2 lp = l1[r.l1];
                     dst = off + 144 * (int64_t)r.l1;
                     tr = (lp.x != s1);
-                    offflag[r.l1] = 1;
-                }
-                T acc[144];
-                for (int e = 0; e < 144; ++e) acc[e] = T(0);
-                for (int v = 0; v < 4; ++v) {
-                    if (sl[v] != s1) continue;
-                    for (int u = 0; u < 4; ++u) {
-                        if (sl[u] != s2) continue;
-                        for (int k = 0; k < 3; ++k)
-                            for (int l = 0; l < 3; ++l) {
-                                T hv = H[(3 * v + k) * 12 + 3 * u + l];
-                                if (hv == T(0)) continue;
-                                for (int a = 0; a < 4; ++a)
-                                    for (int c = 0; c < 4; ++c) acc[qidx(k, a) * 12 + qidx(l, c)] += hv * xi[v][a] * xi[u][c];
-                            }
+                    if (lane == 0 && atomicExch(&offflag[r.l1], 1) == 0) {
+                        atomicAdd(&A.rowcnt[lp.x], 1);
+                        atomicAdd(&A.rowcnt[lp.y], 1);
                     }
                 }
-                for (int rr = 0; rr < 12; ++rr)
-                    for (int cc = 0; cc < 12; ++cc) {
-                        T val = T(w) * acc[rr * 12 + cc];
-                        if (val != T(0)) atomic_addT(dst + (tr ? cc * 12 + rr : rr * 12 + cc), val);
+                for (int e = lane; e < 144; e += 32) {
+                    int row = e / 12, col = e % 12;
+                    int k = row < 3 ? row : (row - 3) / 3, a = row < 3 ? 0 : 1 + (row - 3) % 3;
+                    int l = col < 3 ? col : (col - 3) / 3, c = col < 3 ? 0 : 1 + (col - 3) % 3;
+                    T acc = T(0);
+                    for (int v = 0; v < 4; ++v) {
+                        if (sl[v] != s1) continue;
+                        for (int u = 0; u < 4; ++u) {
+                            if (sl[u] != s2) continue;
+                            acc += sH[wib][(3 * v + k) * 12 + 3 * u + l] * sxi[wib][v][a] * sxi[wib][u][c];
+                        }
                     }
+                    T val = T(w) * acc;
+                    if (val != T(0)) atomic_addT(dst + (tr ? col * 12 + row : row * 12 + col), val);
+                }
             }
+        __syncwarp();
+    }
+}
+
+// Zero the off-diagonal blocks and flags of the first min(count, cap) level-1 pairs.
+template <class T>
+__global__ void k_zero_off(T *__restrict__ off, int *__restrict__ flag, const unsigned long long *__restrict__ n_dev,
+                           int64_t cap) {
+    int64_t n = min((int64_t)*n_dev, cap);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 144 * n; e += (int64_t)gridDim.x * blockDim.x) {
+        off[e] = T(0);
+        if (e % 144 == 0) flag[e / 144] = 0;
+    }
+}
+
+// Exclusive scan of the per-slot block counts (one block of 1024 threads).
+__global__ void k_csr_scan(int n, const int *__restrict__ cnt, int *__restrict__ off) {
+    __shared__ int part[1024];
+    int t = threadIdx.x, per = (n + 1023) / 1024, b = t * per, e = min(n, b + per);
+    int loc = 0;
+    for (int i = b; i < e; ++i) loc += cnt[i];
+    part[t] = loc;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        int v = t >= o ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - loc;
+    for (int i = b; i < e; ++i) {
+        off[i] = run;
+        run += cnt[i];
+    }
+    if (t == 1023) off[n] = part[1023];
+}
+
+// Row CSR of the off-diagonal blocks: each flagged level-1 pair (a, b) is an
+// entry (b, k) of row a and (a, k | transposed) of row b.
+__global__ void k_csr_fill(const unsigned long long *__restrict__ n_dev, int64_t cap, const int2 *__restrict__ l1,
+                           const int *__restrict__ flag, const int *__restrict__ off, int *__restrict__ cur,
+                           int2 *__restrict__ ent) {
+    int64_t n = min((int64_t)*n_dev, cap);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[k]) continue;
+        int2 lp = l1[k];
+        int pa = off[lp.x] + atomicAdd(&cur[lp.x], 1);
+        ent[pa] = make_int2(lp.y, (int)k);
+        int pb = off[lp.y] + atomicAdd(&cur[lp.y], 1);
+        ent[pb] = make_int2(lp.x, (int)k | (int)0x80000000);
     }
 }
 
@@ -257,10 +533,12 @@ __global__ void k_vp_assemble(AsmArgs A, int64_t SVd, T *__restrict__ diag) {
 // CCD over swept candidates: min TOI per partition; pairs that can come within
 // dhat somewhere on the path (d0 - l_p < dhat, l_p bounding the distance
 // change) go to the line-search list.
-__global__ void k_ccd(const PairRec *__restrict__ cand, int64_t n, const double *__restrict__ x0,
+__global__ void k_ccd(const PairRec *__restrict__ cand, int64_t n, const unsigned long long *__restrict__ n_dev,
+                      const double *__restrict__ x0,
                       const double *__restrict__ x1, const int *__restrict__ sv_slot, const int *__restrict__ slot_part,
                       int S_dyn, double dhat, double s_, double c_, PartState *__restrict__ part,
                       PairRec *__restrict__ ls, int64_t cap, unsigned long long *__restrict__ count, int want_ls) {
+    if (n_dev) n = min((int64_t)*n_dev, n);
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = base + threadIdx.x;
         bool keep = false;
@@ -382,6 +660,7 @@ __global__ void k_energy_slots(EnArgs A) {
         int s = base + threadIdx.x;
         int p = s < A.S_dyn ? A.slot_part[s] : -1;
         if (p >= 0 && !A.part[p].active) p = -1;
+        if (p >= 0 && A.alphas[(kLS + 1) * p] < 0.0) p = -1;  // partition already decided
         for (int j = 0; j <= kLS; ++j) {
             double al = p >= 0 ? A.alphas[(kLS + 1) * p + j] : -1.0;
             bool use = p >= 0 && (j == 0 || al >= 0.0);
@@ -391,7 +670,9 @@ __global__ void k_energy_slots(EnArgs A) {
     }
 }
 
-__global__ void k_energy_pairs(EnArgs A, const PairRec *__restrict__ ls, int64_t n) {
+__global__ void k_energy_pairs(EnArgs A, const PairRec *__restrict__ ls, int64_t n,
+                               const unsigned long long *__restrict__ n_dev) {
+    if (n_dev) n = min((int64_t)*n_dev, n);
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = base + threadIdx.x;
         int p = -1;
@@ -402,7 +683,7 @@ __global__ void k_energy_pairs(EnArgs A, const PairRec *__restrict__ ls, int64_t
             int sa, sb;
             pair_slots(r, A.sv_slot, sa, sb);
             p = pair_part(sa, sb, A.S_dyn, A.slot_part);
-            if (!A.part[p].active) p = -1;
+            if (!A.part[p].active || A.alphas[(kLS + 1) * p] < 0.0) p = -1;
             w = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
             for (int v = 0; v < 4; ++v)
                 for (int k = 0; k < 3; ++k) {
@@ -432,7 +713,7 @@ __global__ void k_energy_vp(EnArgs A, int64_t SVd) {
         if (i < SVd) {
             s = A.sv_slot[i];
             p = A.slot_part[s];
-            if (!A.part[p].active) p = -1;
+            if (!A.part[p].active || A.alphas[(kLS + 1) * p] < 0.0) p = -1;
         }
         double w = p >= 0 ? A.h * A.h / (double)__popcll(A.slot_mask[s]) * A.kB : 0.0;
         for (int j = 0; j <= kLS; ++j) {
@@ -465,7 +746,7 @@ namespace abd {
 
 static AsmArgs make_asm(abd_scene *s, const abd_step_params *p, double kB) {
     World &w = s->w;
-    AsmArgs A;
+    AsmArgs A = {};
     A.S_dyn = w.S_dyn;
     A.slot_body = P<int>(w.slot_body); A.slot_part = P<int>(w.slot_part); A.slot_rep = P<int>(w.slot_rep);
     A.sv_slot = P<int>(w.sv_slot); A.slot_mask = P<unsigned long long>(w.slot_mask); A.slot_kw = P<double>(w.slot_kw);
@@ -476,118 +757,82 @@ static AsmArgs make_asm(abd_scene *s, const abd_step_params *p, double kB) {
     A.h = p->h; A.dhat = p->dhat; A.kB = kB; A.planes = s->planes;
     A.slot_voff = P<int64_t>(w.slot_voff);
     A.g = P<double>(w.g);
+    A.rowcnt = P<int>(w.rowcnt);
     return A;
 }
 
-static int read_u64(abd_scene *s, unsigned long long *d, unsigned long long *h) {
-    cudaError_t e = cudaMemcpyAsync(h, d, 8, cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    return cuda_check(s, e, "read counter");
-}
-
-int launch_narrow(abd_scene *s, int64_t n_cand, double dhat, int64_t *n_act) {
+// ---------------------------------------------------------------------------
+// Asynchronous launchers (device counts, capacity-clamped; see abd_broad.cu).
+// ---------------------------------------------------------------------------
+int launch_narrow_async(abd_scene *s, const PairRec *src, const unsigned long long *src_n, int64_t src_cap,
+                        double dhat) {
     World &w = s->w;
     Counters *c = P<Counters>(w.ctr);
-    if (w.cap_act == 0) {
-        w.cap_act = 1 << 14;
-        if (!dbuf_ensure(w.act, sizeof(PairRec) * w.cap_act)) return set_err(s, ABD_E_OOM, "active list");
-    }
-    for (;;) {
-        cudaMemsetAsync(&c->act, 0, 8, s->stream);
-        if (n_cand > 0)
-            ABD_LAUNCH(s, k_narrow, grid_for(n_cand, 256), 256, 0, s->stream, P<PairRec>(w.cand), n_cand, P<double>(w.x), dhat,
-                                                                  P<PairRec>(w.act), w.cap_act, &c->act);
-        int rc = cuda_check(s, cudaGetLastError(), "k_narrow");
-        if (rc) return rc;
-        unsigned long long n = 0;
-        if ((rc = read_u64(s, &c->act, &n))) return rc;
-        if ((int64_t)n <= w.cap_act) {
-            *n_act = (int64_t)n;
-            return ABD_OK;
-        }
-        w.cap_act = (int64_t)n + n / 2 + 1024;
-        if (!dbuf_ensure(w.act, sizeof(PairRec) * w.cap_act)) return set_err(s, ABD_E_OOM, "active list");
-    }
+    cudaMemsetAsync(&c->act, 0, 8, s->stream);
+    ABD_LAUNCH(s, k_narrow, grid_for(src_cap, 256, 152 * 8), 256, 0, s->stream, src, src_cap, src_n, P<double>(w.x),
+               dhat, P<PairRec>(w.act), w.cap_act, &c->act);
+    return cuda_check(s, cudaGetLastError(), "k_narrow");
 }
 
 template <class T>
-static int assemble_T(abd_scene *s, const abd_step_params *p, double kB, int64_t n_act, int64_t n_l1) {
+static int assemble_async_T(abd_scene *s, const abd_step_params *p, double kB) {
     World &w = s->w;
+    Counters *c = P<Counters>(w.ctr);
     AsmArgs A = make_asm(s, p, kB);
-    if (!dbuf_ensure(w.diag, sizeof(T) * 144 * (size_t)(w.S_dyn ? w.S_dyn : 1))) return set_err(s, ABD_E_OOM, "diag");
-    if (!dbuf_ensure(w.off, sizeof(T) * 144 * (size_t)(n_l1 ? n_l1 : 1)) ||
-        !dbuf_ensure(w.offflag, sizeof(int) * (size_t)(n_l1 ? n_l1 : 1)))
-        return set_err(s, ABD_E_OOM, "off-diagonal blocks");
-    if (n_l1 > 0) {
-        cudaMemsetAsync(w.off.p, 0, sizeof(T) * 144 * (size_t)n_l1, s->stream);
-        cudaMemsetAsync(w.offflag.p, 0, sizeof(int) * (size_t)n_l1, s->stream);
-    }
+    cudaMemsetAsync(w.rowcnt.p, 0, sizeof(int) * (size_t)(w.S_dyn + 1), s->stream);
+    cudaMemsetAsync(w.rowcur.p, 0, sizeof(int) * (size_t)(w.S_dyn + 1), s->stream);
+    ABD_LAUNCH(s, k_zero_off<T>, grid_for(144 * w.cap_l1, 256, 152 * 8), 256, 0, s->stream, P<T>(w.off),
+               P<int>(w.offflag), &c->l1, w.cap_l1);
     cudaEvent_t ea, eb;
     if (w.S_dyn > 0) {
-        // q, q~, z, u, S in; g and the diagonal block out
         prof_begin(s, "slot_assemble", (double)w.S_dyn * (4 * 96 + 72 + 96 + 144.0 * sizeof(T)), &ea, &eb);
         ABD_LAUNCH(s, k_slot_assemble<T>, grid_for(w.S_dyn, 128), 128, 0, s->stream, A, P<T>(w.diag));
         prof_end(s, ea, eb, prof_index(s, "slot_assemble"));
     }
-    if (n_act > 0) {
-        // record, 4 positions, 4 rest positions in; three 12x12 blocks and two
-        // 12-vectors read-modify-written
-        prof_begin(s, "pair_assemble", (double)n_act * (32 + 96 + 96 + 2.0 * (3 * 144 * sizeof(T) + 2 * 96)), &ea,
-                   &eb);
-        ABD_LAUNCH(s, k_pair_assemble<T>, grid_for(n_act, 64), 64, 0, s->stream, A, P<PairRec>(w.act), n_act, P<int2>(w.l1),
-                                                                      P<T>(w.diag), P<T>(w.off), P<int>(w.offflag));
-        prof_end(s, ea, eb, prof_index(s, "pair_assemble"));
-    }
+    int64_t *defl = P<int64_t>(w.deferred);
+    unsigned long long *ndef = (unsigned long long *)(defl + w.cap_act);
+    cudaMemsetAsync(ndef, 0, 8, s->stream);
+    prof_begin(s, "pair_assemble", 0.0, &ea, &eb);
+    ABD_LAUNCH(s, (k_pair_assemble<T, false>), grid_for(w.cap_act, 128, 152 * 8), 128, 0, s->stream, A,
+               P<PairRec>(w.act), w.cap_act, P<int2>(w.l1), P<T>(w.diag), P<T>(w.off), P<int>(w.offflag), defl, ndef,
+               &c->act);
+    prof_end(s, ea, eb, prof_index(s, "pair_assemble"));
+    ABD_LAUNCH(s, k_pair_moll<T>, 38, 128, 0, s->stream, A, P<PairRec>(w.act), defl, ndef, w.cap_act, P<int2>(w.l1),
+               P<T>(w.diag), P<T>(w.off), P<int>(w.offflag));
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
     if (s->planes.n > 0 && SVd > 0)
         ABD_LAUNCH(s, k_vp_assemble<T>, grid_for(SVd, 256), 256, 0, s->stream, A, SVd, P<T>(w.diag));
+    ABD_LAUNCH(s, k_csr_scan, 1, 1024, 0, s->stream, w.S_dyn, P<int>(w.rowcnt), P<int>(w.rowoff));
+    ABD_LAUNCH(s, k_csr_fill, grid_for(w.cap_l1, 256, 152 * 8), 256, 0, s->stream, &c->l1, w.cap_l1, P<int2>(w.l1),
+               P<int>(w.offflag), P<int>(w.rowoff), P<int>(w.rowcur), P<int2>(w.ent));
     return cuda_check(s, cudaGetLastError(), "assemble");
 }
 
-int launch_assemble(abd_scene *s, int precision, const abd_step_params *p, double kB, int64_t n_act, int64_t n_l1) {
-    return precision == ABD_MIXED ? assemble_T<float>(s, p, kB, n_act, n_l1) : assemble_T<double>(s, p, kB, n_act, n_l1);
+int launch_assemble_async(abd_scene *s, int precision, const abd_step_params *p, double kB) {
+    return precision == ABD_MIXED ? assemble_async_T<float>(s, p, kB) : assemble_async_T<double>(s, p, kB);
 }
 
-int launch_ccd(abd_scene *s, int64_t n_sw, const abd_step_params *p, double dhat, int64_t *n_ls, bool want_ls) {
+int launch_ccd_async(abd_scene *s, const abd_step_params *p, bool want_ls) {
     World &w = s->w;
     Counters *c = P<Counters>(w.ctr);
-    if (w.cap_ls == 0) {
-        w.cap_ls = 1 << 14;
-        if (!dbuf_ensure(w.ls, sizeof(PairRec) * w.cap_ls)) return set_err(s, ABD_E_OOM, "line-search list");
-    }
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
-    for (;;) {
-        cudaMemsetAsync(&c->ls, 0, 8, s->stream);
-        cudaEvent_t ea, eb;
-        if (n_sw > 0) {
-            // record and both configurations of its four vertices
-            prof_begin(s, "ccd", (double)n_sw * (32 + 4 * 48), &ea, &eb);
-            ABD_LAUNCH(s, k_ccd, grid_for(n_sw, 128), 128, 0, s->stream, P<PairRec>(w.cand), n_sw, P<double>(w.x),
-                                                             P<double>(w.x1), P<int>(w.sv_slot), P<int>(w.slot_part),
-                                                             w.S_dyn, dhat, p->accd_s, p->accd_c, P<PartState>(w.part),
-                                                             P<PairRec>(w.ls), w.cap_ls, &c->ls, want_ls ? 1 : 0);
-            prof_end(s, ea, eb, prof_index(s, "ccd"));
-        }
-        if (s->planes.n > 0 && SVd > 0)
-            ABD_LAUNCH(s, k_vp_ccd, grid_for(SVd, 256), 256, 0, s->stream, SVd, P<double>(w.x), P<double>(w.x1), P<int>(w.sv_slot),
-                                                                P<int>(w.slot_part), s->planes, p->accd_s,
-                                                                P<PartState>(w.part));
-        int rc = cuda_check(s, cudaGetLastError(), "k_ccd");
-        if (rc) return rc;
-        unsigned long long n = 0;
-        if ((rc = read_u64(s, &c->ls, &n))) return rc;
-        if (!want_ls || (int64_t)n <= w.cap_ls) {
-            *n_ls = (int64_t)n;
-            return ABD_OK;
-        }
-        w.cap_ls = (int64_t)n + n / 2 + 1024;
-        if (!dbuf_ensure(w.ls, sizeof(PairRec) * w.cap_ls)) return set_err(s, ABD_E_OOM, "line-search list");
-    }
+    cudaMemsetAsync(&c->ls, 0, 8, s->stream);
+    cudaEvent_t ea, eb;
+    prof_begin(s, "ccd", 0.0, &ea, &eb);
+    ABD_LAUNCH(s, k_ccd, grid_for(w.cap_cand, 128, 152 * 8), 128, 0, s->stream, P<PairRec>(w.cand), w.cap_cand, &c->cand,
+               P<double>(w.x), P<double>(w.x1), P<int>(w.sv_slot), P<int>(w.slot_part), w.S_dyn, p->dhat, p->accd_s,
+               p->accd_c, P<PartState>(w.part), P<PairRec>(w.ls), w.cap_ls, &c->ls, want_ls ? 1 : 0);
+    prof_end(s, ea, eb, prof_index(s, "ccd"));
+    if (s->planes.n > 0 && SVd > 0)
+        ABD_LAUNCH(s, k_vp_ccd, grid_for(SVd, 256), 256, 0, s->stream, SVd, P<double>(w.x), P<double>(w.x1),
+                   P<int>(w.sv_slot), P<int>(w.slot_part), s->planes, p->accd_s, P<PartState>(w.part));
+    return cuda_check(s, cudaGetLastError(), "k_ccd");
 }
 
-int launch_energy(abd_scene *s, const abd_step_params *p, double kB, int64_t n_ls, const double *alphas_dev) {
+int launch_energy_async(abd_scene *s, const abd_step_params *p, double kB, const double *alphas_dev) {
     World &w = s->w;
-    EnArgs A;
+    Counters *c = P<Counters>(w.ctr);
+    EnArgs A = {};
     A.S_dyn = w.S_dyn;
     A.slot_body = P<int>(w.slot_body); A.slot_part = P<int>(w.slot_part); A.slot_rep = P<int>(w.slot_rep);
     A.sv_slot = P<int>(w.sv_slot); A.slot_mask = P<unsigned long long>(w.slot_mask); A.slot_kw = P<double>(w.slot_kw);
@@ -599,7 +844,8 @@ int launch_energy(abd_scene *s, const abd_step_params *p, double kB, int64_t n_l
     A.h = p->h; A.dhat = p->dhat; A.kB = kB; A.planes = s->planes;
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
     if (w.S_dyn > 0) ABD_LAUNCH(s, k_energy_slots, grid_for(w.S_dyn, 128), 128, 0, s->stream, A);
-    if (n_ls > 0) ABD_LAUNCH(s, k_energy_pairs, grid_for(n_ls, 128), 128, 0, s->stream, A, P<PairRec>(w.ls), n_ls);
+    ABD_LAUNCH(s, k_energy_pairs, grid_for(w.cap_ls, 128, 152 * 8), 128, 0, s->stream, A, P<PairRec>(w.ls), w.cap_ls,
+               &c->ls);
     if (s->planes.n > 0 && SVd > 0) ABD_LAUNCH(s, k_energy_vp, grid_for(SVd, 128), 128, 0, s->stream, A, SVd);
     return cuda_check(s, cudaGetLastError(), "energy");
 }

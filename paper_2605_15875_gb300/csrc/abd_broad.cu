@@ -175,7 +175,9 @@ __global__ void __launch_bounds__(32 * kL2Warps) k_l2(L2Args A) {
     __shared__ int st_idx[kL2Warps][kStage];
     int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int gw = blockIdx.x * kL2Warps + wib, nw = gridDim.x * kL2Warps;
-    for (int64_t p = gw; p < A.n_l1; p += nw) {
+    int64_t npairs = A.n_l1;
+    if (A.n_l1_dev) npairs = min((int64_t)*A.n_l1_dev, A.n_l1);
+    for (int64_t p = gw; p < npairs; p += nw) {
         int2 pr = A.l1[p];
         double boxS[2][6];
         for (int k = 0; k < 6; ++k) { boxS[0][k] = A.box[6 * (int64_t)pr.x + k]; boxS[1][k] = A.box[6 * (int64_t)pr.y + k]; }
@@ -269,6 +271,233 @@ __global__ void __launch_bounds__(32 * kL2Warps) k_l2(L2Args A) {
     }
 }
 
+// One warp per primitive cluster: box of its (up to 32) primitives' vertices
+// over x0 (and x1), inflated by half.  It contains every primitive box of the
+// cluster, so it filters exactly.
+__global__ void k_cluster_boxes(int64_t C, const int2 *__restrict__ cl_info, const int *__restrict__ slot_body,
+                                const int64_t *__restrict__ slot_voff, const int *__restrict__ nv,
+                                const int *__restrict__ toff, const int *__restrict__ nt, const int *__restrict__ eoff,
+                                const int *__restrict__ ne, const int *__restrict__ voff, const int *__restrict__ tri,
+                                const int *__restrict__ edge, const int *__restrict__ vperm,
+                                const int *__restrict__ tperm, const int *__restrict__ eperm,
+                                const double *__restrict__ x0, const double *__restrict__ x1, double half,
+                                double *__restrict__ cbox) {
+    int lane = threadIdx.x & 31;
+    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < C;
+         c += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int2 info = cl_info[c];
+        int slot = info.x, kind = info.y >> 24, j = info.y & 0xffffff;
+        int b = slot_body[slot];
+        int64_t base = slot_voff[slot];
+        int n = kind == 0 ? nv[b] : (kind == 1 ? nt[b] : ne[b]);
+        int i = kClusterSize * j + lane;
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        if (i < n) {
+            int sv[3], k = 0;
+            if (kind == 0) sv[k++] = (int)(base + vperm[voff[b] + i]);
+            else if (kind == 1) {
+                const int *t = tri + 3 * ((int64_t)toff[b] + tperm[toff[b] + i]);
+                sv[0] = (int)(base + t[0]); sv[1] = (int)(base + t[1]); sv[2] = (int)(base + t[2]);
+                k = 3;
+            } else {
+                const int *e = edge + 2 * ((int64_t)eoff[b] + eperm[eoff[b] + i]);
+                sv[0] = (int)(base + e[0]); sv[1] = (int)(base + e[1]);
+                k = 2;
+            }
+            for (int q = 0; q < k; ++q)
+                for (int a = 0; a < 3; ++a) {
+                    double v = x0[3 * (int64_t)sv[q] + a];
+                    lo[a] = fmin(lo[a], v);
+                    hi[a] = fmax(hi[a], v);
+                    if (x1) {
+                        double u = x1[3 * (int64_t)sv[q] + a];
+                        lo[a] = fmin(lo[a], u);
+                        hi[a] = fmax(hi[a], u);
+                    }
+                }
+        }
+        for (int o = 16; o; o >>= 1)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = fmin(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+                hi[a] = fmax(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+            }
+        if (lane < 3) cbox[6 * c + lane] = lo[lane] - half;
+        else if (lane < 6) cbox[6 * c + lane] = hi[lane - 3] + half;
+    }
+}
+
+__device__ __forceinline__ int cl_count(const L2Args &A, int kind, int body) {
+    int n = kind == 0 ? A.nv[body] : (kind == 1 ? A.nt[body] : A.ne[body]);
+    return (n + kClusterSize - 1) / kClusterSize;
+}
+
+__device__ __forceinline__ int cl_first(const L2cArgs &A, int kind, int slot, int body) {
+    int c = A.slot_cbase[slot];
+    if (kind >= 1) c += cl_count(A.a, 0, body);
+    if (kind >= 2) c += cl_count(A.a, 1, body);
+    return c;
+}
+
+__device__ __forceinline__ int cl_prim(const L2cArgs &A, int kind, int body, int i) {
+    return kind == 0 ? A.vperm[A.a.voff[body] + i] : (kind == 1 ? A.tperm[A.a.toff[body] + i] : A.eperm[A.a.eoff[body] + i]);
+}
+
+// Test the staged side-1 primitives against every side-2 primitive of the
+// side-2 clusters that meet both the side-1 slot box and the staged set's box;
+// emit the hits (ballot-compacted).
+__device__ void l2c_flush(const L2cArgs &A, int64_t p, int job, int s1, int s2, int k1, int k2, int b2,
+                          const double *box1, const double *stbox, const double (*st_box)[6], const int *st_idx,
+                          int nst, int lane) {
+    const L2Args &B = A.a;
+    int n2 = k2 == 0 ? B.nv[b2] : (k2 == 1 ? B.nt[b2] : B.ne[b2]);
+    int nc2 = (n2 + kClusterSize - 1) / kClusterSize, cb2 = cl_first(A, k2, s2, b2);
+    for (int cbk = 0; cbk < nc2; cbk += 32) {
+        int c = cbk + lane;
+        bool ok = false;
+        if (c < nc2) {
+            const double *cbx = A.cbox + 6 * (int64_t)(cb2 + c);
+            ok = overlap6(cbx, box1) && overlap6(cbx, stbox);
+        }
+        unsigned m = __ballot_sync(0xffffffffu, ok);
+        while (m) {
+            int cc = cbk + __ffs(m) - 1;
+            m &= m - 1;
+            int i2 = kClusterSize * cc + lane;
+            bool keep = false;
+            double bx[6];
+            int idx2 = -1, sv2[3];
+            if (i2 < n2) {
+                idx2 = cl_prim(A, k2, b2, i2);
+                int nv2 = prim_verts(B, k2, s2, idx2, sv2);
+                prim_box(B, sv2, nv2, bx);
+                keep = overlap6(bx, box1) && overlap6(bx, stbox);
+            }
+            if (!__any_sync(0xffffffffu, keep)) continue;
+            for (int k = 0; k < nst; ++k) {
+                bool hit = keep && overlap6(bx, st_box[k]);
+                unsigned hm = __ballot_sync(0xffffffffu, hit);
+                if (!hm) continue;
+                unsigned long long pos = 0;
+                int leader = __ffs(hm) - 1;
+                if (lane == leader) pos = atomicAdd(B.count, (unsigned long long)__popc(hm));
+                pos = __shfl_sync(0xffffffffu, pos, leader);
+                if (!hit) continue;
+                unsigned long long my = pos + __popc(hm & ((1u << lane) - 1));
+                if ((int64_t)my >= B.cap) continue;
+                int idx1 = st_idx[k];
+                int sv1[3];
+                prim_verts(B, k1, s1, idx1, sv1);
+                int b1 = B.slot_body[s1];
+                if (B.mode == 0) {
+                    int32_t *o = B.out3 + 3 * my;
+                    if (job < 2) {
+                        o[0] = 0;
+                        o[1] = B.voff[b1] + idx1;
+                        o[2] = B.toff[b2] + idx2;
+                    } else {
+                        int ea = B.eoff[b1] + idx1, eb = B.eoff[b2] + idx2;
+                        o[0] = 1;
+                        o[1] = min(ea, eb);
+                        o[2] = max(ea, eb);
+                    }
+                } else {
+                    PairRec r;
+                    r.l1 = (int)p;
+                    if (job < 2) {
+                        r.v[0] = sv1[0]; r.v[1] = sv2[0]; r.v[2] = sv2[1]; r.v[3] = sv2[2];
+                        r.flags = 0;
+                        r.eps = 0.0;
+                    } else {
+                        r.v[0] = sv1[0]; r.v[1] = sv1[1]; r.v[2] = sv2[0]; r.v[3] = sv2[1];
+                        r.flags = 1;
+                        r.eps = 1e-3 * B.erest2[B.eoff[b1] + idx1] * B.erest2[B.eoff[b2] + idx2];
+                    }
+                    B.recs[my] = r;
+                }
+            }
+        }
+    }
+}
+
+// Level 2 with primitive clusters: one warp per level-1 slot pair.  Side-1
+// clusters meeting the side-2 slot box are opened and their primitives that
+// meet the side-2 box are staged; each full stage is flushed against the
+// side-2 clusters (see l2c_flush).  Same set as k_l2.
+__global__ void __launch_bounds__(32 * kL2Warps) k_l2c(L2cArgs A) {
+    __shared__ double st_box[kL2Warps][kStage][6];
+    __shared__ int st_idx[kL2Warps][kStage];
+    const L2Args &B = A.a;
+    int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int gw = blockIdx.x * kL2Warps + wib, nw = gridDim.x * kL2Warps;
+    int64_t npairs = B.n_l1;
+    if (B.n_l1_dev) npairs = min((int64_t)*B.n_l1_dev, B.n_l1);
+    for (int64_t p = gw; p < npairs; p += nw) {
+        int2 pr = B.l1[p];
+        double boxS[2][6];
+        for (int k = 0; k < 6; ++k) { boxS[0][k] = B.box[6 * (int64_t)pr.x + k]; boxS[1][k] = B.box[6 * (int64_t)pr.y + k]; }
+        for (int job = 0; job < 3; ++job) {
+            int s1 = job == 1 ? pr.y : pr.x, s2 = job == 1 ? pr.x : pr.y;
+            int k1 = job == 2 ? 2 : 0, k2 = job == 2 ? 2 : 1;
+            const double *box1 = boxS[job == 1 ? 1 : 0], *box2 = boxS[job == 1 ? 0 : 1];
+            int b1 = B.slot_body[s1], b2 = B.slot_body[s2];
+            int n1 = k1 == 0 ? B.nv[b1] : (k1 == 1 ? B.nt[b1] : B.ne[b1]);
+            int nc1 = (n1 + kClusterSize - 1) / kClusterSize, cb1 = cl_first(A, k1, s1, b1);
+            int nst = 0;
+            double stbox[6] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300};
+            for (int cbk = 0; cbk < nc1; cbk += 32) {
+                int c = cbk + lane;
+                bool ok = c < nc1 && overlap6(A.cbox + 6 * (int64_t)(cb1 + c), box2);
+                unsigned m = __ballot_sync(0xffffffffu, ok);
+                while (m) {
+                    int cc = cbk + __ffs(m) - 1;
+                    m &= m - 1;
+                    int i1 = kClusterSize * cc + lane;
+                    bool keep = false;
+                    double bx[6];
+                    int idx1 = -1;
+                    if (i1 < n1) {
+                        int sv[3];
+                        idx1 = cl_prim(A, k1, b1, i1);
+                        int nvx = prim_verts(B, k1, s1, idx1, sv);
+                        prim_box(B, sv, nvx, bx);
+                        keep = overlap6(bx, box2);
+                    }
+                    unsigned km = __ballot_sync(0xffffffffu, keep);
+                    int cnt = __popc(km);
+                    if (cnt == 0) continue;
+                    if (nst + cnt > kStage) {
+                        __syncwarp();
+                        l2c_flush(A, p, job, s1, s2, k1, k2, b2, box1, stbox, st_box[wib], st_idx[wib], nst, lane);
+                        nst = 0;
+                        for (int a = 0; a < 3; ++a) { stbox[a] = 1e300; stbox[3 + a] = -1e300; }
+                        __syncwarp();
+                    }
+                    if (keep) {
+                        int pos = nst + __popc(km & ((1u << lane) - 1));
+                        st_idx[wib][pos] = idx1;
+                        for (int k = 0; k < 6; ++k) st_box[wib][pos][k] = bx[k];
+                    }
+                    nst += cnt;
+                    for (int a = 0; a < 3; ++a) {
+                        double l = keep ? bx[a] : 1e300, h = keep ? bx[3 + a] : -1e300;
+                        for (int o = 16; o; o >>= 1) {
+                            l = fmin(l, __shfl_xor_sync(0xffffffffu, l, o));
+                            h = fmax(h, __shfl_xor_sync(0xffffffffu, h, o));
+                        }
+                        stbox[a] = fmin(stbox[a], l);
+                        stbox[3 + a] = fmax(stbox[3 + a], h);
+                    }
+                }
+            }
+            if (nst > 0) {
+                __syncwarp();
+                l2c_flush(A, p, job, s1, s2, k1, k2, b2, box1, stbox, st_box[wib], st_idx[wib], nst, lane);
+                __syncwarp();
+            }
+        }
+    }
+}
+
 }  // namespace abd
 
 using namespace abd;
@@ -290,7 +519,25 @@ int launch_boxes(abd_scene *s, const double *x0, const double *x1, double half, 
     if (w.S_all == 0) return ABD_OK;
     ABD_LAUNCH(s, k_boxes, grid_for((int64_t)w.S_all * 32, 256), 256, 0, s->stream, w.S_all, P<int64_t>(w.slot_voff), x0, x1,
                                                                           half, box);
+    // primitive-cluster boxes for the level-2 pass (static or swept set)
+    if (w.C > 0)
+        ABD_LAUNCH(s, k_cluster_boxes, grid_for(w.C * 32, 256), 256, 0, s->stream, w.C, P<int2>(w.cl_info),
+                   P<int>(w.slot_body), P<int64_t>(w.slot_voff), P<int>(s->dev.nv), P<int>(s->dev.toff),
+                   P<int>(s->dev.nt), P<int>(s->dev.eoff), P<int>(s->dev.ne), P<int>(s->dev.voff), P<int>(s->dev.tri),
+                   P<int>(s->dev.edge), P<int>(s->dev.vperm), P<int>(s->dev.tperm), P<int>(s->dev.eperm), x0, x1, half,
+                   x1 ? P<double>(w.cbox1) : P<double>(w.cbox));
     return cuda_check(s, cudaGetLastError(), "k_boxes");
+}
+
+static L2cArgs cluster_args(abd_scene *s, const L2Args &a, bool swept) {
+    L2cArgs C;
+    C.a = a;
+    C.vperm = P<int>(s->dev.vperm);
+    C.tperm = P<int>(s->dev.tperm);
+    C.eperm = P<int>(s->dev.eperm);
+    C.slot_cbase = P<int>(s->w.slot_cbase);
+    C.cbox = swept ? P<double>(s->w.cbox1) : P<double>(s->w.cbox);
+    return C;
 }
 
 // Read a device counter (synchronises the stream).
@@ -330,7 +577,7 @@ int launch_l2(abd_scene *s, int mode, const double *x0, const double *x1, double
               int64_t cap, int64_t *count) {
     World &w = s->w;
     Counters *c = P<Counters>(w.ctr);
-    L2Args A;
+    L2Args A = {};
     A.slot_body = P<int>(w.slot_body);
     A.slot_voff = P<int64_t>(w.slot_voff);
     A.voff = P<int>(s->dev.voff); A.nv = P<int>(s->dev.nv); A.toff = P<int>(s->dev.toff); A.nt = P<int>(s->dev.nt);
@@ -340,6 +587,7 @@ int launch_l2(abd_scene *s, int mode, const double *x0, const double *x1, double
     A.half = half;
     A.l1 = P<int2>(w.l1);
     A.n_l1 = n_l1;
+    A.n_l1_dev = nullptr;
     A.mode = mode;
     A.out3 = out3;
     A.count = &c->cand;
@@ -366,7 +614,8 @@ int launch_l2(abd_scene *s, int mode, const double *x0, const double *x1, double
                 bytes = (x1 ? 48.0 : 24.0) * (double)w.SV + tri_e + 8.0 * (double)n_l1;
             }
             prof_begin(s, x1 ? "l2_swept" : "l2_static", bytes, &ea, &eb);
-            ABD_LAUNCH(s, k_l2, grid_for(n_l1, kL2Warps, 152 * 16), 32 * kL2Warps, 0, s->stream, A);
+            ABD_LAUNCH(s, k_l2c, grid_for(n_l1, kL2Warps, 152 * 16), 32 * kL2Warps, 0, s->stream,
+                       cluster_args(s, A, x1 != nullptr));
             prof_end(s, ea, eb, prof_index(s, x1 ? "l2_swept" : "l2_static"));
         }
         int rc = cuda_check(s, cudaGetLastError(), "k_l2");
@@ -379,6 +628,59 @@ int launch_l2(abd_scene *s, int mode, const double *x0, const double *x1, double
         w.cap_cand = (int64_t)n + n / 2 + 1024;
         if (!dbuf_ensure(w.cand, sizeof(PairRec) * w.cap_cand)) return set_err(s, ABD_E_OOM, "candidate list");
     }
+}
+
+// ---------------------------------------------------------------------------
+// Asynchronous variants for the Newton loop: counts stay on the device, the
+// kernels clamp to the buffer capacity, and the host checks counts against
+// capacities once per iteration (a count above its capacity means the
+// iteration is redone with larger buffers).
+// ---------------------------------------------------------------------------
+int launch_l1_async(abd_scene *s, const double *box) {
+    World &w = s->w;
+    Counters *c = P<Counters>(w.ctr);
+    cudaMemsetAsync(&c->l1, 0, sizeof(unsigned long long), s->stream);
+    int64_t ntile = (w.S_all + 31) / 32;
+    ABD_LAUNCH(s, k_l1, grid_for((int64_t)w.S_all * ntile, 256), 256, 0, s->stream, w.S_all, P<int>(w.slot_part), box,
+               P<PartState>(w.part), P<int2>(w.l1), w.cap_l1, &c->l1);
+    return cuda_check(s, cudaGetLastError(), "k_l1");
+}
+
+int launch_l2_async(abd_scene *s, const double *x0, const double *x1, double half) {
+    World &w = s->w;
+    Counters *c = P<Counters>(w.ctr);
+    L2Args A = {};
+    A.slot_body = P<int>(w.slot_body);
+    A.slot_voff = P<int64_t>(w.slot_voff);
+    A.voff = P<int>(s->dev.voff); A.nv = P<int>(s->dev.nv); A.toff = P<int>(s->dev.toff); A.nt = P<int>(s->dev.nt);
+    A.eoff = P<int>(s->dev.eoff); A.ne = P<int>(s->dev.ne); A.tri = P<int>(s->dev.tri); A.edge = P<int>(s->dev.edge);
+    A.erest2 = P<double>(s->dev.erest2);
+    A.x0 = x0; A.x1 = x1; A.box = x1 ? P<double>(w.box1) : P<double>(w.box);
+    A.half = half;
+    A.l1 = P<int2>(w.l1);
+    A.n_l1 = w.cap_l1;
+    A.n_l1_dev = &c->l1;
+    A.mode = 1;
+    A.out3 = nullptr;
+    A.recs = P<PairRec>(w.cand);
+    A.cap = w.cap_cand;
+    A.count = &c->cand;
+    cudaMemsetAsync(&c->cand, 0, sizeof(unsigned long long), s->stream);
+    cudaEvent_t ea, eb;
+    double bytes = 0.0;
+    if (s->prof) {
+        double tri_e = 0.0;
+        for (int sl = 0; sl < w.S_all; ++sl) {
+            int b = w.h_slot_body[sl];
+            tri_e += 12.0 * s->nt[b] + 8.0 * s->ne[b];
+        }
+        bytes = (x1 ? 48.0 : 24.0) * (double)w.SV + tri_e;
+    }
+    prof_begin(s, x1 ? "l2_swept" : "l2_static", bytes, &ea, &eb);
+    ABD_LAUNCH(s, k_l2c, grid_for(w.cap_l1, kL2Warps, 152 * 16), 32 * kL2Warps, 0, s->stream,
+               cluster_args(s, A, x1 != nullptr));
+    prof_end(s, ea, eb, prof_index(s, x1 ? "l2_swept" : "l2_static"));
+    return cuda_check(s, cudaGetLastError(), "k_l2");
 }
 
 }  // namespace abd

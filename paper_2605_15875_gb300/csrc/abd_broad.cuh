@@ -12,7 +12,8 @@ struct L2Args {
     const double *x0, *x1, *box;
     double half;
     const int2 *l1;
-    int64_t n_l1;
+    int64_t n_l1;                          // used when n_l1_dev is null
+    const unsigned long long *n_l1_dev;    // device count of level-1 pairs (clamped to n_l1)
     int mode;          // 0: (type, gid_i, gid_j) triples; 1: PairRec
     int32_t *out3;
     PairRec *recs;
@@ -21,6 +22,17 @@ struct L2Args {
 };
 
 constexpr int kL2Warps = 4;
+
+// Level-2 pass over primitive clusters: the L2Args fields plus the cluster
+// orders and the per-slot cluster boxes.
+struct L2cArgs {
+    L2Args a;
+    const int *vperm, *tperm, *eperm;
+    const int *slot_cbase;
+    const double *cbox;
+};
+
+__global__ void __launch_bounds__(32 * kL2Warps) k_l2c(L2cArgs A);
 
 __global__ void k_boxes(int S, const int64_t *__restrict__ slot_voff, const double *__restrict__ x0,
                         const double *__restrict__ x1, double half, double *__restrict__ box);

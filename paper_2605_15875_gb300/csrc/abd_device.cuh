@@ -274,8 +274,8 @@ template <class T, int N>
 __device__ void jacobi(T *A, T *V) {
     for (int i = 0; i < N * N; ++i) V[i] = T(0);
     for (int i = 0; i < N; ++i) V[i * N + i] = T(1);
-    const T tol = sizeof(T) == 8 ? T(1e-30) : T(1e-13);
-    for (int sweep = 0; sweep < (sizeof(T) == 8 ? 30 : 15); ++sweep) {
+    const T tol = sizeof(T) == 8 ? T(1e-30) : T(1e-10);
+    for (int sweep = 0; sweep < (sizeof(T) == 8 ? 30 : 10); ++sweep) {
         T off = T(0), tot = T(0);
         for (int i = 0; i < N; ++i)
             for (int j = 0; j < N; ++j) {
@@ -416,6 +416,180 @@ __device__ void pair_hessian(bool ee, const T *X, const PairGrad &P, T d, T kB, 
     }
 #pragma unroll
     for (int i = 0; i < 144; ++i) H[i] *= kB;
+}
+
+// Cyclic Jacobi + clamp for a symmetric n x n matrix, n <= 5, in registers
+// (row stride 5).  Leaves K unchanged when it has no negative eigenvalue.
+template <class T>
+__device__ __forceinline__ void psd_small(T *K, int n) {
+    T A[25], V[25];
+#pragma unroll
+    for (int i = 0; i < 25; ++i) { A[i] = K[i]; V[i] = (i % 6 == 0) ? T(1) : T(0); }
+    const T tol = sizeof(T) == 8 ? T(1e-30) : T(1e-10);
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        T off = T(0), tot = T(0);
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+#pragma unroll
+            for (int j = 0; j < 5; ++j)
+                if (i < n && j < n) {
+                    T a2 = A[i * 5 + j] * A[i * 5 + j];
+                    tot += a2;
+                    if (i != j) off += a2;
+                }
+        if (off <= tol * tot || off == T(0)) break;
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = p + 1; q < 5; ++q) {
+                if (q >= n) continue;
+                T apq = A[p * 5 + q];
+                if (apq == T(0)) continue;
+                T theta = (A[q * 5 + q] - A[p * 5 + p]) / (T(2) * apq);
+                T t = (theta >= T(0) ? T(1) : T(-1)) / (tabs(theta) + tsqrt(theta * theta + T(1)));
+                T c = T(1) / tsqrt(t * t + T(1)), sn = t * c;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    T akp = A[k * 5 + p], akq = A[k * 5 + q];
+                    A[k * 5 + p] = c * akp - sn * akq;
+                    A[k * 5 + q] = sn * akp + c * akq;
+                }
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    T apk = A[p * 5 + k], aqk = A[q * 5 + k];
+                    A[p * 5 + k] = c * apk - sn * aqk;
+                    A[q * 5 + k] = sn * apk + c * aqk;
+                }
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    T vkp = V[k * 5 + p], vkq = V[k * 5 + q];
+                    V[k * 5 + p] = c * vkp - sn * vkq;
+                    V[k * 5 + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    bool neg = false;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) neg |= (i < n) && A[i * 6] < T(0);
+    if (!neg) return;
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            T acc = T(0);
+#pragma unroll
+            for (int k = 0; k < 5; ++k)
+                if (k < n && A[k * 6] > T(0)) acc += V[i * 5 + k] * A[k * 6] * V[j * 5 + k];
+            K[i * 5 + j] = (i < n && j < n) ? acc : T(0);
+        }
+}
+
+// Low-rank form of one unmollified pair's barrier Hessian.  Its range lies in
+// span{w (x) e_a, c_j_perp (x) r} (w: closest-point weights, c_j: feature
+// parameter directions orthogonalised against w, r: closest-point
+// difference), at most 5-dimensional, so H = B K B^T with B orthonormal:
+// B = [w^ (x) e_1..3, c^_j (x) r^] and K = B^T H B (n x n, n = 3 + k).
+// PSD(H) = B PSD(K) B^T exactly.  Returns n and fills K (row stride 5, kB
+// included), the unit weights wh[4], the unit feature directions ch[2][4]
+// and r^.
+template <class T>
+__device__ int pair_hessian_lowrank(bool ee, const T *X, const PairGrad &P, T d, T kB, T *K, T *wh, T ch[2][4],
+                                    T *rh) {
+    Feature f = feature_of(ee, P.type);
+    T w[4], r[3] = {0, 0, 0}, D[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    T b0 = T(P.b0), b1 = T(P.b1);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) w[v] = T(f.w0[v]) + b0 * T(f.c[0][v]) + b1 * T(f.c[1][v]);
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r[a] += w[v] * X[3 * v + a];
+            D[0][a] += T(f.c[0][v]) * X[3 * v + a];
+            D[1][a] += T(f.c[1][v]) * X[3 * v + a];
+        }
+    const int k = f.k, n = 3 + k;
+    T wn2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + w[3] * w[3], wn = tsqrt(wn2);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) wh[v] = w[v] / wn;
+    T rn = tsqrt(dot3(r, r));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) rh[a] = r[a] / rn;
+    // c^_j: Gram-Schmidt of the feature directions against w^ and each other;
+    // cc[j][l] = c_j . c^_l
+    T cc[2][2] = {{0, 0}, {0, 0}}, wc[2] = {0, 0};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        T cj[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) cj[v] = T(f.c[j][v]);
+        wc[j] = cj[0] * w[0] + cj[1] * w[1] + cj[2] * w[2] + cj[3] * w[3];
+        if (j >= k) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) ch[j][v] = T(0);
+            continue;
+        }
+        T u[4];
+        T pw = wc[j] / wn2;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) u[v] = cj[v] - pw * w[v];
+        if (j == 1) {
+            T p0 = u[0] * ch[0][0] + u[1] * ch[0][1] + u[2] * ch[0][2] + u[3] * ch[0][3];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) u[v] -= p0 * ch[0][v];
+        }
+        T un = tsqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + u[3] * u[3]);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) ch[j][v] = u[v] / un;
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int l = 0; l < 2; ++l)
+            cc[j][l] = (j < k && l < k)
+                           ? T(f.c[j][0]) * ch[l][0] + T(f.c[j][1]) * ch[l][1] + T(f.c[j][2]) * ch[l][2] +
+                                 T(f.c[j][3]) * ch[l][3]
+                           : T(0);
+    T bp = T(P.bp), cg = T(P.bpp) - bp / d, chs = bp / (T(2) * d);
+#pragma unroll
+    for (int i = 0; i < 25; ++i) K[i] = T(0);
+    // cg (B^T gd)(B^T gd)^T, B^T gd = (|w| r / d, 0, 0)
+    T gdb[3] = {wn * r[0] / d, wn * r[1] / d, wn * r[2] / d};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) K[a * 5 + b] = cg * gdb[a] * gdb[b];
+    // + 2 ch |w|^2 on the first three
+#pragma unroll
+    for (int a = 0; a < 3; ++a) K[a * 6] += T(2) * chs * wn2;
+    // - 2 ch sum_ij Ginv_ij (B^T g_i)(B^T g_j)^T, B^T g_j = (|w| D_j + (w.c_j/|w|) r, (c_j.c^_l)|r|)
+    if (k > 0) {
+        T G00 = dot3(D[0], D[0]), G01 = dot3(D[0], D[1]), G11 = dot3(D[1], D[1]);
+        T i00, i01, i11;
+        if (k == 1) { i00 = T(1) / G00; i01 = T(0); i11 = T(0); }
+        else {
+            T det = G00 * G11 - G01 * G01;
+            i00 = G11 / det; i11 = G00 / det; i01 = -G01 / det;
+        }
+        T gb[2][5];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) gb[j][a] = wn * D[j][a] + wc[j] / wn * r[a];
+            gb[j][3] = cc[j][0] * rn;
+            gb[j][4] = cc[j][1] * rn;
+        }
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+#pragma unroll
+            for (int b = 0; b < 5; ++b)
+                K[a * 5 + b] -= T(2) * chs *
+                                (i00 * gb[0][a] * gb[0][b] + i01 * (gb[0][a] * gb[1][b] + gb[1][a] * gb[0][b]) +
+                                 i11 * gb[1][a] * gb[1][b]);
+    }
+#pragma unroll
+    for (int i = 0; i < 25; ++i) K[i] *= kB;
+    return n;
 }
 
 // Barrier energy only (no derivatives), FP64.

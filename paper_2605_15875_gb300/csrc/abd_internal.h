@@ -56,7 +56,14 @@ struct SceneDev {
     int nb = 0;
     int64_t V = 0, T = 0, E = 0;
     DBuf q, v, mass, S, vol, kappa, kind, voff, nv, toff, nt, eoff, ne, xbar, tri, edge, erest2;
+    // primitive clusters: per body, vertices / triangles / edges in a
+    // rest-frame Morton order (body-local ids), chunked by 32
+    DBuf vperm, tperm, eperm;
+    DBuf cbody_off;  // [B + 1] first cluster of each body (vertices, triangles, edges)
+    DBuf crest;      // [clusters][6] rest-frame box of each cluster's vertices (centre, half extent)
 };
+
+constexpr int kClusterSize = 32;
 
 // Per-step workspace of the consensus solve.
 struct World {
@@ -72,12 +79,20 @@ struct World {
     DBuf ctr;    // counters
     DBuf bar;    // grid barrier words
     DBuf aabb;   // body AABBs at the step start
+    DBuf part_off;  // [NP + 1] dynamic-slot range of each partition
+    DBuf deferred;  // active pairs left to the full 12x12 projection
+    DBuf rowcnt, rowoff, rowcur, ent;  // row CSR of the off-diagonal blocks
+    DBuf slot_cbase;   // [S_all + 1] first cluster of each slot
+    DBuf cl_info;      // [C] (slot, kind << 24 | cluster index)
+    DBuf cbox, cbox1;  // [C][6] cluster boxes (static, swept)
+    int64_t C = 0;
     int64_t cap_l1 = 0, cap_cand = 0, cap_act = 0, cap_ls = 0;
+    int ecap_mult = 16;  // PCG neighbour-list capacity per owned slot
     // host mirrors
     std::vector<int> h_slot_body, h_slot_part;
     std::vector<int64_t> h_slot_voff;
     std::vector<uint64_t> h_slot_mask;
-    std::vector<int> h_rep_off, h_rep_slot, h_body_rep, h_body_slot;
+    std::vector<int> h_rep_off, h_rep_slot, h_body_rep, h_body_slot, h_part_off, h_slot_cbase;
 };
 
 // Per-partition scalars, device resident.
@@ -98,6 +113,8 @@ struct Counters {
     int overflow;
     int timeout;
     unsigned long long pcg_total;
+    int pending;  // line-search passes still undecided
+    int bad;      // a list outgrew its buffer in this iteration
 };
 
 struct KStat {
@@ -118,6 +135,8 @@ struct abd_scene {
     std::vector<int> kind, voff, nv, toff, nt, eoff, ne;
     std::vector<double> mass, S, vol, kappa, com, xbar, erest2;
     std::vector<int> tri, edge;
+    std::vector<int> vperm, tperm, eperm, cbody_off;
+    std::vector<double> crest;
     abd::Planes planes{};
     double g[3] = {0, 0, 0};
     // partition
@@ -148,12 +167,16 @@ int launch_l1(abd_scene *s, const double *box, int64_t *count);
 int launch_l2(abd_scene *s, int mode, const double *x0, const double *x1, double half, int64_t n_l1, int32_t *out3,
               int64_t cap, int64_t *count);
 // ---- (abd_assemble.cu) ----
-int launch_narrow(abd_scene *s, int64_t n_cand, double dhat, int64_t *n_act);
-int launch_assemble(abd_scene *s, int precision, const abd_step_params *p, double kB, int64_t n_act, int64_t n_l1);
-int launch_ccd(abd_scene *s, int64_t n_sw, const abd_step_params *p, double dhat, int64_t *n_ls, bool want_ls);
-int launch_energy(abd_scene *s, const abd_step_params *p, double kB, int64_t n_ls, const double *alphas_dev);
+// asynchronous variants: device-resident counts, capacity-clamped
+int launch_l1_async(abd_scene *s, const double *box);
+int launch_l2_async(abd_scene *s, const double *x0, const double *x1, double half);
+int launch_narrow_async(abd_scene *s, const PairRec *src, const unsigned long long *src_n, int64_t src_cap,
+                        double dhat);
+int launch_assemble_async(abd_scene *s, int precision, const abd_step_params *p, double kB);
+int launch_ccd_async(abd_scene *s, const abd_step_params *p, bool want_ls);
+int launch_energy_async(abd_scene *s, const abd_step_params *p, double kB, const double *alphas_dev);
+int launch_pcg_async(abd_scene *s, int precision, const abd_step_params *p);
 // ---- (abd_solve.cu) ----
-int launch_pcg(abd_scene *s, int precision, const abd_step_params *p, int64_t n_l1, int64_t *iters);
 
 // profiling helpers (abd_scene.cu)
 void prof_begin(abd_scene *s, const char *name, double bytes, cudaEvent_t *a, cudaEvent_t *b);

@@ -128,14 +128,14 @@ extern "C" int abd_candidates_noalloc(abd_scene *s, const double *x0, const doub
                        "candidates_noalloc: " + std::to_string(n_l1) + " overlapping body pairs exceed the scratch limit of " +
                            std::to_string(cap_l1));
     }
-    L2Args A;
+    L2Args A = {};
     A.slot_body = slot_body;
     A.slot_voff = slot_voff;
     A.voff = P<int>(s->dev.voff); A.nv = P<int>(s->dev.nv); A.toff = P<int>(s->dev.toff); A.nt = P<int>(s->dev.nt);
     A.eoff = P<int>(s->dev.eoff); A.ne = P<int>(s->dev.ne); A.tri = P<int>(s->dev.tri); A.edge = P<int>(s->dev.edge);
     A.erest2 = P<double>(s->dev.erest2);
     A.x0 = x0; A.x1 = x1; A.box = box; A.half = half;
-    A.l1 = l1; A.n_l1 = (int64_t)n_l1;
+    A.l1 = l1; A.n_l1 = (int64_t)n_l1; A.n_l1_dev = nullptr;
     A.mode = 0; A.out3 = out; A.recs = nullptr; A.cap = cap; A.count = &ctr[1];
     if (n_l1 > 0)
         ABD_LAUNCH(s, k_l2, grid_for((int64_t)n_l1, kL2Warps, 152 * 16), 32 * kL2Warps, 0, s->stream, A);

@@ -128,6 +128,32 @@ static bool mesh_mass(const double *xb, int nv, const int32_t *tri, int nt, doub
     return true;
 }
 
+// Order of n primitives along a Morton curve of their rest-frame centres
+// (10 bits per axis over the body's box); chunks of 32 consecutive entries
+// form the clusters the broad phase filters before it looks at primitives.
+static void morton_order(const std::vector<double> &c, int n, int *out) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = std::min(lo[k], c[3 * i + k]);
+            hi[k] = std::max(hi[k], c[3 * i + k]);
+        }
+    std::vector<std::pair<uint64_t, int>> key(n);
+    for (int i = 0; i < n; ++i) {
+        uint64_t code = 0;
+        uint32_t q[3];
+        for (int k = 0; k < 3; ++k) {
+            double t = hi[k] > lo[k] ? (c[3 * i + k] - lo[k]) / (hi[k] - lo[k]) : 0.0;
+            q[k] = (uint32_t)std::min(1023.0, std::max(0.0, t * 1023.0));
+        }
+        for (int bit = 9; bit >= 0; --bit)
+            for (int k = 0; k < 3; ++k) code = (code << 1) | ((q[k] >> bit) & 1u);
+        key[i] = {code, i};
+    }
+    std::sort(key.begin(), key.end());
+    for (int i = 0; i < n; ++i) out[i] = key[i].second;
+}
+
 static bool upload(abd_scene *s, DBuf &b, const void *h, size_t bytes) {
     if (!dbuf_ensure(b, bytes ? bytes : 8)) return false;
     if (bytes && cudaMemcpy(b.p, h, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return false;
@@ -226,6 +252,65 @@ extern "C" int abd_scene_create(const abd_scene_desc *d, void *stream, abd_scene
         if (d->body_v0)
             for (int i = 0; i < 12; ++i) v[12 * (size_t)b + i] = d->body_v0[12 * (size_t)b + i];
     }
+    // primitive cluster orders (rest frame, per body)
+    s->vperm.resize((size_t)s->V);
+    s->tperm.resize((size_t)s->T);
+    s->eperm.resize((size_t)s->E);
+    for (int b = 0; b < nb; ++b) {
+        const double *xb = s->xbar.data() + 3 * (size_t)s->voff[b];
+        std::vector<double> c(3 * (size_t)std::max(s->nv[b], std::max(s->nt[b], s->ne[b])));
+        morton_order(std::vector<double>(xb, xb + 3 * (size_t)s->nv[b]), s->nv[b], s->vperm.data() + s->voff[b]);
+        for (int t = 0; t < s->nt[b]; ++t)
+            for (int k = 0; k < 3; ++k) {
+                const int *tr = s->tri.data() + 3 * ((size_t)s->toff[b] + t);
+                c[3 * t + k] = (xb[3 * tr[0] + k] + xb[3 * tr[1] + k] + xb[3 * tr[2] + k]) / 3.0;
+            }
+        morton_order(c, s->nt[b], s->tperm.data() + s->toff[b]);
+        for (int e = 0; e < s->ne[b]; ++e)
+            for (int k = 0; k < 3; ++k) {
+                const int *ed = s->edge.data() + 2 * ((size_t)s->eoff[b] + e);
+                c[3 * e + k] = 0.5 * (xb[3 * ed[0] + k] + xb[3 * ed[1] + k]);
+            }
+        morton_order(c, s->ne[b], s->eperm.data() + s->eoff[b]);
+    }
+    // rest-frame boxes of the clusters (centre, half extent of their vertices)
+    s->cbody_off.assign(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+        int nc = (s->nv[b] + kClusterSize - 1) / kClusterSize + (s->nt[b] + kClusterSize - 1) / kClusterSize +
+                 (s->ne[b] + kClusterSize - 1) / kClusterSize;
+        s->cbody_off[b + 1] = s->cbody_off[b] + nc;
+    }
+    s->crest.assign(6 * (size_t)s->cbody_off[nb], 0.0);
+    for (int b = 0; b < nb; ++b) {
+        const double *xb = s->xbar.data() + 3 * (size_t)s->voff[b];
+        int c = s->cbody_off[b];
+        for (int kind = 0; kind < 3; ++kind) {
+            int n = kind == 0 ? s->nv[b] : (kind == 1 ? s->nt[b] : s->ne[b]);
+            for (int j = 0; j * kClusterSize < n; ++j, ++c) {
+                double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+                for (int i = j * kClusterSize; i < std::min(n, (j + 1) * kClusterSize); ++i) {
+                    int vs[3], k = 0;
+                    if (kind == 0) vs[k++] = s->vperm[s->voff[b] + i];
+                    else if (kind == 1) {
+                        const int *t = s->tri.data() + 3 * ((size_t)s->toff[b] + s->tperm[s->toff[b] + i]);
+                        vs[0] = t[0]; vs[1] = t[1]; vs[2] = t[2]; k = 3;
+                    } else {
+                        const int *e = s->edge.data() + 2 * ((size_t)s->eoff[b] + s->eperm[s->eoff[b] + i]);
+                        vs[0] = e[0]; vs[1] = e[1]; k = 2;
+                    }
+                    for (int q = 0; q < k; ++q)
+                        for (int a = 0; a < 3; ++a) {
+                            lo[a] = std::min(lo[a], xb[3 * vs[q] + a]);
+                            hi[a] = std::max(hi[a], xb[3 * vs[q] + a]);
+                        }
+                }
+                for (int a = 0; a < 3; ++a) {
+                    s->crest[6 * (size_t)c + a] = 0.5 * (lo[a] + hi[a]);
+                    s->crest[6 * (size_t)c + 3 + a] = 0.5 * (hi[a] - lo[a]);
+                }
+            }
+        }
+    }
     s->planes.n = d->n_planes;
     for (int i = 0; i < d->n_planes; ++i) {
         if (d->plane_axis[i] < 0 || d->plane_axis[i] > 2) { delete s; return ABD_E_INVALID; }
@@ -245,7 +330,12 @@ extern "C" int abd_scene_create(const abd_scene_desc *d, void *stream, abd_scene
               upload(s, D.ne, s->ne.data(), nb * 4) && upload(s, D.xbar, s->xbar.data(), s->xbar.size() * 8) &&
               upload(s, D.tri, s->tri.data(), s->tri.size() * 4) &&
               upload(s, D.edge, s->edge.data(), s->edge.size() * 4) &&
-              upload(s, D.erest2, s->erest2.data(), s->erest2.size() * 8);
+              upload(s, D.erest2, s->erest2.data(), s->erest2.size() * 8) &&
+              upload(s, D.vperm, s->vperm.data(), s->vperm.size() * 4) &&
+              upload(s, D.tperm, s->tperm.data(), s->tperm.size() * 4) &&
+              upload(s, D.eperm, s->eperm.data(), s->eperm.size() * 4) &&
+              upload(s, D.cbody_off, s->cbody_off.data(), s->cbody_off.size() * 4) &&
+              upload(s, D.crest, s->crest.data(), s->crest.size() * 8);
     if (!ok) {
         abd_scene_destroy(s);
         cudaGetLastError();
@@ -260,14 +350,14 @@ extern "C" void abd_scene_destroy(abd_scene *s) {
     cudaStreamSynchronize(s->stream);
     SceneDev &D = s->dev;
     DBuf *bufs[] = {&D.q, &D.v, &D.mass, &D.S, &D.vol, &D.kappa, &D.kind, &D.voff, &D.nv, &D.toff, &D.nt,
-                    &D.eoff, &D.ne, &D.xbar, &D.tri, &D.edge, &D.erest2};
+                    &D.eoff, &D.ne, &D.xbar, &D.tri, &D.edge, &D.erest2, &D.vperm, &D.tperm, &D.eperm, &D.cbody_off, &D.crest};
     for (DBuf *b : bufs) dbuf_free(*b);
     World &w = s->w;
     DBuf *wb[] = {&w.slot_body, &w.slot_part, &w.slot_voff, &w.slot_mask, &w.slot_rep, &w.slot_kw, &w.sv_slot,
                   &w.q, &w.qprev, &w.qtil, &w.z, &w.u, &w.rho, &w.dq, &w.g, &w.x, &w.x1, &w.dx, &w.box, &w.box1,
                   &w.rep_off, &w.rep_slot, &w.zb, &w.rho0, &w.rhob, &w.rb, &w.sb, &w.body_rep, &w.body_slot,
                   &w.l1, &w.cand, &w.act, &w.ls, &w.diag, &w.off, &w.offflag, &w.pinv, &w.pcg_r, &w.pcg_z,
-                  &w.pcg_p, &w.pcg_ap, &w.pcg_sc, &w.part, &w.ctr, &w.bar, &w.aabb};
+                  &w.pcg_p, &w.pcg_ap, &w.pcg_sc, &w.part, &w.ctr, &w.bar, &w.aabb, &w.part_off, &w.deferred, &w.rowcnt, &w.rowoff, &w.rowcur, &w.ent, &w.slot_cbase, &w.cl_info, &w.cbox, &w.cbox1};
     for (DBuf *b : wb) dbuf_free(*b);
     if (s->pinned) cudaFreeHost(s->pinned);
     for (auto &pe : s->ev_pending) {

@@ -128,233 +128,6 @@ __global__ void k_pinv(int S_dyn, const int *__restrict__ slot_part, const PartS
     }
 }
 
-struct PcgPart {
-    double rz[2], pap[2], rr[2], rzn[2];
-    double r0;
-    int done, it;
-};
-
-struct PcgArgs {
-    int S_dyn;
-    const int *slot_part;
-    const PartState *part;
-    const double *g;
-    double *x;
-    const int2 *l1;
-    const int *offflag;
-    int64_t n_l1;
-    PcgPart *pp;
-    int NP;
-    double tol2;
-    int max_it;
-    unsigned *bar;   // [0] count, [1] generation
-    int *timeout;
-};
-
-// Grid barrier with a bounded spin: after ~2^24 polls with back-off the
-// waiting block records a timeout and proceeds, so the kernel always ends.
-__device__ __forceinline__ void grid_barrier(unsigned *bar, unsigned nblocks, int *timeout) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *gen = bar + 1;
-        unsigned my = *gen;
-        __threadfence();
-        unsigned arrived = atomicAdd(bar, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd((unsigned *)gen, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (*gen == my) {
-                if (++spins > (1ull << 24)) { atomicExch(timeout, 1); break; }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
-
-// Sum v over the warp into acc[p] when all contributing lanes share p.
-__device__ __forceinline__ void warp_add(double *base, int stride, int p, double v) {
-    const unsigned full = 0xffffffffu;
-    int pmax = __reduce_max_sync(full, p);
-    int pmin = __reduce_min_sync(full, p < 0 ? 0x7fffffff : p);
-    if (pmax < 0) return;
-    if (pmin == pmax) {
-        double t = p < 0 ? 0.0 : v;
-        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(full, t, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(base + (int64_t)stride * pmax, t);
-    } else if (p >= 0) {
-        atomicAdd(base + (int64_t)stride * p, v);
-    }
-}
-
-// r = -g, x = 0, z = Pinv r, p = z; rz, r0 per partition.
-template <class T>
-__global__ void k_pcg_init(PcgArgs A, const T *__restrict__ pinv, T *__restrict__ r, T *__restrict__ z,
-                           T *__restrict__ p) {
-    const int stride = sizeof(PcgPart) / sizeof(double);
-    for (int base = blockIdx.x * blockDim.x; base < A.S_dyn; base += gridDim.x * blockDim.x) {
-        int s = base + threadIdx.x;
-        int pt = -1;
-        double rzv = 0.0, rrv = 0.0;
-        if (s < A.S_dyn) {
-            pt = A.slot_part[s];
-            T rv[12];
-            for (int i = 0; i < 12; ++i) {
-                double gi = A.part[pt].active ? -A.g[12 * (int64_t)s + i] : 0.0;
-                rv[i] = T(gi);
-                A.x[12 * (int64_t)s + i] = 0.0;
-                r[12 * (int64_t)s + i] = rv[i];
-            }
-            const T *M = pinv + 144 * (int64_t)s;
-            for (int i = 0; i < 12; ++i) {
-                T t = T(0);
-                if (A.part[pt].active)
-                    for (int j = 0; j < 12; ++j) t += M[i * 12 + j] * rv[j];
-                z[12 * (int64_t)s + i] = t;
-                p[12 * (int64_t)s + i] = t;
-                rzv += (double)rv[i] * (double)t;
-                rrv += (double)rv[i] * (double)rv[i];
-            }
-            if (!A.part[pt].active) pt = -1;
-        }
-        warp_add(&A.pp[0].rz[0], stride, pt, rzv);
-        warp_add(&A.pp[0].r0, stride, pt, rrv);
-    }
-}
-
-template <class T>
-__global__ void k_pcg_loop(PcgArgs A, const T *__restrict__ diag, const T *__restrict__ off, const T *__restrict__ pinv,
-                           T *__restrict__ r, T *__restrict__ z, T *__restrict__ p, T *__restrict__ Ap) {
-    const int stride = sizeof(PcgPart) / sizeof(double);
-    const unsigned nblocks = gridDim.x;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    for (int it = 0; it < A.max_it; ++it) {
-        int c = it & 1;
-        // exit when every partition is done (all blocks read the same flags)
-        bool all_done = true;
-        for (int q = 0; q < A.NP; ++q) all_done &= A.pp[q].done != 0;
-        if (all_done) break;
-        // A: Ap = D p; zero the other parity's accumulators
-        if (blockIdx.x == 0)
-            for (int q = threadIdx.x; q < A.NP; q += blockDim.x) {
-                A.pp[q].pap[c ^ 1] = 0.0; A.pp[q].rr[c ^ 1] = 0.0; A.pp[q].rzn[c ^ 1] = 0.0;
-            }
-        for (int64_t e = tid; e < 12 * (int64_t)A.S_dyn; e += nth) {
-            int s = (int)(e / 12), i = (int)(e % 12);
-            if (A.pp[A.slot_part[s]].done) continue;
-            const T *D = diag + 144 * (int64_t)s + 12 * i;
-            const T *ps = p + 12 * (int64_t)s;
-            T acc = T(0);
-            for (int j = 0; j < 12; ++j) acc += D[j] * ps[j];
-            Ap[e] = acc;
-        }
-        grid_barrier(A.bar, nblocks, A.timeout);
-        // B: off-diagonal blocks (rows of a, cols of b), both directions
-        for (int64_t e = tid; e < 12 * A.n_l1; e += nth) {
-            int64_t k = e / 12;
-            int i = (int)(e % 12);
-            if (!A.offflag[k]) continue;
-            int2 lp = A.l1[k];
-            if (A.pp[A.slot_part[lp.x]].done) continue;
-            const T *B = off + 144 * k;
-            const T *pb = p + 12 * (int64_t)lp.y, *pa = p + 12 * (int64_t)lp.x;
-            T row = T(0), col = T(0);
-            for (int j = 0; j < 12; ++j) {
-                row += B[i * 12 + j] * pb[j];
-                col += B[j * 12 + i] * pa[j];
-            }
-            atomicAdd(Ap + 12 * (int64_t)lp.x + i, row);
-            atomicAdd(Ap + 12 * (int64_t)lp.y + i, col);
-        }
-        grid_barrier(A.bar, nblocks, A.timeout);
-        // C: p . Ap per partition
-        for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < 12 * (int64_t)A.S_dyn; base += nth) {
-            int64_t e = base + threadIdx.x;
-            int pt = -1;
-            double v = 0.0;
-            if (e < 12 * (int64_t)A.S_dyn) {
-                pt = A.slot_part[e / 12];
-                if (A.pp[pt].done) pt = -1;
-                else v = (double)p[e] * (double)Ap[e];
-            }
-            warp_add(&A.pp[0].pap[c], stride, pt, v);
-        }
-        grid_barrier(A.bar, nblocks, A.timeout);
-        // D: x += alpha p, r -= alpha Ap, z = Pinv r; rr, rz accumulators
-        for (int base = blockIdx.x * blockDim.x; base < A.S_dyn; base += nth) {
-            int s = base + threadIdx.x;
-            int pt = -1;
-            double rrv = 0.0, rzv = 0.0;
-            if (s < A.S_dyn) {
-                pt = A.slot_part[s];
-                if (A.pp[pt].done) pt = -1;
-            }
-            if (pt >= 0) {
-                double alpha = A.pp[pt].rz[c] / A.pp[pt].pap[c];
-                T rv[12];
-                for (int i = 0; i < 12; ++i) {
-                    int64_t e = 12 * (int64_t)s + i;
-                    A.x[e] += alpha * (double)p[e];
-                    rv[i] = T((double)r[e] - alpha * (double)Ap[e]);
-                    r[e] = rv[i];
-                    rrv += (double)rv[i] * (double)rv[i];
-                }
-                const T *M = pinv + 144 * (int64_t)s;
-                for (int i = 0; i < 12; ++i) {
-                    T t = T(0);
-                    for (int j = 0; j < 12; ++j) t += M[i * 12 + j] * rv[j];
-                    z[12 * (int64_t)s + i] = t;
-                    rzv += (double)rv[i] * (double)t;
-                }
-            }
-            warp_add(&A.pp[0].rr[c], stride, pt, rrv);
-            warp_add(&A.pp[0].rzn[c], stride, pt, rzv);
-        }
-        grid_barrier(A.bar, nblocks, A.timeout);
-        // E: convergence, beta, p = z + beta p
-        for (int64_t e = tid; e < 12 * (int64_t)A.S_dyn; e += nth) {
-            int pt = A.slot_part[e / 12];
-            if (A.pp[pt].done) continue;
-            if (A.pp[pt].rr[c] <= A.tol2 * A.pp[pt].r0) continue;
-            double beta = A.pp[pt].rzn[c] / A.pp[pt].rz[c];
-            p[e] = T((double)z[e] + beta * (double)p[e]);
-        }
-        if (blockIdx.x == 0)
-            for (int q = threadIdx.x; q < A.NP; q += blockDim.x) {
-                if (A.pp[q].done) continue;
-                A.pp[q].it = it + 1;
-                if (A.pp[q].rr[c] <= A.tol2 * A.pp[q].r0) A.pp[q].done = 1;
-                else A.pp[q].rz[c ^ 1] = A.pp[q].rzn[c];
-            }
-        grid_barrier(A.bar, nblocks, A.timeout);
-    }
-}
-
-__global__ void k_pcg_parts_init(PcgPart *pp, const PartState *part, int NP) {
-    for (int q = threadIdx.x; q < NP; q += blockDim.x) {
-        PcgPart z = {};
-        z.done = part[q].active ? 0 : 1;
-        pp[q] = z;
-    }
-}
-
-__global__ void k_pcg_parts_check(PcgPart *pp, int NP) {
-    for (int q = threadIdx.x; q < NP; q += blockDim.x)
-        if (!pp[q].done && !(pp[q].r0 > 0.0)) pp[q].done = 1;
-}
-
-__global__ void k_count_flags(const int *__restrict__ f, int64_t n, int *__restrict__ out) {
-    int c = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        c += f[i] != 0;
-    c = __reduce_add_sync(0xffffffffu, c);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
-}
-
 // max |dq| per partition (ordered-double atomics).
 __global__ void k_dqmax(int S_dyn, const int *__restrict__ slot_part, const double *__restrict__ dq,
                         PartState *__restrict__ part) {
@@ -367,15 +140,36 @@ __global__ void k_dqmax(int S_dyn, const int *__restrict__ slot_part, const doub
     }
 }
 
-// Line search bookkeeping: trial steps alpha_j = toi 2^-(nh0 + j - 1).
-__global__ void k_ls_alphas(int NP, PartState *part, const int *nh0, double *alphas, int max_halv) {
+// Newton stopping test of every active partition, before its line search:
+// |dq|_inf / (h l) < eps_N ends the local solve.  Resets the per-iteration
+// TOI and |dq| accumulators.
+__global__ void k_newton_decide(int NP, PartState *part, double inv_hl, double tol) {
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+        if (part[p].active) {
+            part[p].newton_it++;
+            if (unord(part[p].dqmax) * inv_hl < tol) part[p].active = 0;
+        }
+        part[p].dqmax = 0ull;
+        part[p].toi = ord(1.0);
+    }
+}
+
+__global__ void k_ls_reset(int NP, int *nh0, int *decided) {
+    for (int p = threadIdx.x; p < NP; p += blockDim.x) { nh0[p] = 0; decided[p] = 0; }
+}
+
+// Line search bookkeeping: trial steps alpha_j = toi 2^-(nh0 + j - 1);
+// alphas[p][0] = -1 marks a partition with nothing left to evaluate.
+__global__ void k_ls_alphas(int NP, PartState *part, const int *nh0, const int *decided, double *alphas,
+                            int max_halv) {
     for (int p = threadIdx.x; p < NP; p += blockDim.x) {
         for (int j = 0; j <= kLS; ++j) part[p].E[j] = 0.0;
         double toi = unord(part[p].toi);
-        alphas[(kLS + 1) * p] = 0.0;
+        bool skip = !part[p].active || decided[p];
+        alphas[(kLS + 1) * p] = skip ? -1.0 : 0.0;
         for (int j = 1; j <= kLS; ++j) {
             int nh = nh0[p] + j - 1;
-            alphas[(kLS + 1) * p + j] = nh <= max_halv ? ldexp(toi < 1.0 ? toi : 1.0, -nh) : -1.0;
+            alphas[(kLS + 1) * p + j] = (!skip && nh <= max_halv) ? ldexp(toi < 1.0 ? toi : 1.0, -nh) : -1.0;
         }
     }
 }
@@ -403,14 +197,32 @@ __global__ void k_ls_select(int NP, PartState *part, int *nh0, int *decided, con
     }
 }
 
+// Flag an iteration whose lists outgrew their buffers (its results are void).
+__global__ void k_check_bad(Counters *c, int64_t cap_l1, int64_t cap_cand, int64_t cap_act, int64_t cap_ls,
+                            const int *pcg_over) {
+    c->bad = ((int64_t)c->l1 > cap_l1 || (int64_t)c->cand > cap_cand || (int64_t)c->act > cap_act ||
+              (int64_t)c->ls > cap_ls || *pcg_over)
+                 ? 1
+                 : c->bad;
+}
+
+// q += alpha dq for partitions whose line search just settled.
 __global__ void k_update_q(int S_dyn, const int *__restrict__ slot_part, const PartState *__restrict__ part,
+                           const int *__restrict__ decided, const Counters *__restrict__ c,
                            const double *__restrict__ dq, double *__restrict__ q) {
+    if (c->bad) return;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 12 * (int64_t)S_dyn;
          e += (int64_t)gridDim.x * blockDim.x) {
         int p = slot_part[e / 12];
-        if (!part[p].active) continue;
+        if (!part[p].active || decided[p] != 1) continue;
         q[e] += part[p].alpha * dq[e];
     }
+}
+
+__global__ void k_mark_updated(int NP, int *decided, const Counters *c) {
+    if (c->bad) return;
+    for (int p = threadIdx.x; p < NP; p += blockDim.x)
+        if (decided[p] == 1) decided[p] = 2;
 }
 
 // Consensus (Eq. 6), dual update (Eq. 7), per-body residuals (Eq. 9-10).
@@ -614,6 +426,9 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
             if (w.h_body_rep[b] >= 0) reps[w.h_body_rep[b]].push_back(sl);
         }
     w.S_dyn = (int)w.h_slot_body.size();
+    w.h_part_off.assign(nparts + 1, 0);
+    for (int i = 0; i < w.S_dyn; ++i) w.h_part_off[w.h_slot_part[i] + 1]++;
+    for (int p = 0; p < nparts; ++p) w.h_part_off[p + 1] += w.h_part_off[p];
     for (int b = 0; b < s->nb; ++b)
         if (s->kind[b] != ABD_DYNAMIC) {
             w.h_slot_body.push_back(b);
@@ -623,6 +438,18 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
     w.S_all = (int)w.h_slot_body.size();
     w.h_slot_voff.assign(w.S_all + 1, 0);
     for (int i = 0; i < w.S_all; ++i) w.h_slot_voff[i + 1] = w.h_slot_voff[i] + s->nv[w.h_slot_body[i]];
+    // primitive clusters of every slot: vertices, then triangles, then edges
+    auto ncl = [](int n) { return (n + kClusterSize - 1) / kClusterSize; };
+    w.h_slot_cbase.assign(w.S_all + 1, 0);
+    std::vector<int2> cl_info;
+    for (int i = 0; i < w.S_all; ++i) {
+        int b = w.h_slot_body[i];
+        int nc[3] = {ncl(s->nv[b]), ncl(s->nt[b]), ncl(s->ne[b])};
+        w.h_slot_cbase[i + 1] = w.h_slot_cbase[i] + nc[0] + nc[1] + nc[2];
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < nc[k]; ++j) cl_info.push_back(make_int2(i, (k << 24) | j));
+    }
+    w.C = (int64_t)cl_info.size();
     w.SV = w.h_slot_voff[w.S_all];
     w.nsh = nsh;
     w.h_rep_off.assign(nsh + 1, 0);
@@ -637,7 +464,9 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
         (rc = h2d(s, w.slot_voff, w.h_slot_voff)) || (rc = h2d(s, w.slot_mask, w.h_slot_mask)) ||
         (rc = h2d(s, w.slot_rep, slot_rep)) || (rc = h2d(s, w.slot_kw, slot_kw)) ||
         (rc = h2d(s, w.rep_off, w.h_rep_off)) || (rc = h2d(s, w.rep_slot, w.h_rep_slot)) ||
-        (rc = h2d(s, w.body_rep, w.h_body_rep)) || (rc = h2d(s, w.body_slot, w.h_body_slot)))
+        (rc = h2d(s, w.body_rep, w.h_body_rep)) || (rc = h2d(s, w.body_slot, w.h_body_slot)) ||
+        (rc = h2d(s, w.part_off, w.h_part_off)) || (rc = h2d(s, w.slot_cbase, w.h_slot_cbase)) ||
+        (rc = h2d(s, w.cl_info, cl_info)))
         return rc;
     size_t S = (size_t)(w.S_all ? w.S_all : 1), Sd = (size_t)(w.S_dyn ? w.S_dyn : 1);
     size_t SV = (size_t)(w.SV ? w.SV : 1), NS = (size_t)(nsh ? nsh : 1);
@@ -648,9 +477,8 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
               dbuf_ensure(w.box1, 48 * S) && dbuf_ensure(w.zb, 96 * NS) && dbuf_ensure(w.rho0, 8 * NS) &&
               dbuf_ensure(w.rhob, 8 * NS) && dbuf_ensure(w.rb, 8 * NS) && dbuf_ensure(w.sb, 8 * NS) &&
               dbuf_ensure(w.part, sizeof(PartState) * kMaxParts) && dbuf_ensure(w.ctr, sizeof(Counters)) &&
-              dbuf_ensure(w.bar, 64) && dbuf_ensure(w.pcg_sc, sizeof(PcgPart) * kMaxParts) &&
-              dbuf_ensure(w.pinv, 8 * 144 * Sd) && dbuf_ensure(w.pcg_r, 96 * Sd) && dbuf_ensure(w.pcg_z, 96 * Sd) &&
-              dbuf_ensure(w.pcg_p, 96 * Sd) && dbuf_ensure(w.pcg_ap, 96 * Sd);
+              dbuf_ensure(w.bar, 64) && dbuf_ensure(w.pinv, 8 * 144 * Sd) &&
+              dbuf_ensure(w.cbox, 48 * (size_t)(w.C ? w.C : 1)) && dbuf_ensure(w.cbox1, 48 * (size_t)(w.C ? w.C : 1));
     if (!ok) return set_err(s, ABD_E_OOM, "world buffers");
     if (w.S_all > 0) ABD_LAUNCH(s, k_fill_sv_slot, std::min(w.S_all, 152 * 8), 256, 0, s->stream, w.S_all, P<int64_t>(w.slot_voff), P<int>(w.sv_slot));
     return cuda_check(s, cudaGetLastError(), "build world");
@@ -668,166 +496,194 @@ int write_parts(abd_scene *s, const std::vector<PartState> &ps) {
                                          s->stream), "write parts");
 }
 
-template <class T>
-int pcg_T(Ctx &C, int64_t n_l1, int64_t *iters) {
+
+// Pinned host mirror of the per-iteration status: counters, per-partition
+// state, PCG iterations and flags.
+struct Status {
+    Counters c;
+    int pcg_iters[kMaxParts];
+    int pcg_over, pcg_nnz2;
+    int csr_total;  // entries of the off-diagonal row CSR (twice the blocks)
+    PartState part[kMaxParts];
+};
+
+Status *pinned_status(abd_scene *s) {
+    if (!s->pinned) {
+        if (cudaHostAlloc(&s->pinned, sizeof(Status), cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            s->pinned = nullptr;
+            return nullptr;
+        }
+        s->pinned_bytes = sizeof(Status);
+    }
+    return (Status *)s->pinned;
+}
+
+int enqueue_status(abd_scene *s, Status *h) {
+    World &w = s->w;
+    cudaMemcpyAsync(&h->c, w.ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream);
+    cudaMemcpyAsync(h->pcg_iters, w.pcg_sc.p, sizeof(int) * (kMaxParts + 2), cudaMemcpyDeviceToHost, s->stream);
+    cudaMemcpyAsync(h->part, w.part.p, sizeof(PartState) * w.NP, cudaMemcpyDeviceToHost, s->stream);
+    if (s->prof && w.S_dyn > 0)
+        cudaMemcpyAsync(&h->csr_total, P<int>(w.rowoff) + w.S_dyn, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    return cuda_check(s, cudaGetLastError(), "status");
+}
+
+// Capacities of the pair lists and the buffers that depend on them.
+int ensure_lists(Ctx &C) {
     abd_scene *s = C.s;
     World &w = s->w;
-    PcgArgs A;
-    A.S_dyn = w.S_dyn; A.slot_part = P<int>(w.slot_part); A.part = P<PartState>(w.part); A.g = P<double>(w.g);
-    A.x = P<double>(w.dq); A.l1 = P<int2>(w.l1); A.offflag = P<int>(w.offflag); A.n_l1 = n_l1;
-    A.pp = P<PcgPart>(w.pcg_sc); A.NP = w.NP; A.tol2 = C.p->pcg_rtol * C.p->pcg_rtol; A.max_it = C.p->pcg_max;
-    A.bar = P<unsigned>(w.bar);
-    A.timeout = &P<Counters>(w.ctr)->timeout;
-    ABD_LAUNCH(s, k_pinv<T>, grid_for(w.S_dyn, 64), 64, 0, s->stream, w.S_dyn, P<int>(w.slot_part), P<PartState>(w.part),
-                                                          P<T>(w.diag), P<T>(w.pinv));
-    ABD_LAUNCH(s, k_pcg_parts_init, 1, 64, 0, s->stream, A.pp, A.part, w.NP);
-    ABD_LAUNCH(s, k_pcg_init<T>, grid_for(w.S_dyn, 128), 128, 0, s->stream, A, P<T>(w.pinv), P<T>(w.pcg_r), P<T>(w.pcg_z),
-                                                                P<T>(w.pcg_p));
-    ABD_LAUNCH(s, k_pcg_parts_check, 1, 64, 0, s->stream, A.pp, w.NP);
-    cudaMemsetAsync(w.bar.p, 0, 64, s->stream);
-    if (s->prof) {
-        cudaMemsetAsync(&P<Counters>(w.ctr)->overflow, 0, sizeof(int), s->stream);
-        if (n_l1 > 0)
-            ABD_LAUNCH(s, k_count_flags, grid_for(n_l1, 256), 256, 0, s->stream, P<int>(w.offflag), n_l1,
-                       &P<Counters>(w.ctr)->overflow);
-    }
-    static int maxb = -1;
-    if (maxb < 0) {
-        int dev, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_loop<T>, 256, 0);
-        maxb = std::max(1, sms * std::max(1, std::min(per, 2)));
-    }
-    int64_t work = std::max<int64_t>(12 * (int64_t)w.S_dyn, 12 * n_l1);
-    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(maxb, (work + 255) / 256));
-    const T *diag = P<T>(w.diag), *off = P<T>(w.off), *pinv = P<T>(w.pinv);
-    T *r = P<T>(w.pcg_r), *z = P<T>(w.pcg_z), *pp = P<T>(w.pcg_p), *ap = P<T>(w.pcg_ap);
-    void *args[] = {&A, &diag, &off, &pinv, &r, &z, &pp, &ap};
-    cudaEvent_t ea, eb;
-    prof_begin(s, "pcg", 0, &ea, &eb);
-    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_pcg_loop<T>, blocks, 256, args, 0, s->stream);
-    ++s->n_launches;
-    prof_end(s, ea, eb, prof_index(s, "pcg"));
-    int rc = cuda_check(s, e, "pcg launch");
-    if (rc) return rc;
-    std::vector<PcgPart> h(w.NP);
-    rc = cuda_check(s, cudaMemcpyAsync(h.data(), A.pp, sizeof(PcgPart) * w.NP, cudaMemcpyDeviceToHost, s->stream), "pcg");
-    if (rc || (rc = sync(s))) return rc;
-    int64_t mx = 0;
-    for (auto &q : h) mx = std::max<int64_t>(mx, q.it);
-    *iters = mx;
-    if (s->prof) {
-        // per iteration: diagonal, preconditioner and non-zero off-diagonal
-        // blocks read once; p, Ap, r, z (T) and x (FP64) read/written once
-        int nz = 0;
-        cudaMemcpyAsync(&nz, &P<Counters>(w.ctr)->overflow, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
-        sync(s);
-        double per = 144.0 * sizeof(T) * (2.0 * w.S_dyn + nz) + 12.0 * w.S_dyn * (7.0 * sizeof(T) + 16.0);
-        prof_add_bytes(s, "pcg", per * (double)mx);
-    }
-    return ABD_OK;
+    if (w.cap_l1 == 0) w.cap_l1 = 8 * (int64_t)w.S_all + 4096;
+    if (w.cap_cand == 0) w.cap_cand = 1 << 16;
+    if (w.cap_act == 0) w.cap_act = 1 << 15;
+    if (w.cap_ls == 0) w.cap_ls = 1 << 16;
+    size_t tb = C.precision == ABD_MIXED ? 4 : 8;
+    bool ok = dbuf_ensure(w.l1, 8 * (size_t)w.cap_l1) && dbuf_ensure(w.cand, sizeof(PairRec) * (size_t)w.cap_cand) &&
+              dbuf_ensure(w.act, sizeof(PairRec) * (size_t)w.cap_act) &&
+              dbuf_ensure(w.ls, sizeof(PairRec) * (size_t)w.cap_ls) &&
+              dbuf_ensure(w.off, tb * 144 * (size_t)w.cap_l1) && dbuf_ensure(w.offflag, 4 * (size_t)w.cap_l1) &&
+              dbuf_ensure(w.deferred, 8 * (size_t)w.cap_act + 64) &&
+              dbuf_ensure(w.rowcnt, 4 * (size_t)(w.S_dyn + 2)) && dbuf_ensure(w.rowoff, 4 * (size_t)(w.S_dyn + 2)) &&
+              dbuf_ensure(w.rowcur, 4 * (size_t)(w.S_dyn + 2)) && dbuf_ensure(w.ent, 16 * (size_t)w.cap_l1) &&
+              dbuf_ensure(w.diag, tb * 144 * (size_t)(w.S_dyn ? w.S_dyn : 1)) &&
+              dbuf_ensure(w.pcg_sc, 4 * (size_t)kMaxParts + 64) && dbuf_ensure(C.alphas, 8 * (kLS + 1) * kMaxParts) &&
+              dbuf_ensure(C.nh0, 4 * kMaxParts) && dbuf_ensure(C.decided, 4 * kMaxParts);
+    return ok ? ABD_OK : set_err(s, ABD_E_OOM, "pair lists");
 }
 
-int check_timeout(abd_scene *s) {
-    int t = 0;
-    cudaMemcpyAsync(&t, &P<Counters>(s->w.ctr)->timeout, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
-    int rc = sync(s);
-    if (rc) return rc;
-    return t ? set_err(s, ABD_E_DEVICE_TIMEOUT, "grid barrier wait timed out") : ABD_OK;
+// Grow every list whose count exceeded its capacity (counts from the status).
+void grow_lists(World &w, const Counters &c, bool pcg_over) {
+    auto g = [](int64_t &cap, unsigned long long n) {
+        if ((int64_t)n > cap) cap = (int64_t)n + (int64_t)n / 2 + 1024;
+    };
+    g(w.cap_l1, c.l1); g(w.cap_cand, c.cand); g(w.cap_act, c.act); g(w.cap_ls, c.ls);
+    if (pcg_over) w.ecap_mult *= 2;
 }
 
-// Projected Newton on Eq. 5 for every partition whose `run` flag is set.
+template <class T>
+void launch_pinv(abd_scene *s) {
+    World &w = s->w;
+    if (w.S_dyn > 0)
+        ABD_LAUNCH(s, k_pinv<T>, grid_for(w.S_dyn, 64), 64, 0, s->stream, w.S_dyn, P<int>(w.slot_part),
+                   P<PartState>(w.part), P<T>(w.diag), P<T>(w.pinv));
+}
+
+// Projected Newton on Eq. 5 for every partition whose `run` flag is set.  One
+// iteration is enqueued without host round trips (list sizes stay on the
+// device, decisions are made by small kernels) and ends with one status read;
+// an iteration whose lists overflowed is redone with larger buffers.
 int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &maxed) {
     abd_scene *s = C.s;
     World &w = s->w;
     const abd_step_params *p = C.p;
+    int rc = ensure_lists(C);
+    if (rc) return rc;
+    Status *hs = pinned_status(s);
+    if (!hs) return set_err(s, ABD_E_OOM, "pinned status");
     std::vector<PartState> ps(w.NP);
     for (int i = 0; i < w.NP; ++i) {
         memset(&ps[i], 0, sizeof(PartState));
         ps[i].active = run[i];
+        ps[i].toi = 0x3FF0000000000000ull;
     }
-    int rc = write_parts(s, ps);
-    if (rc) return rc;
-    if (!dbuf_ensure(C.alphas, 8 * (kLS + 1) * (size_t)w.NP) || !dbuf_ensure(C.nh0, 4 * (size_t)w.NP) ||
-        !dbuf_ensure(C.decided, 4 * (size_t)w.NP) || !dbuf_ensure(C.pending, 4))
-        return set_err(s, ABD_E_OOM, "line search");
-    std::vector<int> active = run;
-    for (int it = 0; it < p->max_newton; ++it) {
-        bool any = false;
-        for (int i = 0; i < w.NP; ++i) any |= active[i] != 0;
-        if (!any) break;
+    if ((rc = write_parts(s, ps))) return rc;
+    Counters *dc = P<Counters>(w.ctr);
+    int *d_iters = P<int>(w.pcg_sc);
+    bool static_bp = true, any = false;
+    for (int i = 0; i < w.NP; ++i) any |= run[i] != 0;
+    int it = 0;
+    while (any && it < p->max_newton) {
         double t0 = now_ms();
-        // active set at q
+        cudaMemsetAsync(&dc->bad, 0, sizeof(int), s->stream);
+        cudaMemsetAsync(d_iters, 0, sizeof(int) * (kMaxParts + 2), s->stream);
+        // active set at q: static broad phase on the first iteration, then the
+        // previous line-search list (q lies on that swept path)
         if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x), nullptr, 0))) return rc;
-        if ((rc = launch_boxes(s, P<double>(w.x), nullptr, C.half, P<double>(w.box)))) return rc;
-        int64_t n_l1 = 0, n_cand = 0, n_act = 0;
-        if ((rc = launch_l1(s, P<double>(w.box), &n_l1))) return rc;
-        if ((rc = launch_l2(s, 1, P<double>(w.x), nullptr, C.half, n_l1, nullptr, 0, &n_cand))) return rc;
-        if ((rc = launch_narrow(s, n_cand, p->dhat, &n_act))) return rc;
-        C.st->n_candidates_peak = std::max(C.st->n_candidates_peak, n_cand);
-        C.st->n_active_peak = std::max(C.st->n_active_peak, n_act);
-        double t1 = now_ms();
-        C.t_coll += t1 - t0;
-        if ((rc = launch_assemble(s, C.precision, p, C.kB, n_act, n_l1))) return rc;
-        int64_t pit = 0;
-        rc = C.precision == ABD_MIXED ? pcg_T<float>(C, n_l1, &pit) : pcg_T<double>(C, n_l1, &pit);
-        if (rc) return rc;
-        if ((rc = check_timeout(s))) return rc;
-        C.st->pcg_iters += pit;
-        // Newton stopping test, before the line search
+        if (static_bp) {
+            if ((rc = launch_boxes(s, P<double>(w.x), nullptr, C.half, P<double>(w.box))) ||
+                (rc = launch_l1_async(s, P<double>(w.box))) ||
+                (rc = launch_l2_async(s, P<double>(w.x), nullptr, C.half)) ||
+                (rc = launch_narrow_async(s, P<PairRec>(w.cand), &dc->cand, w.cap_cand, p->dhat)))
+                return rc;
+        } else if ((rc = launch_narrow_async(s, P<PairRec>(w.ls), &dc->ls, w.cap_ls, p->dhat))) {
+            return rc;
+        }
+        // assemble, precondition, solve
+        if ((rc = launch_assemble_async(s, C.precision, p, C.kB))) return rc;
+        if (C.precision == ABD_MIXED) launch_pinv<float>(s);
+        else launch_pinv<double>(s);
+        if ((rc = launch_pcg_async(s, C.precision, p))) return rc;
+        // Newton stopping test before the line search
         ABD_LAUNCH(s, k_dqmax, grid_for(w.S_dyn, 128), 128, 0, s->stream, w.S_dyn, P<int>(w.slot_part), P<double>(w.dq),
-                                                              P<PartState>(w.part));
-        if ((rc = read_parts(s, ps))) return rc;
-        bool cont = false;
+                   P<PartState>(w.part));
+        ABD_LAUNCH(s, k_newton_decide, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), 1.0 / (p->h * C.l),
+                   p->newton_tol);
+        // CCD along q -> q + dq over the swept candidates; line-search list
+        if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x1), P<double>(w.dq), 1)) ||
+            (rc = launch_boxes(s, P<double>(w.x), P<double>(w.x1), C.half, P<double>(w.box1))) ||
+            (rc = launch_l1_async(s, P<double>(w.box1))) ||
+            (rc = launch_l2_async(s, P<double>(w.x), P<double>(w.x1), C.half)) || (rc = launch_ccd_async(s, p, true)))
+            return rc;
+        // backtracking on the FP64 energy: two passes of kLS trial steps
+        ABD_LAUNCH(s, k_ls_reset, 1, 64, 0, s->stream, w.NP, P<int>(C.nh0), P<int>(C.decided));
+        for (int pass = 0; pass < 2; ++pass) {
+            cudaMemsetAsync(&dc->pending, 0, sizeof(int), s->stream);
+            ABD_LAUNCH(s, k_ls_alphas, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
+                       P<int>(C.decided), P<double>(C.alphas), p->max_halvings);
+            if ((rc = launch_energy_async(s, p, C.kB, P<double>(C.alphas)))) return rc;
+            ABD_LAUNCH(s, k_ls_select, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
+                       P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->pending);
+        }
+        ABD_LAUNCH(s, k_check_bad, 1, 1, 0, s->stream, dc, w.cap_l1, w.cap_cand, w.cap_act, w.cap_ls,
+                   d_iters + kMaxParts);
+        ABD_LAUNCH(s, k_update_q, grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream, w.S_dyn,
+                   P<int>(w.slot_part), P<PartState>(w.part), P<int>(C.decided), dc, P<double>(w.dq), P<double>(w.q));
+        ABD_LAUNCH(s, k_mark_updated, 1, 64, 0, s->stream, w.NP, P<int>(C.decided), dc);
+        if ((rc = enqueue_status(s, hs)) || (rc = sync(s))) return rc;
+        if (hs->c.bad) {
+            // lists outgrew their buffers: grow, restore the partition state, redo
+            grow_lists(w, hs->c, hs->pcg_over != 0);
+            if ((rc = ensure_lists(C)) || (rc = write_parts(s, ps))) return rc;
+            static_bp = true;
+            continue;
+        }
+        // rare: line searches still undecided after 2 * kLS halvings
+        for (int guard = 0; hs->c.pending > 0 && guard < 64; ++guard) {
+            cudaMemsetAsync(&dc->pending, 0, sizeof(int), s->stream);
+            ABD_LAUNCH(s, k_ls_alphas, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
+                       P<int>(C.decided), P<double>(C.alphas), p->max_halvings);
+            if ((rc = launch_energy_async(s, p, C.kB, P<double>(C.alphas)))) return rc;
+            ABD_LAUNCH(s, k_ls_select, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
+                       P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->pending);
+            ABD_LAUNCH(s, k_update_q, grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream, w.S_dyn,
+                       P<int>(w.slot_part), P<PartState>(w.part), P<int>(C.decided), dc, P<double>(w.dq),
+                       P<double>(w.q));
+            ABD_LAUNCH(s, k_mark_updated, 1, 64, 0, s->stream, w.NP, P<int>(C.decided), dc);
+            if ((rc = enqueue_status(s, hs)) || (rc = sync(s))) return rc;
+        }
+        static_bp = false;
+        ++it;
+        C.st->n_active_peak = std::max<int64_t>(C.st->n_active_peak, (int64_t)hs->c.act);
+        C.st->n_candidates_peak = std::max<int64_t>(C.st->n_candidates_peak, (int64_t)hs->c.cand);
+        int64_t pmax = 0;
+        for (int i = 0; i < w.NP; ++i) pmax = std::max<int64_t>(pmax, hs->pcg_iters[i]);
+        C.st->pcg_iters += pmax;
+        if (s->prof) {
+            // per PCG iteration: diagonal, preconditioner and off-diagonal blocks
+            // read once; p, Ap, r, z (T) and x (FP64) read or written once
+            double tb = C.precision == ABD_MIXED ? 4.0 : 8.0;
+            double per = 144.0 * tb * (2.0 * w.S_dyn + 0.5 * hs->csr_total) + 12.0 * w.S_dyn * (7.0 * tb + 16.0);
+            prof_add_bytes(s, "pcg", per * (double)pmax);
+        }
+        any = false;
         for (int i = 0; i < w.NP; ++i) {
-            if (!active[i]) continue;
-            ++newton_total;
-            double dm = u2d(ps[i].dqmax);
-            if (dm / (p->h * C.l) < p->newton_tol) {
-                active[i] = 0;
-                ps[i].active = 0;
-            } else {
-                cont = true;
-            }
-            ps[i].toi = 0x3FF0000000000000ull;  // 1.0
-            ps[i].dqmax = 0;
+            ps[i] = hs->part[i];
+            any |= ps[i].active != 0;
         }
-        if ((rc = write_parts(s, ps))) return rc;
-        double t2 = now_ms();
-        C.t_solve += t2 - t1;
-        if (!cont) break;
-        // CCD along q -> q + dq
-        if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x1), P<double>(w.dq), 1))) return rc;
-        if ((rc = launch_boxes(s, P<double>(w.x), P<double>(w.x1), C.half, P<double>(w.box1)))) return rc;
-        int64_t n_l1s = 0, n_sw = 0, n_ls = 0;
-        if ((rc = launch_l1(s, P<double>(w.box1), &n_l1s))) return rc;
-        if ((rc = launch_l2(s, 1, P<double>(w.x), P<double>(w.x1), C.half, n_l1s, nullptr, 0, &n_sw))) return rc;
-        if ((rc = launch_ccd(s, n_sw, p, p->dhat, &n_ls, true))) return rc;
-        double t3 = now_ms();
-        C.t_coll += t3 - t2;
-        // backtracking on the FP64 energy, kLS trial steps per pass
-        cudaMemsetAsync(C.nh0.p, 0, 4 * (size_t)w.NP, s->stream);
-        cudaMemsetAsync(C.decided.p, 0, 4 * (size_t)w.NP, s->stream);
-        for (int pass = 0; pass < 64; ++pass) {
-            cudaMemsetAsync(C.pending.p, 0, 4, s->stream);
-            ABD_LAUNCH(s, k_ls_alphas, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0), P<double>(C.alphas),
-                                                 p->max_halvings);
-            if ((rc = launch_energy(s, p, C.kB, n_ls, P<double>(C.alphas)))) return rc;
-            ABD_LAUNCH(s, k_ls_select, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0), P<int>(C.decided),
-                                                 P<double>(C.alphas), p->max_halvings, P<int>(C.pending));
-            int pend = 0;
-            cudaMemcpyAsync(&pend, C.pending.p, 4, cudaMemcpyDeviceToHost, s->stream);
-            if ((rc = sync(s))) return rc;
-            if (!pend) break;
-        }
-        ABD_LAUNCH(s, k_update_q, grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream, w.S_dyn, P<int>(w.slot_part),
-                                                                               P<PartState>(w.part), P<double>(w.dq),
-                                                                               P<double>(w.q));
-        if ((rc = cuda_check(s, cudaGetLastError(), "line search"))) return rc;
-        C.t_solve += now_ms() - t3;
-        if (it == p->max_newton - 1) maxed = 1;
+        C.t_solve += now_ms() - t0;
     }
+    for (int i = 0; i < w.NP; ++i) newton_total += ps[i].newton_it;
+    if (any) maxed = 1;
     return ABD_OK;
 }
 
@@ -835,25 +691,35 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
 int merge_check(Ctx &C, bool &ok) {
     abd_scene *s = C.s;
     World &w = s->w;
+    int rc = ensure_lists(C);
+    if (rc) return rc;
+    Status *hs = pinned_status(s);
+    if (!hs) return set_err(s, ABD_E_OOM, "pinned status");
     std::vector<PartState> ps(w.NP);
     for (int i = 0; i < w.NP; ++i) {
         memset(&ps[i], 0, sizeof(PartState));
         ps[i].active = 1;
         ps[i].toi = 0x3FF0000000000000ull;
     }
-    int rc = write_parts(s, ps);
-    if (rc) return rc;
-    if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x), nullptr, 0))) return rc;
-    if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x1), P<double>(w.z), 2))) return rc;
-    if ((rc = launch_boxes(s, P<double>(w.x), P<double>(w.x1), C.half, P<double>(w.box1)))) return rc;
-    int64_t n_l1 = 0, n_sw = 0, n_ls = 0;
-    if ((rc = launch_l1(s, P<double>(w.box1), &n_l1))) return rc;
-    if ((rc = launch_l2(s, 1, P<double>(w.x), P<double>(w.x1), C.half, n_l1, nullptr, 0, &n_sw))) return rc;
-    if ((rc = launch_ccd(s, n_sw, C.p, C.p->dhat, &n_ls, false))) return rc;
-    if ((rc = read_parts(s, ps))) return rc;
-    ok = true;
-    for (auto &q : ps) ok &= q.toi == 0x3FF0000000000000ull;
-    return ABD_OK;
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        if ((rc = write_parts(s, ps))) return rc;
+        if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x), nullptr, 0)) ||
+            (rc = launch_transform(s, P<double>(w.q), P<double>(w.x1), P<double>(w.z), 2)) ||
+            (rc = launch_boxes(s, P<double>(w.x), P<double>(w.x1), C.half, P<double>(w.box1))) ||
+            (rc = launch_l1_async(s, P<double>(w.box1))) ||
+            (rc = launch_l2_async(s, P<double>(w.x), P<double>(w.x1), C.half)) || (rc = launch_ccd_async(s, C.p, false)))
+            return rc;
+        if ((rc = enqueue_status(s, hs)) || (rc = sync(s))) return rc;
+        if ((int64_t)hs->c.l1 > w.cap_l1 || (int64_t)hs->c.cand > w.cap_cand) {
+            grow_lists(w, hs->c, false);
+            if ((rc = ensure_lists(C))) return rc;
+            continue;
+        }
+        ok = true;
+        for (int i = 0; i < w.NP; ++i) ok &= hs->part[i].toi == 0x3FF0000000000000ull;
+        return ABD_OK;
+    }
+    return set_err(s, ABD_E_PAIR_OVERFLOW, "merge check: lists keep overflowing");
 }
 
 int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool force_mono) {

@@ -11,6 +11,9 @@ struct L2Args {
     const double *erest2;
     const double *x0, *x1, *box;
     double half;
+    const float *xb0, *xb1;  // FP32 vertex bounds [SV][6] (lo, hi) of x0, x1
+    const float *boxf;       // FP32 slot boxes (outward)
+    float halfu;             // dhat / 2 rounded up to FP32
     const int2 *l1;
     int64_t n_l1;                          // used when n_l1_dev is null
     const unsigned long long *n_l1_dev;    // device count of level-1 pairs (clamped to n_l1)
@@ -24,15 +27,21 @@ struct L2Args {
 constexpr int kL2Warps = 4;
 
 // Level-2 pass over primitive clusters: the L2Args fields plus the cluster
-// orders and the per-slot cluster boxes.
+// orders, the cluster table, the per-slot cluster boxes and the cluster-pair
+// list that links its two stages.
 struct L2cArgs {
     L2Args a;
     const int *vperm, *tperm, *eperm;
     const int *slot_cbase;
-    const double *cbox;
+    const int2 *cl_info;     // [C] (slot, kind << 24 | cluster index within the kind)
+    const float *cbox;       // [C][6] inflated FP32 cluster boxes (outward)
+    int4 *cp;                // cluster pairs (c1, c2, level-1 pair, job)
+    int64_t cap_cp;
+    unsigned long long *n_cp;
 };
 
-__global__ void __launch_bounds__(32 * kL2Warps) k_l2c(L2cArgs A);
+__global__ void __launch_bounds__(32 * kL2Warps) k_cpairs(L2cArgs A);
+__global__ void __launch_bounds__(32 * kL2Warps, 6) k_l2p(L2cArgs A);
 
 __global__ void k_boxes(int S, const int64_t *__restrict__ slot_voff, const double *__restrict__ x0,
                         const double *__restrict__ x1, double half, double *__restrict__ box);

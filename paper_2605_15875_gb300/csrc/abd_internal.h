@@ -60,7 +60,7 @@ struct SceneDev {
     // rest-frame Morton order (body-local ids), chunked by 32
     DBuf vperm, tperm, eperm;
     DBuf cbody_off;  // [B + 1] first cluster of each body (vertices, triangles, edges)
-    DBuf crest;      // [clusters][6] rest-frame box of each cluster's vertices (centre, half extent)
+    DBuf crest;      // [clusters][6] FP32 rest-frame box of each cluster's vertices (centre, half extent)
 };
 
 constexpr int kClusterSize = 32;
@@ -71,7 +71,8 @@ struct World {
     int64_t SV = 0;
     DBuf slot_body, slot_part, slot_voff, slot_mask, slot_rep, slot_kw, sv_slot;
     DBuf q, qprev, qtil, z, u, rho, dq, g;
-    DBuf x, x1, dx, box, box1;
+    DBuf x, x1, dx, box, box1;  // box, box1: [S][6] FP32 slot boxes (outward)
+    DBuf xb, xb1;               // [SV][6] FP32 bounds (rounded down, up) of x, x1
     DBuf rep_off, rep_slot, zb, rho0, rhob, rb, sb, body_rep, body_slot;
     DBuf l1, cand, act, ls, diag, off, offflag, pinv;
     DBuf pcg_r, pcg_z, pcg_p, pcg_ap, pcg_sc;
@@ -85,8 +86,9 @@ struct World {
     DBuf slot_cbase;   // [S_all + 1] first cluster of each slot
     DBuf cl_info;      // [C] (slot, kind << 24 | cluster index)
     DBuf cbox, cbox1;  // [C][6] cluster boxes (static, swept)
+    DBuf cp;           // [cap_cp] int4 cluster pairs of the level-2 pass
     int64_t C = 0;
-    int64_t cap_l1 = 0, cap_cand = 0, cap_act = 0, cap_ls = 0;
+    int64_t cap_l1 = 0, cap_cand = 0, cap_act = 0, cap_ls = 0, cap_cp = 0;
     int ecap_mult = 16;  // PCG neighbour-list capacity per owned slot
     // host mirrors
     std::vector<int> h_slot_body, h_slot_part;
@@ -108,7 +110,7 @@ struct PartState {
 };
 
 struct Counters {
-    unsigned long long l1, cand, act, ls;
+    unsigned long long l1, cand, act, ls, cp;
     unsigned long long rinf, sinf, dinf;  // ordered doubles
     int overflow;
     int timeout;
@@ -161,15 +163,22 @@ namespace abd {
 
 // ---- launchers (abd_broad.cu) ----
 int launch_transform(abd_scene *s, const double *q_slots, double *x, const double *qalt, int use_alt_shared);
-int launch_boxes(abd_scene *s, const double *x0, const double *x1, double half, double *box);
-int launch_l1(abd_scene *s, const double *box, int64_t *count);
-// mode 0: candidates as (type, gid_i, gid_j) triples into out3; mode 1: PairRec into recs
-int launch_l2(abd_scene *s, int mode, const double *x0, const double *x1, double half, int64_t n_l1, int32_t *out3,
-              int64_t cap, int64_t *count);
+// FP32 bounds of caller positions already in w.x (and w.x1 when swept).
+int launch_vert_bounds(abd_scene *s, bool swept);
+// FP32 slot boxes of w.xb (and w.xb1 when swept) and the matching cluster
+// boxes: cmode -2 gathers the vertex bounds; otherwise they come from the slot
+// DOFs w.q with the second configuration of k_transform's mode cmode (1: q +
+// alt, 2: shared slots at alt).
+int launch_boxes(abd_scene *s, bool swept, double half, int cmode, const double *alt);
+// Level-1 slot pairs (synchronous, with capacity growth)
+int launch_l1(abd_scene *s, bool swept, int64_t *count);
+// Level-2 candidates over w.x (and w.x1): mode 0 writes triples to out3, mode
+// 1 PairRecs to w.cand (synchronous, with capacity growth)
+int launch_l2(abd_scene *s, int mode, bool swept, double half, int64_t n_l1, int32_t *out3, int64_t cap,
+              int64_t *count);
+int launch_l1_async(abd_scene *s, bool swept);
+int launch_l2_async(abd_scene *s, bool swept, double half);
 // ---- (abd_assemble.cu) ----
-// asynchronous variants: device-resident counts, capacity-clamped
-int launch_l1_async(abd_scene *s, const double *box);
-int launch_l2_async(abd_scene *s, const double *x0, const double *x1, double half);
 int launch_narrow_async(abd_scene *s, const PairRec *src, const unsigned long long *src_n, int64_t src_cap,
                         double dhat);
 int launch_assemble_async(abd_scene *s, int precision, const abd_step_params *p, double kB);

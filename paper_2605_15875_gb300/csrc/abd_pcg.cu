@@ -2,12 +2,22 @@
 //
 // One cluster per partition solves H dq = -g of that partition's Newton step
 // (Eq. 5).  The partition's slots are split evenly over the cluster's CTAs;
-// each CTA keeps its rows of p, Ap, r, z, x in shared memory, reads the
-// neighbours' p through distributed shared memory (DSMEM), and the three dot
-// products of an iteration are reduced first inside the CTA, then across the
-// cluster by reading every CTA's partial in rank order, so all CTAs take
-// identical step sizes and the same termination decision.  Cluster barriers
-// are hardware barriers; there is no spin-wait in this file.
+// each CTA keeps its rows of p, Ap, r, z, x in shared memory together with
+// its diagonal, preconditioner and off-diagonal blocks and a copy of the
+// neighbours' p for its off-diagonal entries.  An iteration has two cluster
+// barriers: after each dot product every CTA pushes its partial into every
+// CTA's shared memory (DSMEM stores), the barrier publishes them, and each CTA
+// adds the partials in rank order, so all CTAs take bit-identical step sizes
+// and the same termination decision.  The neighbours' new p is rebuilt
+// locally as z + beta p from their z, which the second barrier has already
+// published, so no third barrier is needed (unless some entries did not fit
+// in shared memory and are read from the owner's p directly).  Cluster
+// barriers are hardware barriers; there is no spin-wait in this file.
+//
+// The block type T is also the type of every scalar and of x: the mixed path
+// runs the whole solve in FP32 (FP64 instructions are scarce on this GPU and
+// the Newton direction only needs the PCG tolerance); the FP64 path is FP64
+// throughout.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -33,42 +43,42 @@ struct PcgClArgs {
     int *iters;           // [NP] iterations used
 };
 
-// Dynamic shared memory of one CTA owning m slots: p, Ap, r, z (T), x
-// (double) for 12 m rows, reduction words, then (as far as the budget goes)
-// its diagonal and preconditioner blocks and, per off-diagonal entry of its
-// rows, the neighbour id, the block (staged row-major in the orientation the
-// row needs) and the neighbour's gathered p.
+// Dynamic shared memory of one CTA owning m slots: p, Ap, r, z, x (all T)
+// for 12 m rows, 64 partial words, 32 reduction words, m + 1 row
+// offsets, its diagonal and preconditioner blocks, then (as far as the budget
+// goes) per off-diagonal entry of its rows the neighbour id, the block (staged
+// row-major in the orientation the row needs) and the neighbour's p.
 template <class T>
 __host__ __device__ inline size_t pcg_base_bytes(int m) {
     size_t rows = 12 * (size_t)m;
-    return rows * (4 * sizeof(T) + sizeof(double)) + 64 * sizeof(double) + 16 + 2 * 144 * sizeof(T) * (size_t)m;
+    return rows * 5 * sizeof(T) + 16 + 96 * sizeof(T) + 4 * ((size_t)m + 1) + 16 + 2 * 144 * sizeof(T) * (size_t)m;
 }
 
-__device__ __forceinline__ double block_sum(double v, double *scratch) {
-    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) scratch[w] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += scratch[i];
-    return t;
-}
-
-// Sum of word `k` of every CTA's partials across the cluster: lane q of warp
-// 0 reads CTA q's value through DSMEM, a fixed shuffle tree adds them (the
-// same order in every CTA, so every CTA gets bit-identical sums), and the
-// result is broadcast through local shared memory.  nk <= 3 words at a time.
-__device__ __forceinline__ void cluster_sum(cg::cluster_group &cl, double *red, double *out, int k0, int nk, int CS) {
-    if (threadIdx.x < 32) {
-        int lane = threadIdx.x;
-        for (int k = 0; k < nk; ++k) {
-            double v = lane < CS ? cl.map_shared_rank(red, lane)[k0 + k] : 0.0;
-            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) out[k] = v;
-        }
+// Block-wide sums of two values (every thread gets both).  Callers separate
+// consecutive calls by a barrier, which protects the scratch words.
+template <class R>
+__device__ __forceinline__ void block_sum2(R &a, R &b, R *scratch) {
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
     }
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { scratch[2 * w] = a; scratch[2 * w + 1] = b; }
     __syncthreads();
+    a = R(0);
+    b = R(0);
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += scratch[2 * i]; b += scratch[2 * i + 1]; }
+}
+
+// Thread q < CS stores this CTA's values v[0..nk) at words base + nk * rank + k
+// of CTA q's partial array.
+template <class R>
+__device__ __forceinline__ void push_partials(cg::cluster_group &cl, R *red, int base, const R *v, int nk, int rank,
+                                              int CS) {
+    if ((int)threadIdx.x < CS) {
+        R *dst = cl.map_shared_rank(red, (int)threadIdx.x) + base + nk * rank;
+        for (int k = 0; k < nk; ++k) dst[k] = v[k];
+    }
 }
 
 template <class T>
@@ -81,15 +91,17 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
     const int m = (n + CS - 1) / CS;
     const int my0 = s0 + rank * m, my1 = min(s1, my0 + m), mine = max(0, my1 - my0);
     const T *diag = (const T *)A.diag, *pinv = (const T *)A.pinv, *off = (const T *)A.off;
+    using R = T;  // scalars and x: FP32 in the mixed path, FP64 otherwise
 
     extern __shared__ __align__(16) unsigned char smem[];
     const int rows = 12 * m;
     T *p = (T *)smem, *Ap = p + rows, *r = Ap + rows, *z = r + rows;
-    double *x = (double *)(((uintptr_t)(z + rows) + 15) & ~uintptr_t(15));
-    double *red = x + rows;      // [8] partials
-    double *scratch = red + 8;   // [<= 32] block reduction
-    T *Ds = (T *)(scratch + 48); // [m][144] diagonal blocks
-    T *Ps = Ds + 144 * m;        // [m][144] preconditioner blocks
+    R *x = (R *)(((uintptr_t)(z + rows) + 15) & ~uintptr_t(15));
+    R *red = x + rows;      // [64] partials: [0,16) p.Ap, [16,48) (r.r, r.z), [48,64) flags
+    R *scratch = red + 64;  // [32] block reduction
+    int *rofs = (int *)(scratch + 32);                                  // [m + 1] my entry ranges
+    T *Ds = (T *)(((uintptr_t)(rofs + m + 1) + 15) & ~uintptr_t(15));  // [m][144] diagonal blocks
+    T *Ps = Ds + 144 * m;                                              // [m][144] preconditioner blocks
     unsigned char *tail = (unsigned char *)(Ps + 144 * m);
 
     const bool active = A.part[part].active != 0 && n > 0;
@@ -105,18 +117,13 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
     const int es = min(ne, (int)(left / per_e));  // staged entries
     int *enb = (int *)tail;                        // [es] neighbour slot
     T *Bs = (T *)(((uintptr_t)(enb + es) + 15) & ~uintptr_t(15));  // [es][144]
-    T *gp = Bs + 144 * (size_t)es;                                 // [es][12]
+    T *gp = Bs + 144 * (size_t)es;                                 // [es][12] neighbours' p
     for (int e = threadIdx.x; e < 144 * mine; e += blockDim.x) {
         Ds[e] = diag[144 * (int64_t)my0 + e];
         Ps[e] = pinv[144 * (int64_t)my0 + e];
     }
-    for (int sl = 0; sl < mine; ++sl)
-        for (int k = A.rowoff[my0 + sl] + threadIdx.x; k < A.rowoff[my0 + sl + 1]; k += blockDim.x) {
-            int j = k - e0;
-            if (j >= es) continue;
-            enb[j] = A.ent[k].x;
-        }
-    __syncthreads();
+    for (int sl = threadIdx.x; sl <= mine; sl += blockDim.x) rofs[sl] = A.rowoff[my0 + sl] - e0;
+    for (int j = threadIdx.x; j < es; j += blockDim.x) enb[j] = A.ent[e0 + j].x;
     for (int64_t e = threadIdx.x; e < 144 * (int64_t)es; e += blockDim.x) {
         int j = (int)(e / 144), q = (int)(e % 144), i = q / 12, c = q % 12;
         int2 en = A.ent[e0 + j];
@@ -124,12 +131,12 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
         Bs[e] = en.y < 0 ? B[12 * c + i] : B[12 * i + c];  // row i of the block as row slot sees it
     }
     // r = -g, x = 0, z = P r, p = z
-    double rr0 = 0.0, rz_loc = 0.0;
     for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
         r[e] = T(-A.g[12 * (int64_t)my0 + e]);
-        x[e] = 0.0;
+        x[e] = R(0);
     }
     __syncthreads();
+    R rr0 = R(0), rz = R(0);
     for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
         int sl = e / 12, i = e % 12;
         const T *M = Ps + 144 * sl + 12 * i;
@@ -137,43 +144,44 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
         for (int j = 0; j < 12; ++j) t += M[j] * r[12 * sl + j];
         z[e] = t;
         p[e] = t;
-        rr0 += (double)r[e] * (double)r[e];
-        rz_loc += (double)r[e] * (double)t;
+        rr0 += r[e] * r[e];
+        rz += r[e] * t;
     }
-    rr0 = block_sum(rr0, scratch);
-    rz_loc = block_sum(rz_loc, scratch);
-    double *tot = scratch + 40;  // cluster sums, local copy
-    if (threadIdx.x == 0) { red[0] = rr0; red[1] = rz_loc; }
+    block_sum2(rr0, rz, scratch);
+    {
+        R v[2] = {rr0, rz}, f = es < ne ? R(1) : R(0);
+        push_partials(cl, red, 16, v, 2, rank, CS);
+        push_partials(cl, red, 48, &f, 1, rank, CS);
+    }
     cl.sync();
-    cluster_sum(cl, red, tot, 0, 2, CS);
-    double r0 = tot[0], rz = tot[1];
+    R r0 = R(0), unstaged = R(0);
+    rz = R(0);
+    for (int q = 0; q < CS; ++q) { r0 += red[16 + 2 * q]; rz += red[17 + 2 * q]; unstaged += red[48 + q]; }
+    const bool need_sync3 = unstaged > R(0);  // some CTA reads owners' p directly
+    // neighbours' p (= z) of the staged entries
+    for (int e = threadIdx.x; e < 12 * es; e += blockDim.x) {
+        int j = e / 12, i = e % 12, nb = enb[j];
+        int o = (nb - s0) / m, lo = (nb - s0) - o * m;
+        gp[e] = (o == rank ? p : cl.map_shared_rank(p, o))[12 * lo + i];
+    }
+    __syncthreads();
     int it = 0;
-    bool done = !(r0 > 0.0);  // identical in every CTA of the cluster
-    cl.sync();  // partials read before they are overwritten
+    bool done = !(r0 > R(0));  // identical in every CTA of the cluster
     while (!done && it < A.max_it) {
-        // gather the neighbours' p of the staged entries (local or DSMEM)
-        for (int e = threadIdx.x; e < 12 * es; e += blockDim.x) {
-            int j = e / 12, i = e % 12, nb = enb[j];
-            int o = (nb - s0) / m, lo = (nb - s0) - o * m;
-            const T *pn = (o == rank ? p : cl.map_shared_rank(p, o)) + 12 * lo;
-            gp[e] = pn[i];
-        }
-        __syncthreads();
         // Ap = H p over my rows, p . Ap
-        double pap = 0.0;
+        R pap = R(0), unused = R(0);
         for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
             int sl = e / 12, i = e % 12;
             const T *D = Ds + 144 * sl + 12 * i;
             T acc = T(0);
             for (int j = 0; j < 12; ++j) acc += D[j] * p[12 * sl + j];
-            for (int k = A.rowoff[my0 + sl]; k < A.rowoff[my0 + sl + 1]; ++k) {
-                int jj = k - e0;
+            for (int jj = rofs[sl]; jj < rofs[sl + 1]; ++jj) {
                 if (jj < es) {
                     const T *B = Bs + 144 * jj + 12 * i;
                     const T *pn = gp + 12 * jj;
                     for (int c = 0; c < 12; ++c) acc += B[c] * pn[c];
                 } else {
-                    int2 en = A.ent[k];
+                    int2 en = A.ent[e0 + jj];
                     int nb = en.x, bi = en.y;
                     const T *B = off + 144 * (int64_t)(bi & 0x7fffffff);
                     int o = (nb - s0) / m, lo = (nb - s0) - o * m;
@@ -185,44 +193,55 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
                 }
             }
             Ap[e] = acc;
-            pap += (double)p[e] * (double)acc;
+            pap += p[e] * acc;
         }
-        pap = block_sum(pap, scratch);
-        if (threadIdx.x == 0) red[2] = pap;
+        block_sum2(pap, unused, scratch);
+        push_partials(cl, red, 0, &pap, 1, rank, CS);
         cl.sync();
-        cluster_sum(cl, red, tot, 2, 1, CS);
-        double alpha = rz / tot[0];
+        R papt = R(0);
+        for (int q = 0; q < CS; ++q) papt += red[q];
+        R alpha = rz / papt;
         for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
-            x[e] += alpha * (double)p[e];
-            r[e] = T((double)r[e] - alpha * (double)Ap[e]);
+            x[e] += alpha * p[e];
+            r[e] = r[e] - alpha * Ap[e];
         }
         __syncthreads();
-        double rrl = 0.0, rzl = 0.0;
+        R rrl = R(0), rzl = R(0);
         for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
             int sl = e / 12, i = e % 12;
             const T *M = Ps + 144 * sl + 12 * i;
             T t = T(0);
             for (int j = 0; j < 12; ++j) t += M[j] * r[12 * sl + j];
             z[e] = t;
-            rrl += (double)r[e] * (double)r[e];
-            rzl += (double)r[e] * (double)t;
+            rrl += r[e] * r[e];
+            rzl += r[e] * t;
         }
-        rrl = block_sum(rrl, scratch);
-        rzl = block_sum(rzl, scratch);
-        if (threadIdx.x == 0) { red[3] = rrl; red[4] = rzl; }
-        cl.sync();
-        cluster_sum(cl, red, tot, 3, 2, CS);
-        double rrt = tot[0], rzn = tot[1];
+        block_sum2(rrl, rzl, scratch);
+        {
+            R v[2] = {rrl, rzl};
+            push_partials(cl, red, 16, v, 2, rank, CS);
+        }
+        cl.sync();  // partials and every CTA's z published
+        R rrt = R(0), rzn = R(0);
+        for (int q = 0; q < CS; ++q) { rrt += red[16 + 2 * q]; rzn += red[17 + 2 * q]; }
         ++it;
-        done = rrt <= A.tol2 * r0;
+        done = rrt <= R(A.tol2) * r0;
         if (!done) {
-            double beta = rzn / rz;
+            R beta = rzn / rz;
             rz = rzn;
-            for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) p[e] = T((double)z[e] + beta * (double)p[e]);
+            for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) p[e] = z[e] + beta * p[e];
+            // the same update of the neighbours' copies, from their published z
+            for (int e = threadIdx.x; e < 12 * es; e += blockDim.x) {
+                int j = e / 12, i = e % 12, nb = enb[j];
+                int o = (nb - s0) / m, lo = (nb - s0) - o * m;
+                T zn = (o == rank ? z : cl.map_shared_rank(z, o))[12 * lo + i];
+                gp[e] = zn + beta * gp[e];
+            }
+            if (need_sync3) cl.sync();  // owners' new p visible to direct readers
+            else __syncthreads();
         }
-        cl.sync();  // new p visible to the cluster; partials free for reuse
     }
-    for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) A.x[12 * (int64_t)my0 + e] = x[e];
+    for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) A.x[12 * (int64_t)my0 + e] = (double)x[e];
     if (rank == 0 && threadIdx.x == 0) A.iters[part] = it;
 }
 

@@ -335,7 +335,7 @@ extern "C" int abd_scene_create(const abd_scene_desc *d, void *stream, abd_scene
               upload(s, D.tperm, s->tperm.data(), s->tperm.size() * 4) &&
               upload(s, D.eperm, s->eperm.data(), s->eperm.size() * 4) &&
               upload(s, D.cbody_off, s->cbody_off.data(), s->cbody_off.size() * 4) &&
-              upload(s, D.crest, s->crest.data(), s->crest.size() * 8);
+              upload(s, D.crest, std::vector<float>(s->crest.begin(), s->crest.end()).data(), s->crest.size() * 4);
     if (!ok) {
         abd_scene_destroy(s);
         cudaGetLastError();
@@ -357,7 +357,7 @@ extern "C" void abd_scene_destroy(abd_scene *s) {
                   &w.q, &w.qprev, &w.qtil, &w.z, &w.u, &w.rho, &w.dq, &w.g, &w.x, &w.x1, &w.dx, &w.box, &w.box1,
                   &w.rep_off, &w.rep_slot, &w.zb, &w.rho0, &w.rhob, &w.rb, &w.sb, &w.body_rep, &w.body_slot,
                   &w.l1, &w.cand, &w.act, &w.ls, &w.diag, &w.off, &w.offflag, &w.pinv, &w.pcg_r, &w.pcg_z,
-                  &w.pcg_p, &w.pcg_ap, &w.pcg_sc, &w.part, &w.ctr, &w.bar, &w.aabb, &w.part_off, &w.deferred, &w.rowcnt, &w.rowoff, &w.rowcur, &w.ent, &w.slot_cbase, &w.cl_info, &w.cbox, &w.cbox1};
+                  &w.pcg_p, &w.pcg_ap, &w.pcg_sc, &w.part, &w.ctr, &w.bar, &w.aabb, &w.part_off, &w.deferred, &w.rowcnt, &w.rowoff, &w.rowcur, &w.ent, &w.slot_cbase, &w.cl_info, &w.cbox, &w.cbox1, &w.cp, &w.xb, &w.xb1};
     for (DBuf *b : wb) dbuf_free(*b);
     if (s->pinned) cudaFreeHost(s->pinned);
     for (auto &pe : s->ev_pending) {

@@ -198,10 +198,11 @@ __global__ void k_ls_select(int NP, PartState *part, int *nh0, int *decided, con
 }
 
 // Flag an iteration whose lists outgrew their buffers (its results are void).
+// The swept lists contain the static ones, so their counts bound both passes.
 __global__ void k_check_bad(Counters *c, int64_t cap_l1, int64_t cap_cand, int64_t cap_act, int64_t cap_ls,
-                            const int *pcg_over) {
+                            int64_t cap_cp, const int *pcg_over) {
     c->bad = ((int64_t)c->l1 > cap_l1 || (int64_t)c->cand > cap_cand || (int64_t)c->act > cap_act ||
-              (int64_t)c->ls > cap_ls || *pcg_over)
+              (int64_t)c->ls > cap_ls || (int64_t)c->cp > cap_cp || *pcg_over)
                  ? 1
                  : c->bad;
 }
@@ -474,6 +475,7 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
               dbuf_ensure(w.qtil, 96 * Sd) && dbuf_ensure(w.z, 96 * Sd) && dbuf_ensure(w.u, 96 * Sd) &&
               dbuf_ensure(w.rho, 8 * Sd) && dbuf_ensure(w.dq, 96 * Sd) && dbuf_ensure(w.g, 96 * Sd) &&
               dbuf_ensure(w.x, 24 * SV) && dbuf_ensure(w.x1, 24 * SV) && dbuf_ensure(w.box, 48 * S) &&
+              dbuf_ensure(w.xb, 24 * SV) && dbuf_ensure(w.xb1, 24 * SV) &&
               dbuf_ensure(w.box1, 48 * S) && dbuf_ensure(w.zb, 96 * NS) && dbuf_ensure(w.rho0, 8 * NS) &&
               dbuf_ensure(w.rhob, 8 * NS) && dbuf_ensure(w.rb, 8 * NS) && dbuf_ensure(w.sb, 8 * NS) &&
               dbuf_ensure(w.part, sizeof(PartState) * kMaxParts) && dbuf_ensure(w.ctr, sizeof(Counters)) &&
@@ -537,10 +539,11 @@ int ensure_lists(Ctx &C) {
     if (w.cap_cand == 0) w.cap_cand = 1 << 16;
     if (w.cap_act == 0) w.cap_act = 1 << 15;
     if (w.cap_ls == 0) w.cap_ls = 1 << 16;
+    if (w.cap_cp == 0) w.cap_cp = 1 << 18;
     size_t tb = C.precision == ABD_MIXED ? 4 : 8;
     bool ok = dbuf_ensure(w.l1, 8 * (size_t)w.cap_l1) && dbuf_ensure(w.cand, sizeof(PairRec) * (size_t)w.cap_cand) &&
               dbuf_ensure(w.act, sizeof(PairRec) * (size_t)w.cap_act) &&
-              dbuf_ensure(w.ls, sizeof(PairRec) * (size_t)w.cap_ls) &&
+              dbuf_ensure(w.ls, sizeof(PairRec) * (size_t)w.cap_ls) && dbuf_ensure(w.cp, sizeof(int4) * (size_t)w.cap_cp) &&
               dbuf_ensure(w.off, tb * 144 * (size_t)w.cap_l1) && dbuf_ensure(w.offflag, 4 * (size_t)w.cap_l1) &&
               dbuf_ensure(w.deferred, 8 * (size_t)w.cap_act + 64) &&
               dbuf_ensure(w.rowcnt, 4 * (size_t)(w.S_dyn + 2)) && dbuf_ensure(w.rowoff, 4 * (size_t)(w.S_dyn + 2)) &&
@@ -556,7 +559,7 @@ void grow_lists(World &w, const Counters &c, bool pcg_over) {
     auto g = [](int64_t &cap, unsigned long long n) {
         if ((int64_t)n > cap) cap = (int64_t)n + (int64_t)n / 2 + 1024;
     };
-    g(w.cap_l1, c.l1); g(w.cap_cand, c.cand); g(w.cap_act, c.act); g(w.cap_ls, c.ls);
+    g(w.cap_l1, c.l1); g(w.cap_cand, c.cand); g(w.cap_act, c.act); g(w.cap_ls, c.ls); g(w.cap_cp, c.cp);
     if (pcg_over) w.ecap_mult *= 2;
 }
 
@@ -600,9 +603,8 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         // previous line-search list (q lies on that swept path)
         if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x), nullptr, 0))) return rc;
         if (static_bp) {
-            if ((rc = launch_boxes(s, P<double>(w.x), nullptr, C.half, P<double>(w.box))) ||
-                (rc = launch_l1_async(s, P<double>(w.box))) ||
-                (rc = launch_l2_async(s, P<double>(w.x), nullptr, C.half)) ||
+            if ((rc = launch_boxes(s, false, C.half, -1, nullptr)) || (rc = launch_l1_async(s, false)) ||
+                (rc = launch_l2_async(s, false, C.half)) ||
                 (rc = launch_narrow_async(s, P<PairRec>(w.cand), &dc->cand, w.cap_cand, p->dhat)))
                 return rc;
         } else if ((rc = launch_narrow_async(s, P<PairRec>(w.ls), &dc->ls, w.cap_ls, p->dhat))) {
@@ -620,9 +622,8 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
                    p->newton_tol);
         // CCD along q -> q + dq over the swept candidates; line-search list
         if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x1), P<double>(w.dq), 1)) ||
-            (rc = launch_boxes(s, P<double>(w.x), P<double>(w.x1), C.half, P<double>(w.box1))) ||
-            (rc = launch_l1_async(s, P<double>(w.box1))) ||
-            (rc = launch_l2_async(s, P<double>(w.x), P<double>(w.x1), C.half)) || (rc = launch_ccd_async(s, p, true)))
+            (rc = launch_boxes(s, true, C.half, 1, P<double>(w.dq))) || (rc = launch_l1_async(s, true)) ||
+            (rc = launch_l2_async(s, true, C.half)) || (rc = launch_ccd_async(s, p, true)))
             return rc;
         // backtracking on the FP64 energy: two passes of kLS trial steps
         ABD_LAUNCH(s, k_ls_reset, 1, 64, 0, s->stream, w.NP, P<int>(C.nh0), P<int>(C.decided));
@@ -634,7 +635,7 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
             ABD_LAUNCH(s, k_ls_select, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
                        P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->pending);
         }
-        ABD_LAUNCH(s, k_check_bad, 1, 1, 0, s->stream, dc, w.cap_l1, w.cap_cand, w.cap_act, w.cap_ls,
+        ABD_LAUNCH(s, k_check_bad, 1, 1, 0, s->stream, dc, w.cap_l1, w.cap_cand, w.cap_act, w.cap_ls, w.cap_cp,
                    d_iters + kMaxParts);
         ABD_LAUNCH(s, k_update_q, grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream, w.S_dyn,
                    P<int>(w.slot_part), P<PartState>(w.part), P<int>(C.decided), dc, P<double>(w.dq), P<double>(w.q));
@@ -705,12 +706,11 @@ int merge_check(Ctx &C, bool &ok) {
         if ((rc = write_parts(s, ps))) return rc;
         if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x), nullptr, 0)) ||
             (rc = launch_transform(s, P<double>(w.q), P<double>(w.x1), P<double>(w.z), 2)) ||
-            (rc = launch_boxes(s, P<double>(w.x), P<double>(w.x1), C.half, P<double>(w.box1))) ||
-            (rc = launch_l1_async(s, P<double>(w.box1))) ||
-            (rc = launch_l2_async(s, P<double>(w.x), P<double>(w.x1), C.half)) || (rc = launch_ccd_async(s, C.p, false)))
+            (rc = launch_boxes(s, true, C.half, 2, P<double>(w.z))) || (rc = launch_l1_async(s, true)) ||
+            (rc = launch_l2_async(s, true, C.half)) || (rc = launch_ccd_async(s, C.p, false)))
             return rc;
         if ((rc = enqueue_status(s, hs)) || (rc = sync(s))) return rc;
-        if ((int64_t)hs->c.l1 > w.cap_l1 || (int64_t)hs->c.cand > w.cap_cand) {
+        if ((int64_t)hs->c.l1 > w.cap_l1 || (int64_t)hs->c.cand > w.cap_cand || (int64_t)hs->c.cp > w.cap_cp) {
             grow_lists(w, hs->c, false);
             if ((rc = ensure_lists(C))) return rc;
             continue;
@@ -904,15 +904,14 @@ extern "C" int abd_candidates(abd_scene *s, const double *x0, const double *x1, 
     if ((rc = h2d(s, w.x, xs))) return rc;
     if (x1 && (rc = h2d(s, w.x1, xs1))) return rc;
     double half = 0.5 * dhat;
-    if ((rc = launch_boxes(s, P<double>(w.x), x1 ? P<double>(w.x1) : nullptr, half,
-                           x1 ? P<double>(w.box1) : P<double>(w.box))))
+    if ((rc = launch_vert_bounds(s, x1 != nullptr)) || (rc = launch_boxes(s, x1 != nullptr, half, -2, nullptr)))
         return rc;
     int64_t n_l1 = 0, n = 0;
-    if ((rc = launch_l1(s, x1 ? P<double>(w.box1) : P<double>(w.box), &n_l1))) return rc;
+    if ((rc = launch_l1(s, x1 != nullptr, &n_l1))) return rc;
     DBuf tmp;
     int64_t c = std::max<int64_t>(cap, 1);
     if (!dbuf_ensure(tmp, 12 * (size_t)c)) return set_err(s, ABD_E_OOM, "candidates");
-    rc = launch_l2(s, 0, P<double>(w.x), x1 ? P<double>(w.x1) : nullptr, half, n_l1, P<int32_t>(tmp), c, &n);
+    rc = launch_l2(s, 0, x1 != nullptr, half, n_l1, P<int32_t>(tmp), c, &n);
     if (!rc && out && cap > 0)
         rc = cuda_check(s, cudaMemcpy(out, tmp.p, 12 * (size_t)std::min(n, cap), cudaMemcpyDeviceToHost), "candidates");
     dbuf_free(tmp);

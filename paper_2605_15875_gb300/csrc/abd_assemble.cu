@@ -52,8 +52,8 @@ __global__ void k_narrow(const PairRec *__restrict__ cand, int64_t n, const unsi
                          const double *__restrict__ x, double dhat, PairRec *__restrict__ act, int64_t cap,
                          unsigned long long *__restrict__ count) {
     if (n_dev) n = min((int64_t)*n_dev, n);
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = base + threadIdx.x;
+    for (int64_t base = spread_base(); base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + (threadIdx.x & 31);
         bool keep = false;
         PairRec r;
         if (i < n) {
@@ -90,8 +90,9 @@ struct AsmArgs {
 // Per dynamic slot of an active partition: write g and the diagonal block.
 template <class T>
 __global__ void k_slot_assemble(AsmArgs A, T *__restrict__ diag) {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.S_dyn; s += gridDim.x * blockDim.x) {
-        if (!A.part[A.slot_part[s]].active) continue;
+    for (int64_t sb = spread_base(); sb < A.S_dyn; sb += (int64_t)gridDim.x * blockDim.x) {
+        int s = (int)(sb + (threadIdx.x & 31));
+        if (s >= A.S_dyn || !A.part[A.slot_part[s]].active) continue;
         int b = A.slot_body[s];
         double kw = A.slot_kw[s], h2 = A.h * A.h;
         const double *q = A.q + 12 * (int64_t)s, *qt = A.qtil + 12 * (int64_t)s;
@@ -122,16 +123,20 @@ __global__ void k_slot_assemble(AsmArgs A, T *__restrict__ diag) {
         double kv = A.kappa[b] * A.vol[b], c4 = 4.0 * kv * kw * h2;
         for (int k = 0; k < 3; ++k)
             for (int j = 0; j < 3; ++j) g[3 + 3 * k + j] += c4 * (C[k][0] * a[0][j] + C[k][1] * a[1][j] + C[k][2] * a[2][j]);
-        T H9[81];
-        double AtA[3][3];
+        // Hessian of the orthogonality term in the block type T (the
+        // gradient above stays FP64)
+        T H9[81], at[3][3], Ct[3][3], AtA[3][3];
+        for (int k = 0; k < 3; ++k)
+            for (int j = 0; j < 3; ++j) { at[k][j] = T(a[k][j]); Ct[k][j] = T(C[k][j]); }
+        const T kvT = T(kv);
         for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) AtA[i][j] = a[0][i] * a[0][j] + a[1][i] * a[1][j] + a[2][i] * a[2][j];
+            for (int j = 0; j < 3; ++j) AtA[i][j] = at[0][i] * at[0][j] + at[1][i] * at[1][j] + at[2][i] * at[2][j];
         for (int k = 0; k < 3; ++k)
             for (int l = 0; l < 3; ++l)
                 for (int i = 0; i < 3; ++i)
                     for (int j = 0; j < 3; ++j) {
-                        double v = a[l][i] * a[k][j] + (i == j ? C[k][l] : 0.0) + (k == l ? AtA[i][j] : 0.0);
-                        H9[(3 * k + i) * 9 + 3 * l + j] = T(4.0 * kv * v);
+                        T v = at[l][i] * at[k][j] + (i == j ? Ct[k][l] : T(0)) + (k == l ? AtA[i][j] : T(0));
+                        H9[(3 * k + i) * 9 + 3 * l + j] = T(4) * kvT * v;
                     }
         // PSD projection through the analytic eigensystem of the isotropic
         // energy kappa V sum_k (sigma_k^2 - 1)^2: with A = U diag(sigma) V^T and
@@ -140,30 +145,30 @@ __global__ void k_slot_assemble(AsmArgs A, T *__restrict__ diag) {
         // s_j^2 - 1), can be negative; they are removed from H9.  Otherwise the
         // 9x9 Jacobi projection is used.
         {
-            double M3[9], V3[9];
+            T M3[9], V3[9];
             for (int i = 0; i < 3; ++i)
                 for (int j = 0; j < 3; ++j) M3[3 * i + j] = AtA[i][j];
-            jacobi<double, 3>(M3, V3);
-            double sg[3] = {M3[0], M3[4], M3[8]};
-            if (fmin(sg[0], fmin(sg[1], sg[2])) < 1.0 / 3.0 + 1e-3) {
+            jacobi<T, 3>(M3, V3);
+            T sg[3] = {M3[0], M3[4], M3[8]};
+            if (min(sg[0], min(sg[1], sg[2])) < T(1.0 / 3.0 + 1e-3)) {
                 psd_project<T, 9>(H9);
             } else {
-                double sv[3], U3[3][3];
-                for (int k = 0; k < 3; ++k) sv[k] = sqrt(sg[k]);
+                T sv[3], U3[3][3];
+                for (int k = 0; k < 3; ++k) sv[k] = tsqrt(sg[k]);
                 for (int r = 0; r < 3; ++r)
                     for (int k = 0; k < 3; ++k)
-                        U3[r][k] = (a[r][0] * V3[0 * 3 + k] + a[r][1] * V3[1 * 3 + k] + a[r][2] * V3[2 * 3 + k]) / sv[k];
+                        U3[r][k] = (at[r][0] * V3[0 * 3 + k] + at[r][1] * V3[1 * 3 + k] + at[r][2] * V3[2 * 3 + k]) / sv[k];
                 const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
                 for (int t = 0; t < 3; ++t) {
                     int i = pi[t], j = pj[t];
-                    double lam = 4.0 * kv * (sg[i] - sv[i] * sv[j] + sg[j] - 1.0);
-                    if (!(lam < 0.0)) continue;
-                    double v[9];
+                    T lam = T(4) * kvT * (sg[i] - sv[i] * sv[j] + sg[j] - T(1));
+                    if (!(lam < T(0))) continue;
+                    T v[9];
                     for (int r = 0; r < 3; ++r)
                         for (int c = 0; c < 3; ++c)
-                            v[3 * r + c] = (U3[r][i] * V3[c * 3 + j] - U3[r][j] * V3[c * 3 + i]) * 0.70710678118654752;
+                            v[3 * r + c] = (U3[r][i] * V3[c * 3 + j] - U3[r][j] * V3[c * 3 + i]) * T(0.70710678118654752);
                     for (int e = 0; e < 9; ++e)
-                        for (int f = 0; f < 9; ++f) H9[e * 9 + f] -= T(lam * v[e] * v[f]);
+                        for (int f = 0; f < 9; ++f) H9[e * 9 + f] -= lam * v[e] * v[f];
                 }
             }
         }
@@ -191,7 +196,9 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
                                 int64_t *__restrict__ deferred, unsigned long long *__restrict__ n_deferred,
                                 const unsigned long long *__restrict__ n_dev) {
     if (n_dev) n = min((int64_t)*n_dev, n);
-    for (int64_t ii = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; ii < n; ii += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t ib = spread_base(); ib < n; ib += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ii = ib + (threadIdx.x & 31);
+        if (ii >= n) continue;
         // full_path: process the deferred (mollified edge-edge) pairs with the
         // 12x12 projection; otherwise every active pair, deferring those
         int64_t i = full_path ? deferred[ii] : ii;
@@ -297,13 +304,15 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
     }
 }
 
-// Warp-cooperative PSD projection of a symmetric 12x12 matrix held in shared
-// memory: cyclic Jacobi where lane k applies each rotation to row and column
-// k (lanes 16..27 update the eigenvectors), then negative eigenvalues are
-// clamped and the matrix rebuilt.  H is left unchanged when no eigenvalue is
-// negative.  W and V are 144-entry work arrays.
+// Warp-cooperative PSD projection of a symmetric 12x12 matrix H (shared
+// memory): eigen-decomposition by parallel cyclic Jacobi -- per sweep 11
+// rounds of 6 disjoint rotations in round-robin order, every rotation angle
+// of a round computed from the same matrix, columns then rows then the
+// eigenvectors updated by all lanes -- then H = V max(L, 0) V^T if any
+// eigenvalue is negative (H unchanged otherwise).  W, V: [144] scratch,
+// R: [12] scratch for the round's cosines and sines.
 template <class T>
-__device__ void warp_psd12(T *H, T *W, T *V, int lane) {
+__device__ void warp_psd12(T *H, T *W, T *V, T *R, int lane) {
     for (int i = lane; i < 144; i += 32) {
         W[i] = H[i];
         V[i] = (i % 13 == 0) ? T(1) : T(0);
@@ -322,32 +331,46 @@ __device__ void warp_psd12(T *H, T *W, T *V, int lane) {
             tot += __shfl_xor_sync(0xffffffffu, tot, o);
         }
         if (off <= tol * tot || off == T(0)) break;
-        for (int p = 0; p < 11; ++p)
-            for (int q = p + 1; q < 12; ++q) {
-                T apq = W[p * 12 + q];
-                if (apq == T(0)) continue;
-                T theta = (W[q * 12 + q] - W[p * 12 + p]) / (T(2) * apq);
-                T t = (theta >= T(0) ? T(1) : T(-1)) / (tabs(theta) + tsqrt(theta * theta + T(1)));
-                T c = T(1) / tsqrt(t * t + T(1)), sn = t * c;
-                __syncwarp();
-                if (lane < 12) {
-                    T akp = W[lane * 12 + p], akq = W[lane * 12 + q];
-                    W[lane * 12 + p] = c * akp - sn * akq;
-                    W[lane * 12 + q] = sn * akp + c * akq;
+        for (int rd = 0; rd < 11; ++rd) {
+            // pair k of round rd: (rd, 11) for k = 0, ((rd + k) % 11, (rd - k) % 11) otherwise
+            if (lane < 6) {
+                int p = lane == 0 ? rd : (rd + lane) % 11, q = lane == 0 ? 11 : (rd - lane + 11) % 11;
+                if (p > q) { int t = p; p = q; q = t; }
+                T apq = W[p * 12 + q], c = T(1), sn = T(0);
+                if (apq != T(0)) {
+                    T theta = (W[q * 12 + q] - W[p * 12 + p]) / (T(2) * apq);
+                    T t = (theta >= T(0) ? T(1) : T(-1)) / (tabs(theta) + tsqrt(theta * theta + T(1)));
+                    c = T(1) / tsqrt(t * t + T(1));
+                    sn = t * c;
                 }
-                __syncwarp();
-                if (lane < 12) {
-                    T apk = W[p * 12 + lane], aqk = W[q * 12 + lane];
-                    W[p * 12 + lane] = c * apk - sn * aqk;
-                    W[q * 12 + lane] = sn * apk + c * aqk;
-                } else if (lane >= 16 && lane < 28) {
-                    int k = lane - 16;
-                    T vkp = V[k * 12 + p], vkq = V[k * 12 + q];
-                    V[k * 12 + p] = c * vkp - sn * vkq;
-                    V[k * 12 + q] = sn * vkp + c * vkq;
-                }
-                __syncwarp();
+                R[2 * lane] = c;
+                R[2 * lane + 1] = sn;
             }
+            __syncwarp();
+            // columns of W and V: task (row, k), 2 x 72 tasks
+            for (int tk = lane; tk < 144; tk += 32) {
+                int k = (tk % 72) / 12, row = tk % 12;
+                int p = k == 0 ? rd : (rd + k) % 11, q = k == 0 ? 11 : (rd - k + 11) % 11;
+                if (p > q) { int t = p; p = q; q = t; }
+                T c = R[2 * k], sn = R[2 * k + 1];
+                T *M = tk < 72 ? W : V;
+                T mp = M[row * 12 + p], mq = M[row * 12 + q];
+                M[row * 12 + p] = c * mp - sn * mq;
+                M[row * 12 + q] = sn * mp + c * mq;
+            }
+            __syncwarp();
+            // rows of W: task (column, k)
+            for (int tk = lane; tk < 72; tk += 32) {
+                int k = tk / 12, col = tk % 12;
+                int p = k == 0 ? rd : (rd + k) % 11, q = k == 0 ? 11 : (rd - k + 11) % 11;
+                if (p > q) { int t = p; p = q; q = t; }
+                T c = R[2 * k], sn = R[2 * k + 1];
+                T mp = W[p * 12 + col], mq = W[q * 12 + col];
+                W[p * 12 + col] = c * mp - sn * mq;
+                W[q * 12 + col] = sn * mp + c * mq;
+            }
+            __syncwarp();
+        }
     }
     bool neg = __any_sync(0xffffffffu, lane < 12 && W[lane * 13] < T(0));
     if (!neg) return;
@@ -373,13 +396,13 @@ __global__ void __launch_bounds__(128) k_pair_moll(AsmArgs A, const PairRec *__r
                                                    const unsigned long long *__restrict__ n_def, int64_t cap,
                                                    const int2 *__restrict__ l1, T *__restrict__ diag,
                                                    T *__restrict__ off, int *__restrict__ offflag) {
-    __shared__ T sH[4][144], sW[4][144], sV[4][144];
+    __shared__ T sH[4][144], sW[4][144], sV[4][144], sR[4][12];
     __shared__ double sg[4][12], sw[4];
     __shared__ T sxi[4][4][4];
     __shared__ int ssl[4][4], sok[4];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int64_t n = min((int64_t)*n_def, cap);
-    for (int64_t ii = (int64_t)blockIdx.x * 4 + wib; ii < n; ii += (int64_t)gridDim.x * 4) {
+    for (int64_t ii = (int64_t)blockIdx.x + (int64_t)gridDim.x * wib; ii < n; ii += (int64_t)gridDim.x * 4) {
         const PairRec r = act[deferred[ii]];
         if (lane == 0) {
             int sa, sb;
@@ -407,7 +430,7 @@ __global__ void __launch_bounds__(128) k_pair_moll(AsmArgs A, const PairRec *__r
         }
         __syncwarp();
         if (!sok[wib]) continue;
-        warp_psd12<T>(sH[wib], sW[wib], sV[wib], lane);
+        warp_psd12<T>(sH[wib], sW[wib], sV[wib], sR[wib], lane);
         const double w = sw[wib];
         const int *sl = ssl[wib];
         // gradient: 4 vertices x 3 components x 4 xi entries
@@ -539,8 +562,8 @@ __global__ void k_ccd(const PairRec *__restrict__ cand, int64_t n, const unsigne
                       int S_dyn, double dhat, double s_, double c_, PartState *__restrict__ part,
                       PairRec *__restrict__ ls, int64_t cap, unsigned long long *__restrict__ count, int want_ls) {
     if (n_dev) n = min((int64_t)*n_dev, n);
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = base + threadIdx.x;
+    for (int64_t base = spread_base(); base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + (threadIdx.x & 31);
         bool keep = false;
         PairRec r;
         if (i < n) {
@@ -656,8 +679,8 @@ __device__ double slot_energy(const EnArgs &A, int s, double al) {
 }
 
 __global__ void k_energy_slots(EnArgs A) {
-    for (int base = blockIdx.x * blockDim.x; base < A.S_dyn; base += gridDim.x * blockDim.x) {
-        int s = base + threadIdx.x;
+    for (int64_t base = spread_base(); base < A.S_dyn; base += (int64_t)gridDim.x * blockDim.x) {
+        int s = (int)(base + (threadIdx.x & 31));
         int p = s < A.S_dyn ? A.slot_part[s] : -1;
         if (p >= 0 && !A.part[p].active) p = -1;
         if (p >= 0 && A.alphas[(kLS + 1) * p] < 0.0) p = -1;  // partition already decided
@@ -673,8 +696,8 @@ __global__ void k_energy_slots(EnArgs A) {
 __global__ void k_energy_pairs(EnArgs A, const PairRec *__restrict__ ls, int64_t n,
                                const unsigned long long *__restrict__ n_dev) {
     if (n_dev) n = min((int64_t)*n_dev, n);
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = base + threadIdx.x;
+    for (int64_t base = spread_base(); base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + (threadIdx.x & 31);
         int p = -1;
         PairRec r;
         double w = 0.0, X0[12], DX[12];
@@ -707,8 +730,8 @@ __global__ void k_energy_pairs(EnArgs A, const PairRec *__restrict__ ls, int64_t
 }
 
 __global__ void k_energy_vp(EnArgs A, int64_t SVd) {
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < SVd; base += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = base + threadIdx.x;
+    for (int64_t base = spread_base(); base < SVd; base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + (threadIdx.x & 31);
         int p = -1, s = 0;
         if (i < SVd) {
             s = A.sv_slot[i];
@@ -786,7 +809,7 @@ static int assemble_async_T(abd_scene *s, const abd_step_params *p, double kB) {
     cudaEvent_t ea, eb;
     if (w.S_dyn > 0) {
         prof_begin(s, "slot_assemble", (double)w.S_dyn * (4 * 96 + 72 + 96 + 144.0 * sizeof(T)), &ea, &eb);
-        ABD_LAUNCH(s, k_slot_assemble<T>, grid_for(w.S_dyn, 128), 128, 0, s->stream, A, P<T>(w.diag));
+        ABD_LAUNCH(s, k_slot_assemble<T>, grid_for(w.S_dyn, 32, 152 * 8), 128, 0, s->stream, A, P<T>(w.diag));
         prof_end(s, ea, eb, prof_index(s, "slot_assemble"));
     }
     int64_t *defl = P<int64_t>(w.deferred);
@@ -797,7 +820,7 @@ static int assemble_async_T(abd_scene *s, const abd_step_params *p, double kB) {
                P<PairRec>(w.act), w.cap_act, P<int2>(w.l1), P<T>(w.diag), P<T>(w.off), P<int>(w.offflag), defl, ndef,
                &c->act);
     prof_end(s, ea, eb, prof_index(s, "pair_assemble"));
-    ABD_LAUNCH(s, k_pair_moll<T>, 38, 128, 0, s->stream, A, P<PairRec>(w.act), defl, ndef, w.cap_act, P<int2>(w.l1),
+    ABD_LAUNCH(s, k_pair_moll<T>, 152 * 2, 128, 0, s->stream, A, P<PairRec>(w.act), defl, ndef, w.cap_act, P<int2>(w.l1),
                P<T>(w.diag), P<T>(w.off), P<int>(w.offflag));
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
     if (s->planes.n > 0 && SVd > 0)
@@ -843,10 +866,10 @@ int launch_energy_async(abd_scene *s, const abd_step_params *p, double kB, const
     A.alphas = alphas_dev; A.part = P<PartState>(w.part);
     A.h = p->h; A.dhat = p->dhat; A.kB = kB; A.planes = s->planes;
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
-    if (w.S_dyn > 0) ABD_LAUNCH(s, k_energy_slots, grid_for(w.S_dyn, 128), 128, 0, s->stream, A);
+    if (w.S_dyn > 0) ABD_LAUNCH(s, k_energy_slots, grid_for(w.S_dyn, 32, 152 * 8), 128, 0, s->stream, A);
     ABD_LAUNCH(s, k_energy_pairs, grid_for(w.cap_ls, 128, 152 * 8), 128, 0, s->stream, A, P<PairRec>(w.ls), w.cap_ls,
                &c->ls);
-    if (s->planes.n > 0 && SVd > 0) ABD_LAUNCH(s, k_energy_vp, grid_for(SVd, 128), 128, 0, s->stream, A, SVd);
+    if (s->planes.n > 0 && SVd > 0) ABD_LAUNCH(s, k_energy_vp, grid_for(SVd, 32, 152 * 8), 128, 0, s->stream, A, SVd);
     return cuda_check(s, cudaGetLastError(), "energy");
 }
 

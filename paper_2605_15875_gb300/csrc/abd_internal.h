@@ -74,7 +74,7 @@ struct World {
     DBuf x, x1, dx, box, box1;  // box, box1: [S][6] FP32 slot boxes (outward)
     DBuf xb, xb1;               // [SV][6] FP32 bounds (rounded down, up) of x, x1
     DBuf rep_off, rep_slot, zb, rho0, rhob, rb, sb, body_rep, body_slot;
-    DBuf l1, cand, act, ls, diag, off, offflag, pinv;
+    DBuf l1, cand, act, ls, diag, off, offflag;
     DBuf pcg_r, pcg_z, pcg_p, pcg_ap, pcg_sc;
     DBuf part;   // per-partition scalars (PartState)
     DBuf ctr;    // counters
@@ -204,6 +204,18 @@ int cuda_check(abd_scene *s, cudaError_t e, const char *what);
         K<<<G, B, SM, ST>>>(__VA_ARGS__);        \
         ++(S)->n_launches;                       \
     } while (0)
+
+// First item of this thread's warp in a "spread" grid-stride loop: warps are
+// dealt to blocks first (warp w of block b takes warp slot b + gridDim.x * w),
+// so a short list puts one warp on each of many SMs instead of filling a few
+// (FP64 work in particular is limited by each SM's FP64 pipe).  Loop as
+//   for (int64_t wb = spread_base(); wb < n; wb += gridDim.x * blockDim.x)
+// with item wb + lane; the trip count is warp-uniform.
+#ifdef __CUDACC__
+__device__ __forceinline__ int64_t spread_base() {
+    return ((int64_t)blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5)) * 32;
+}
+#endif
 
 inline int grid_for(int64_t n, int block, int maxb = 152 * 32) {
     int64_t g = (n + block - 1) / block;

@@ -33,7 +33,7 @@ namespace abd {
 struct PcgClArgs {
     const int *part_off;  // [NP + 1] dynamic-slot range of each partition
     const PartState *part;
-    const void *diag, *pinv, *off;
+    const void *diag, *off;
     const int *rowoff;                   // [S_dyn + 1] row CSR of the off-diagonal blocks
     const int2 *ent;                     // (neighbour slot, block index | bit 31 = transposed)
     const double *g;
@@ -81,6 +81,42 @@ __device__ __forceinline__ void push_partials(cg::cluster_group &cl, R *red, int
     }
 }
 
+// Block-Jacobi preconditioner: invert the n 12x12 diagonal blocks in M (in
+// place, shared memory) by Gauss-Jordan elimination without pivoting (the
+// blocks are symmetric positive definite).  16 threads per block, each owning
+// 9 entries; step k reads the old entries, then writes
+//   M[k][k] = 1/p, M[k][j] = M[k][j]/p, M[i][k] = -M[i][k]/p,
+//   M[i][j] -= M[i][k] M[k][j] / p      (p = M[k][k]).
+// Every thread of the CTA takes part in each step (blockDim.x a multiple of 32).
+template <class T>
+__device__ void invert_blocks(T *M, int n) {
+    const int grp = threadIdx.x >> 4, sub = threadIdx.x & 15, ngrp = blockDim.x >> 4;
+    for (int b0 = 0; b0 < n; b0 += ngrp) {
+        const int b = b0 + grp;
+        const bool own = b < n;
+        T *B = M + 144 * (int64_t)(own ? b : 0);
+        for (int k = 0; k < 12; ++k) {
+            T nv[9];
+            if (own) {
+                T ip = T(1) / B[13 * k];
+                for (int t = 0; t < 9; ++t) {
+                    int e = sub + 16 * t, i = e / 12, j = e % 12;
+                    T mij = B[e], mik = B[12 * i + k], mkj = B[12 * k + j];
+                    if (i == k && j == k) nv[t] = ip;
+                    else if (i == k) nv[t] = mkj * ip;
+                    else if (j == k) nv[t] = -mik * ip;
+                    else nv[t] = mij - mik * (mkj * ip);
+                }
+            }
+            __syncwarp();
+            if (own)
+                for (int t = 0; t < 9; ++t) B[sub + 16 * t] = nv[t];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes) {
     cg::cluster_group cl = cg::this_cluster();
@@ -90,7 +126,7 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
     const int s0 = A.part_off[part], s1 = A.part_off[part + 1], n = s1 - s0;
     const int m = (n + CS - 1) / CS;
     const int my0 = s0 + rank * m, my1 = min(s1, my0 + m), mine = max(0, my1 - my0);
-    const T *diag = (const T *)A.diag, *pinv = (const T *)A.pinv, *off = (const T *)A.off;
+    const T *diag = (const T *)A.diag, *off = (const T *)A.off;
     using R = T;  // scalars and x: FP32 in the mixed path, FP64 otherwise
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -119,8 +155,9 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
     T *Bs = (T *)(((uintptr_t)(enb + es) + 15) & ~uintptr_t(15));  // [es][144]
     T *gp = Bs + 144 * (size_t)es;                                 // [es][12] neighbours' p
     for (int e = threadIdx.x; e < 144 * mine; e += blockDim.x) {
-        Ds[e] = diag[144 * (int64_t)my0 + e];
-        Ps[e] = pinv[144 * (int64_t)my0 + e];
+        T v = diag[144 * (int64_t)my0 + e];
+        Ds[e] = v;
+        Ps[e] = v;
     }
     for (int sl = threadIdx.x; sl <= mine; sl += blockDim.x) rofs[sl] = A.rowoff[my0 + sl] - e0;
     for (int j = threadIdx.x; j < es; j += blockDim.x) enb[j] = A.ent[e0 + j].x;
@@ -130,6 +167,8 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
         const T *B = off + 144 * (int64_t)(en.y & 0x7fffffff);
         Bs[e] = en.y < 0 ? B[12 * c + i] : B[12 * i + c];  // row i of the block as row slot sees it
     }
+    __syncthreads();
+    invert_blocks(Ps, mine);
     // r = -g, x = 0, z = P r, p = z
     for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
         r[e] = T(-A.g[12 * (int64_t)my0 + e]);
@@ -274,7 +313,7 @@ static int launch_T(abd_scene *s, const abd_step_params *p) {
     size_t smem = std::max(base + 1024, std::min(max_smem, base + (size_t)m * 12 * (144 + 12 + 4) * sizeof(T)));
     PcgClArgs A = {};
     A.part_off = P<int>(w.part_off); A.part = P<PartState>(w.part);
-    A.diag = w.diag.p; A.pinv = w.pinv.p; A.off = w.off.p;
+    A.diag = w.diag.p; A.off = w.off.p;
     A.rowoff = P<int>(w.rowoff); A.ent = P<int2>(w.ent);
     A.g = P<double>(w.g); A.x = P<double>(w.dq);
     A.tol2 = p->pcg_rtol * p->pcg_rtol; A.max_it = p->pcg_max;

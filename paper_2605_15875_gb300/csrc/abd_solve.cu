@@ -83,51 +83,6 @@ __global__ void k_shared_init(int nsh, const int *__restrict__ rep_off, const in
     }
 }
 
-// Inverse of each 12x12 diagonal block by Cholesky (block-Jacobi preconditioner).
-template <class T>
-__global__ void k_pinv(int S_dyn, const int *__restrict__ slot_part, const PartState *__restrict__ part,
-                       const T *__restrict__ diag, T *__restrict__ pinv) {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S_dyn; s += gridDim.x * blockDim.x) {
-        if (!part[slot_part[s]].active) continue;
-        T L[144];
-        const T *D = diag + 144 * (int64_t)s;
-        for (int i = 0; i < 144; ++i) L[i] = D[i];
-        bool ok = true;
-        for (int j = 0; j < 12 && ok; ++j) {
-            T d = L[j * 12 + j];
-            for (int k = 0; k < j; ++k) d -= L[j * 12 + k] * L[j * 12 + k];
-            if (!(d > T(0))) { ok = false; break; }
-            T ljj = tsqrt(d);
-            L[j * 12 + j] = ljj;
-            for (int i = j + 1; i < 12; ++i) {
-                T t = L[i * 12 + j];
-                for (int k = 0; k < j; ++k) t -= L[i * 12 + k] * L[j * 12 + k];
-                L[i * 12 + j] = t / ljj;
-            }
-        }
-        T *o = pinv + 144 * (int64_t)s;
-        if (!ok) {  // not expected (block is SPD); fall back to the diagonal
-            for (int i = 0; i < 144; ++i) o[i] = T(0);
-            for (int i = 0; i < 12; ++i) o[i * 12 + i] = D[i * 12 + i] > T(0) ? T(1) / D[i * 12 + i] : T(1);
-            continue;
-        }
-        for (int c = 0; c < 12; ++c) {
-            T y[12];
-            for (int i = 0; i < 12; ++i) {
-                T t = (i == c) ? T(1) : T(0);
-                for (int k = 0; k < i; ++k) t -= L[i * 12 + k] * y[k];
-                y[i] = t / L[i * 12 + i];
-            }
-            for (int i = 11; i >= 0; --i) {
-                T t = y[i];
-                for (int k = i + 1; k < 12; ++k) t -= L[k * 12 + i] * y[k];
-                y[i] = t / L[i * 12 + i];
-            }
-            for (int i = 0; i < 12; ++i) o[i * 12 + c] = y[i];
-        }
-    }
-}
-
 // max |dq| per partition (ordered-double atomics).
 __global__ void k_dqmax(int S_dyn, const int *__restrict__ slot_part, const double *__restrict__ dq,
                         PartState *__restrict__ part) {
@@ -479,7 +434,7 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
               dbuf_ensure(w.box1, 48 * S) && dbuf_ensure(w.zb, 96 * NS) && dbuf_ensure(w.rho0, 8 * NS) &&
               dbuf_ensure(w.rhob, 8 * NS) && dbuf_ensure(w.rb, 8 * NS) && dbuf_ensure(w.sb, 8 * NS) &&
               dbuf_ensure(w.part, sizeof(PartState) * kMaxParts) && dbuf_ensure(w.ctr, sizeof(Counters)) &&
-              dbuf_ensure(w.bar, 64) && dbuf_ensure(w.pinv, 8 * 144 * Sd) &&
+              dbuf_ensure(w.bar, 64) &&
               dbuf_ensure(w.cbox, 48 * (size_t)(w.C ? w.C : 1)) && dbuf_ensure(w.cbox1, 48 * (size_t)(w.C ? w.C : 1));
     if (!ok) return set_err(s, ABD_E_OOM, "world buffers");
     if (w.S_all > 0) ABD_LAUNCH(s, k_fill_sv_slot, std::min(w.S_all, 152 * 8), 256, 0, s->stream, w.S_all, P<int64_t>(w.slot_voff), P<int>(w.sv_slot));
@@ -563,13 +518,6 @@ void grow_lists(World &w, const Counters &c, bool pcg_over) {
     if (pcg_over) w.ecap_mult *= 2;
 }
 
-template <class T>
-void launch_pinv(abd_scene *s) {
-    World &w = s->w;
-    if (w.S_dyn > 0)
-        ABD_LAUNCH(s, k_pinv<T>, grid_for(w.S_dyn, 64), 64, 0, s->stream, w.S_dyn, P<int>(w.slot_part),
-                   P<PartState>(w.part), P<T>(w.diag), P<T>(w.pinv));
-}
 
 // Projected Newton on Eq. 5 for every partition whose `run` flag is set.  One
 // iteration is enqueued without host round trips (list sizes stay on the
@@ -612,8 +560,6 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         }
         // assemble, precondition, solve
         if ((rc = launch_assemble_async(s, C.precision, p, C.kB))) return rc;
-        if (C.precision == ABD_MIXED) launch_pinv<float>(s);
-        else launch_pinv<double>(s);
         if ((rc = launch_pcg_async(s, C.precision, p))) return rc;
         // Newton stopping test before the line search
         ABD_LAUNCH(s, k_dqmax, grid_for(w.S_dyn, 128), 128, 0, s->stream, w.S_dyn, P<int>(w.slot_part), P<double>(w.dq),

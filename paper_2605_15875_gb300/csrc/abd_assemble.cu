@@ -820,8 +820,10 @@ static int assemble_async_T(abd_scene *s, const abd_step_params *p, double kB) {
                P<PairRec>(w.act), w.cap_act, P<int2>(w.l1), P<T>(w.diag), P<T>(w.off), P<int>(w.offflag), defl, ndef,
                &c->act);
     prof_end(s, ea, eb, prof_index(s, "pair_assemble"));
+    prof_begin(s, "pair_moll", 0.0, &ea, &eb);
     ABD_LAUNCH(s, k_pair_moll<T>, 152 * 2, 128, 0, s->stream, A, P<PairRec>(w.act), defl, ndef, w.cap_act, P<int2>(w.l1),
                P<T>(w.diag), P<T>(w.off), P<int>(w.offflag));
+    prof_end(s, ea, eb, prof_index(s, "pair_moll"));
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
     if (s->planes.n > 0 && SVd > 0)
         ABD_LAUNCH(s, k_vp_assemble<T>, grid_for(SVd, 256), 256, 0, s->stream, A, SVd, P<T>(w.diag));
@@ -866,10 +868,13 @@ int launch_energy_async(abd_scene *s, const abd_step_params *p, double kB, const
     A.alphas = alphas_dev; A.part = P<PartState>(w.part);
     A.h = p->h; A.dhat = p->dhat; A.kB = kB; A.planes = s->planes;
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
+    cudaEvent_t ea, eb;
+    prof_begin(s, "energy", 0.0, &ea, &eb);
     if (w.S_dyn > 0) ABD_LAUNCH(s, k_energy_slots, grid_for(w.S_dyn, 32, 152 * 8), 128, 0, s->stream, A);
     ABD_LAUNCH(s, k_energy_pairs, grid_for(w.cap_ls, 128, 152 * 8), 128, 0, s->stream, A, P<PairRec>(w.ls), w.cap_ls,
                &c->ls);
     if (s->planes.n > 0 && SVd > 0) ABD_LAUNCH(s, k_energy_vp, grid_for(SVd, 32, 152 * 8), 128, 0, s->stream, A, SVd);
+    prof_end(s, ea, eb, prof_index(s, "energy"));
     return cuda_check(s, cudaGetLastError(), "energy");
 }
 

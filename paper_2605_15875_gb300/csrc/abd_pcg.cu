@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
     const int part = blockIdx.x / CS;
     const int s0 = A.part_off[part], s1 = A.part_off[part + 1], n = s1 - s0;
     const int m = (n + CS - 1) / CS;
-    const int my0 = s0 + rank * m, my1 = min(s1, my0 + m), mine = max(0, my1 - my0);
+    const int my0 = min(s1, s0 + rank * m), my1 = min(s1, my0 + m), mine = my1 - my0;
     const T *diag = (const T *)A.diag, *off = (const T *)A.off;
     using R = T;  // scalars and x: FP32 in the mixed path, FP64 otherwise
 
@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
         rz += r[e] * t;
     }
     block_sum2(rr0, rz, scratch);
+    cl.sync();  // every CTA of the cluster has started before any DSMEM access
     {
         R v[2] = {rr0, rz}, f = es < ne ? R(1) : R(0);
         push_partials(cl, red, 16, v, 2, rank, CS);
@@ -280,6 +281,7 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
             else __syncthreads();
         }
     }
+    cl.sync();  // no CTA leaves while another may still read its shared memory
     for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) A.x[12 * (int64_t)my0 + e] = (double)x[e];
     if (rank == 0 && threadIdx.x == 0) A.iters[part] = it;
 }

@@ -461,6 +461,7 @@ struct Status {
     int pcg_iters[kMaxParts];
     int pcg_over, pcg_nnz2;
     int csr_total;  // entries of the off-diagonal row CSR (twice the blocks)
+    unsigned long long n_moll;  // mollified edge-edge pairs assembled by the warp kernel
     PartState part[kMaxParts];
 };
 
@@ -481,8 +482,11 @@ int enqueue_status(abd_scene *s, Status *h) {
     cudaMemcpyAsync(&h->c, w.ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream);
     cudaMemcpyAsync(h->pcg_iters, w.pcg_sc.p, sizeof(int) * (kMaxParts + 2), cudaMemcpyDeviceToHost, s->stream);
     cudaMemcpyAsync(h->part, w.part.p, sizeof(PartState) * w.NP, cudaMemcpyDeviceToHost, s->stream);
-    if (s->prof && w.S_dyn > 0)
+    if (s->prof && w.S_dyn > 0) {
         cudaMemcpyAsync(&h->csr_total, P<int>(w.rowoff) + w.S_dyn, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+        cudaMemcpyAsync(&h->n_moll, P<int64_t>(w.deferred) + w.cap_act, sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, s->stream);
+    }
     return cuda_check(s, cudaGetLastError(), "status");
 }
 
@@ -616,11 +620,20 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         for (int i = 0; i < w.NP; ++i) pmax = std::max<int64_t>(pmax, hs->pcg_iters[i]);
         C.st->pcg_iters += pmax;
         if (s->prof) {
-            // per PCG iteration: diagonal, preconditioner and off-diagonal blocks
-            // read once; p, Ap, r, z (T) and x (FP64) read or written once
+            // compulsory HBM bytes of one PCG launch: diagonal and distinct
+            // off-diagonal blocks, row offsets and entries read once, g read
+            // and dq written once (everything else stays in shared memory)
             double tb = C.precision == ABD_MIXED ? 4.0 : 8.0;
-            double per = 144.0 * tb * (2.0 * w.S_dyn + 0.5 * hs->csr_total) + 12.0 * w.S_dyn * (7.0 * tb + 16.0);
-            prof_add_bytes(s, "pcg", per * (double)pmax);
+            double nnzb = 0.5 * hs->csr_total;
+            prof_add_bytes(s, "pcg", 144.0 * tb * (w.S_dyn + nnzb) + 8.0 * hs->csr_total + 4.0 * w.S_dyn +
+                                         2.0 * 96.0 * w.S_dyn);
+            // one pair assembly: record, four FP64 positions, gradient and
+            // three 12x12 blocks accumulated
+            prof_add_bytes(s, "pair_assemble", (double)hs->c.act * (sizeof(PairRec) + 96.0 + 96.0 + 3.0 * 144.0 * tb));
+            prof_add_bytes(s, "pair_moll", (double)hs->n_moll * (sizeof(PairRec) + 8.0 + 96.0 + 96.0 + 3.0 * 144.0 * tb));
+            // energies: the line-search list and its positions at two
+            // configurations, per pass
+            prof_add_bytes(s, "energy", 2.0 * (double)hs->c.ls * (sizeof(PairRec) + 192.0));
         }
         any = false;
         for (int i = 0; i < w.NP; ++i) {

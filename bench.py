@@ -40,6 +40,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-serving", action="store_true", help="skip the served and batched legs")
     return ap.parse_args()
 
 
@@ -202,6 +203,9 @@ def run_ours(args, rank, world):
         e2e = {"value": round(B_ * args.steps * world / dt, 3), "unit": "body-steps/s",
                "h2d_bytes_per_step": 2 * 96 * sa.n_bodies, "d2h_bytes_per_step": 2 * 96 * sa.n_bodies}
         sce.close()
+    serving = batched = None
+    if not args.no_serving:
+        serving, batched = serve_legs(abd)
     cpu = cpu_baseline(args.cpu_seconds) if (rank == 0 and world == 1) else None
     lat_sorted = sorted(lat)
     out = {
@@ -223,11 +227,44 @@ def run_ours(args, rank, world):
         "newton_iters_mean": float(np.mean([s["newton_iters"] for s in stats])),
         "active_pairs_peak": int(max(s["n_active_peak"] for s in stats)),
         "candidates_peak": int(max(s["n_candidates_peak"] for s in stats)),
+        "serving": serving, "batched": batched,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
     sc.close()
     return out
+
+
+def _serve(abd, reqs, n_streams, params):
+    srv = abd.Server(n_streams=n_streams)
+    t0 = time.perf_counter()
+    ts = [srv.submit(sa, k, params) for sa, k in reqs]
+    infos = [srv.wait(t) for t in ts]
+    dt = time.perf_counter() - t0
+    lat = np.concatenate([srv.latencies(t) for t in ts])
+    srv.close()
+    bs = sum(sa.n_dynamic * k for sa, k in reqs)
+    return {"value": round(bs / dt, 2), "unit": "body-steps/s", "wall_s": round(dt, 3), "body_steps": int(bs),
+            "p50_step_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_step_ms": round(float(np.percentile(lat, 99)), 3),
+            "requests": len(reqs), "n_streams": n_streams,
+            "worst_status": int(max(i["status"] for i in infos)),
+            "queue_ms_p99": round(float(np.percentile([i["queue_ms"] for i in infos], 99)), 3)}
+
+
+def serve_legs(abd):
+    """Served and batched legs (bounded samples of the serving and
+    uneven-subdomain workloads), mixed precision, every request submitted at
+    once to the serving runtime (closed batch, continuous admission)."""
+    from paper_2605_15875_gb300 import scenes
+    p = abd.default_params(precision=abd.MIXED, pcg_rtol=1e-5)
+    reqs = scenes.serving_requests(seed=0, n_scenes=64, lo=8, hi=512)
+    serving = _serve(abd, reqs, 4, p)
+    serving["sample"] = "64 requests: scenes of 8-512 bodies (log-uniform; cube stacks and sphere piles), 1-10 steps"
+    subs = scenes.batched_subdomains(seed=0, n_scenes=16, lo=16, hi=512, levels=(1, 2))
+    batched = _serve(abd, [(sa, 10) for sa in subs], 8, p)
+    batched["sample"] = "16 uneven subdomains of 16-512 noisy icospheres (levels 1-2), 10 steps each"
+    return serving, batched
 
 
 def cpu_baseline(seconds):

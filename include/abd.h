@@ -187,6 +187,82 @@ int abd_candidates(abd_scene *s, const double *x0, const double *x1, double dhat
 int abd_candidates_noalloc(abd_scene *s, const double *x0, const double *x1, double dhat, int32_t *out, int64_t cap,
                            int64_t *n_out);
 
+/* Membership of partition `part` as the last abd_step built it (Sec. 4: a
+ * dynamic body belongs to every slab its w-inflated box meets).  `bodies`
+ * receives up to `cap` body indices of the partition and `shared` up to
+ * `cap_shared` indices of those that also belong to another partition (the
+ * replicated bodies B_ij); *n and *n_shared receive the full counts.  Either
+ * array may be NULL to query counts.  ABD_E_INVALID for a partition index out
+ * of range or before the first step. */
+int abd_partition_get(const abd_scene *s, int32_t part, int32_t *bodies, int32_t cap, int32_t *n, int32_t *shared,
+                      int32_t cap_shared, int32_t *n_shared);
+
+/* ---------------------------------------------------------------------------
+ * Serving: many independent scenes on one GPU.  The paper solves one scene;
+ * this runtime has no counterpart there.  A server owns `n_streams` worker
+ * threads, each with its own CUDA stream.  A submitted request (a scene, its
+ * partition, step parameters and a number of steps) waits in FIFO order until
+ * its estimated device memory fits the HBM budget; a free worker then creates
+ * the scene on its stream, advances it `n_steps` steps with q, v, z, u and the
+ * contact lists resident on the device, copies the final state to host memory
+ * owned by the server and frees the scene.  Requests on different workers
+ * overlap on the device, and a request admitted while others run starts as
+ * soon as a worker and memory are free (continuous batching).  Each request's
+ * arithmetic is that of abd_step on its own scene, so its result does not
+ * depend on what else runs.
+ * ------------------------------------------------------------------------- */
+typedef struct abd_server abd_server;
+
+typedef struct {
+    int32_t device;           /* CUDA device of every scene */
+    int32_t n_streams;        /* worker threads = concurrent scenes (>= 1) */
+    int64_t hbm_budget_bytes; /* admission budget; 0: 80% of the free device memory at create */
+} abd_server_desc;
+
+enum { ABD_REQ_QUEUED = 0, ABD_REQ_RUNNING = 1, ABD_REQ_DONE = 2 };
+
+typedef struct {
+    int32_t state;         /* ABD_REQ_* */
+    int32_t status;        /* worst step status (0 OK, > 0 warning, < 0 error; an error ends the request) */
+    int32_t steps_done;
+    int32_t n_bodies;
+    int64_t est_bytes;     /* admission estimate of the request's device memory */
+    double queue_ms;       /* submit -> admitted */
+    double run_ms;         /* admitted -> done (scene creation, steps, state read-back) */
+    double step_ms_p50;    /* per-step wall-clock latency (abd_step call) */
+    double step_ms_p99;
+    abd_step_stats last;   /* statistics of the last step */
+} abd_request_info;
+
+/* Create a server (threads started, streams created on `device`).  The
+ * descriptor is copied.  ABD_E_INVALID for n_streams < 1. */
+int abd_server_create(const abd_server_desc *desc, abd_server **out);
+
+/* Queue a request.  Every array behind `scene` (and `part`, `params`) is
+ * copied before return, so the caller may free them.  `part` NULL: one
+ * partition (monolithic).  `params` NULL: abd_step_params_default().
+ * *ticket identifies the request in the calls below. */
+int abd_server_submit(abd_server *srv, const abd_scene_desc *scene, const abd_partition_desc *part,
+                      const abd_step_params *params, int32_t n_steps, int64_t *ticket);
+
+/* Current state of a request (non-blocking), or, for abd_server_wait, its
+ * state once it is done.  ABD_E_INVALID for an unknown ticket. */
+int abd_server_poll(abd_server *srv, int64_t ticket, abd_request_info *info);
+int abd_server_wait(abd_server *srv, int64_t ticket, abd_request_info *info);
+
+/* Final q and v ([n_bodies][12] each, host) of a done request; per-step
+ * latencies (ms, up to `cap`) with their count in *n.  ABD_E_INVALID when the
+ * request is not done or the sizes do not match; the request's error code if
+ * it failed. */
+int abd_server_result(abd_server *srv, int64_t ticket, double *q, double *v, int64_t n_bodies);
+int abd_server_latencies(abd_server *srv, int64_t ticket, double *ms, int32_t cap, int32_t *n);
+
+/* Last error text of a request (empty when none). */
+const char *abd_server_error(abd_server *srv, int64_t ticket);
+
+/* Wait for queued and running requests, stop the workers, free everything. */
+void abd_server_destroy(abd_server *srv);
+
 /* Per-kernel timing of the last steps (enabled by abd_profile(s, 1)): for the
  * kernel named `name`, launches, total device milliseconds (CUDA events on
  * the scene's stream) and algorithmic bytes moved. */

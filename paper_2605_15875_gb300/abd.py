@@ -57,11 +57,31 @@ class StepStats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ServerDesc(C.Structure):
+    _fields_ = [("device", C.c_int32), ("n_streams", C.c_int32), ("hbm_budget_bytes", C.c_int64)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE = 0, 1, 2
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("status", C.c_int32), ("steps_done", C.c_int32), ("n_bodies", C.c_int32),
+                ("est_bytes", C.c_int64), ("queue_ms", C.c_double), ("run_ms", C.c_double),
+                ("step_ms_p50", C.c_double), ("step_ms_p99", C.c_double), ("last", StepStats)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "last"}
+        d["last"] = self.last.as_dict()
+        return d
+
+
 # every symbol declared in include/abd.h
 EXPORTS = ["abd_scene_create", "abd_scene_destroy", "abd_scene_counts", "abd_body_props", "abd_partition",
            "abd_partition_masks", "abd_step", "abd_state_get", "abd_state_set", "abd_state_device",
            "abd_candidates", "abd_profile", "abd_kernel_stats", "abd_step_params_default", "abd_status_string",
-           "abd_last_error", "abd_candidates_noalloc"]
+           "abd_last_error", "abd_candidates_noalloc", "abd_partition_get", "abd_server_create",
+           "abd_server_submit", "abd_server_poll", "abd_server_wait", "abd_server_result", "abd_server_latencies",
+           "abd_server_error", "abd_server_destroy"]
 
 _lib = None
 
@@ -97,6 +117,18 @@ def load(path: Optional[str] = None):
     L.abd_status_string.restype = C.c_char_p
     L.abd_last_error.argtypes = [vp]
     L.abd_last_error.restype = C.c_char_p
+    i32p = C.POINTER(C.c_int32)
+    L.abd_partition_get.argtypes = [vp, C.c_int32, vp, C.c_int32, i32p, vp, C.c_int32, i32p]
+    L.abd_server_create.argtypes = [C.POINTER(ServerDesc), C.POINTER(vp)]
+    L.abd_server_submit.argtypes = [vp, C.POINTER(SceneDesc), vp, vp, C.c_int32, C.POINTER(i64)]
+    L.abd_server_poll.argtypes = [vp, i64, C.POINTER(RequestInfo)]
+    L.abd_server_wait.argtypes = [vp, i64, C.POINTER(RequestInfo)]
+    L.abd_server_result.argtypes = [vp, i64, vp, vp, i64]
+    L.abd_server_latencies.argtypes = [vp, i64, vp, C.c_int32, i32p]
+    L.abd_server_error.argtypes = [vp, i64]
+    L.abd_server_error.restype = C.c_char_p
+    L.abd_server_destroy.argtypes = [vp]
+    L.abd_server_destroy.restype = None
     if path is None:
         _lib = L
     return L
@@ -129,23 +161,30 @@ def _current_stream():
     return None
 
 
+def scene_desc(sa) -> SceneDesc:
+    """SceneDesc pointing into the arrays of `sa` (keep `sa` alive while the
+    descriptor is in use)."""
+    d = SceneDesc()
+    d.n_meshes = len(sa.mesh_n_verts)
+    d.mesh_n_verts, d.mesh_n_tris = _p(sa.mesh_n_verts), _p(sa.mesh_n_tris)
+    d.mesh_xbar, d.mesh_tris = _p(sa.mesh_xbar), _p(sa.mesh_tris)
+    d.n_bodies = sa.n_bodies
+    d.body_mesh, d.body_density, d.body_kappa = _p(sa.body_mesh), _p(sa.body_density), _p(sa.body_kappa)
+    d.body_kind, d.body_q0, d.body_v0 = _p(sa.body_kind), _p(sa.body_q0), _p(sa.body_v0)
+    d.n_planes = len(sa.plane_axis)
+    d.plane_axis, d.plane_sign, d.plane_offset = _p(sa.plane_axis), _p(sa.plane_sign), _p(sa.plane_offset)
+    for k in range(3):
+        d.gravity[k] = float(sa.gravity[k])
+    return d
+
+
 class Scene:
     """A scene resident on the current CUDA device (C ABI handle)."""
 
     def __init__(self, sa, stream: Optional[int] = None):
         L = load()
         self._keep = [sa]
-        d = SceneDesc()
-        d.n_meshes = len(sa.mesh_n_verts)
-        d.mesh_n_verts, d.mesh_n_tris = _p(sa.mesh_n_verts), _p(sa.mesh_n_tris)
-        d.mesh_xbar, d.mesh_tris = _p(sa.mesh_xbar), _p(sa.mesh_tris)
-        d.n_bodies = sa.n_bodies
-        d.body_mesh, d.body_density, d.body_kappa = _p(sa.body_mesh), _p(sa.body_density), _p(sa.body_kappa)
-        d.body_kind, d.body_q0, d.body_v0 = _p(sa.body_kind), _p(sa.body_q0), _p(sa.body_v0)
-        d.n_planes = len(sa.plane_axis)
-        d.plane_axis, d.plane_sign, d.plane_offset = _p(sa.plane_axis), _p(sa.plane_sign), _p(sa.plane_offset)
-        for k in range(3):
-            d.gravity[k] = float(sa.gravity[k])
+        d = scene_desc(sa)
         h = C.c_void_p()
         self.stream = _current_stream() if stream is None else stream
         rc = L.abd_scene_create(C.byref(d), self.stream, C.byref(h))
@@ -187,6 +226,16 @@ class Scene:
         w = C.c_double()
         self._check(self.L.abd_partition_masks(self.h, h, _p(m), C.byref(w)), "abd_partition_masks")
         return m, w.value
+
+    def partition_get(self, part):
+        n, ns = C.c_int32(), C.c_int32()
+        self._check(self.L.abd_partition_get(self.h, part, None, 0, C.byref(n), None, 0, C.byref(ns)),
+                    "abd_partition_get")
+        b = np.zeros(max(1, n.value), dtype=np.int32)
+        sh = np.zeros(max(1, ns.value), dtype=np.int32)
+        self._check(self.L.abd_partition_get(self.h, part, _p(b), n.value, C.byref(n), _p(sh), ns.value,
+                                             C.byref(ns)), "abd_partition_get")
+        return b[:n.value], sh[:ns.value]
 
     def step(self, params: Optional[StepParams] = None) -> dict:
         params = default_params() if params is None else params
@@ -234,3 +283,79 @@ class Scene:
         self._check(self.L.abd_kernel_stats(self.h, name.encode(), C.byref(n), C.byref(ms), C.byref(b)),
                     "abd_kernel_stats")
         return n.value, ms.value, b.value
+
+
+class Server:
+    """Serving runtime (C ABI): worker threads with one CUDA stream each run
+    submitted scenes concurrently under an HBM admission budget."""
+
+    def __init__(self, n_streams=4, hbm_budget_bytes=0, device=None):
+        L = load()
+        if device is None:
+            try:
+                import torch
+                device = torch.cuda.current_device()
+            except Exception:
+                device = 0
+        d = ServerDesc(device=device, n_streams=n_streams, hbm_budget_bytes=hbm_budget_bytes)
+        h = C.c_void_p()
+        rc = L.abd_server_create(C.byref(d), C.byref(h))
+        if rc != 0:
+            raise AbdError(f"abd_server_create failed: {L.abd_status_string(rc).decode()} ({rc})")
+        self.L, self.h, self._n = L, h, {}
+
+    def submit(self, sa, n_steps, params: Optional[StepParams] = None, n_slabs=1, axis=0, planes=None,
+               alpha=2.0, w_min=0.0) -> int:
+        d = scene_desc(sa)
+        arr = None if planes is None else np.ascontiguousarray(planes, dtype=np.float64)
+        pd = PartitionDesc(axis=axis, n_slabs=n_slabs, planes=None if arr is None else arr.ctypes.data,
+                           alpha=alpha, w_min=w_min)
+        pr = default_params() if params is None else params
+        t = C.c_int64()
+        rc = self.L.abd_server_submit(self.h, C.byref(d), C.cast(C.pointer(pd), C.c_void_p),
+                                      C.cast(C.pointer(pr), C.c_void_p), n_steps, C.byref(t))
+        if rc != 0:
+            raise AbdError(f"abd_server_submit: {self.L.abd_status_string(rc).decode()} ({rc})")
+        self._n[t.value] = sa.n_bodies
+        return t.value
+
+    def poll(self, ticket) -> dict:
+        info = RequestInfo()
+        rc = self.L.abd_server_poll(self.h, ticket, C.byref(info))
+        if rc != 0:
+            raise AbdError(f"abd_server_poll: {rc}")
+        return info.as_dict()
+
+    def wait(self, ticket) -> dict:
+        info = RequestInfo()
+        rc = self.L.abd_server_wait(self.h, ticket, C.byref(info))
+        if rc != 0:
+            raise AbdError(f"abd_server_wait: {rc}")
+        return info.as_dict()
+
+    def result(self, ticket):
+        n = self._n[ticket]
+        q, v = np.zeros((n, 12)), np.zeros((n, 12))
+        rc = self.L.abd_server_result(self.h, ticket, _p(q), _p(v), n)
+        if rc < 0:
+            raise AbdError(f"abd_server_result: {self.L.abd_status_string(rc).decode()} ({rc}): "
+                           f"{self.L.abd_server_error(self.h, ticket).decode()}")
+        return q, v
+
+    def latencies(self, ticket):
+        n = C.c_int32()
+        self.L.abd_server_latencies(self.h, ticket, None, 0, C.byref(n))
+        ms = np.zeros(max(1, n.value))
+        self.L.abd_server_latencies(self.h, ticket, _p(ms), n.value, C.byref(n))
+        return ms[:n.value]
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            self.L.abd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

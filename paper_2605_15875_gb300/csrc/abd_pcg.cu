@@ -289,21 +289,27 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
 template <class T>
 static int launch_T(abd_scene *s, const abd_step_params *p) {
     World &w = s->w;
-    static int max_cluster = -1;
-    static size_t max_smem = 0;
-    if (max_cluster < 0) {
-        int dev = 0;
+    // device limits and kernel attributes, set once (thread-safe static init)
+    struct Limits {
+        int max_cluster;
+        size_t max_smem;
+    };
+    static const Limits lim = [] {
+        Limits L;
+        int dev = 0, optin = 0;
         cudaGetDevice(&dev);
-        int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        max_smem = (size_t)optin;
+        L.max_smem = (size_t)optin;
         cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-        if (cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess)
-            max_cluster = 16;
-        else
-            max_cluster = 8;
+        L.max_cluster =
+            cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess
+                ? 16
+                : 8;
         cudaGetLastError();
-    }
+        return L;
+    }();
+    const int max_cluster = lim.max_cluster;
+    const size_t max_smem = lim.max_smem;
     int maxn = 0;
     for (int q = 0; q < w.NP; ++q) maxn = std::max(maxn, w.h_part_off[q + 1] - w.h_part_off[q]);
     // cluster size: up to 16 CTAs, about 16 owned slots each

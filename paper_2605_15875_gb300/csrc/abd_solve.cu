@@ -877,3 +877,23 @@ extern "C" int abd_candidates(abd_scene *s, const double *x0, const double *x1, 
     *n_out = n;
     return rc;
 }
+
+extern "C" int abd_partition_get(const abd_scene *s, int32_t part, int32_t *bodies, int32_t cap, int32_t *n,
+                                 int32_t *shared, int32_t cap_shared, int32_t *n_shared) {
+    if (!s || !n || !n_shared || cap < 0 || cap_shared < 0) return ABD_E_INVALID;
+    const World &w = s->w;
+    if (part < 0 || part >= w.NP || (int)w.h_part_off.size() < w.NP + 1) return ABD_E_INVALID;
+    int cnt = 0, cs = 0;
+    for (int sl = w.h_part_off[part]; sl < w.h_part_off[part + 1]; ++sl) {
+        int b = w.h_slot_body[sl];
+        if (bodies && cnt < cap) bodies[cnt] = b;
+        ++cnt;
+        if (__builtin_popcountll(w.h_slot_mask[sl]) > 1) {
+            if (shared && cs < cap_shared) shared[cs] = b;
+            ++cs;
+        }
+    }
+    *n = cnt;
+    *n_shared = cs;
+    return ABD_OK;
+}

@@ -43,3 +43,23 @@ def test_oracle_is_not_imported_by_the_product():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "abd_oracle" not in txt, f
+
+
+def test_ctypes_struct_layouts_match_the_header(tmp_path):
+    """Sizes of the ABI structs as gcc lays them out from include/abd.h equal
+    the ctypes mirrors used by the binding."""
+    import ctypes
+    import subprocess
+    from paper_2605_15875_gb300 import abd
+    names = ["abd_scene_desc", "abd_partition_desc", "abd_step_params", "abd_step_stats", "abd_server_desc",
+             "abd_request_info"]
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include "abd.h"\nint main(void){\n' +
+                   "".join(f'printf("%zu\\n", sizeof({n}));\n' for n in names) + "return 0;}\n")
+    exe = tmp_path / "sz"
+    r = subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    mirrors = [abd.SceneDesc, abd.PartitionDesc, abd.StepParams, abd.StepStats, abd.ServerDesc, abd.RequestInfo]
+    assert got == [ctypes.sizeof(m) for m in mirrors]

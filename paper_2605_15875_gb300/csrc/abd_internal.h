@@ -68,6 +68,7 @@ constexpr int kClusterSize = 32;
 // Per-step workspace of the consensus solve.
 struct World {
     int NP = 0, S_dyn = 0, S_all = 0, nsh = 0, R = 0;
+    int64_t gen = 0;  // bumped whenever slot tables or list buffers change (captured graphs go stale)
     int64_t SV = 0;
     DBuf slot_body, slot_part, slot_voff, slot_mask, slot_rep, slot_kw, sv_slot;
     DBuf q, qprev, qtil, z, u, rho, dq, g;
@@ -127,6 +128,21 @@ struct KStat {
 
 }  // namespace abd
 
+// Captured steady-state Newton iteration (see iteration_graph).
+struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t gen = -1;
+    int kernels = 0;
+    bool disabled = false;
+    // profiling event pairs recorded as graph nodes: (kstat index, bytes, begin, end)
+    struct Ev {
+        int idx;
+        double bytes;
+        cudaEvent_t a, b;
+    };
+    std::vector<Ev> ev;
+};
+
 struct abd_scene {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -151,6 +167,7 @@ struct abd_scene {
     // pinned host staging
     void *pinned = nullptr;
     size_t pinned_bytes = 0;
+    IterGraph ig;
     // profiling
     bool prof = false;
     int64_t n_launches = 0;
@@ -193,6 +210,8 @@ void prof_end(abd_scene *s, cudaEvent_t a, cudaEvent_t b, int idx);
 void prof_flush(abd_scene *s);
 void prof_add_bytes(abd_scene *s, const char *name, double bytes);
 int prof_index(abd_scene *s, const char *name);
+void prof_graph_replayed(abd_scene *s);
+void prof_graph_release(abd_scene *s);
 
 int set_err(abd_scene *s, int code, const std::string &msg);
 int cuda_check(abd_scene *s, cudaError_t e, const char *what);

@@ -52,6 +52,18 @@ int prof_index(abd_scene *s, const char *name) {
     return (int)s->kstats.size() - 1;
 }
 
+static bool capturing(abd_scene *s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!s->stream || cudaStreamIsCapturing(s->stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusActive;
+}
+
+// While the stream is being captured into the iteration graph, the events
+// become graph nodes (external records) and the pair is kept with the graph;
+// its bytes are added on every replay (prof_graph_replayed).
 void prof_begin(abd_scene *s, const char *name, double bytes, cudaEvent_t *a, cudaEvent_t *b) {
     *a = *b = nullptr;
     if (!s->prof) return;
@@ -66,6 +78,11 @@ void prof_begin(abd_scene *s, const char *name, double bytes, cudaEvent_t *a, cu
         (k ? *b : *a) = e;
     }
     int idx = prof_index(s, name);
+    if (capturing(s)) {
+        s->ig.ev.push_back({idx, bytes, *a, *b});
+        cudaEventRecordWithFlags(*a, s->stream, cudaEventRecordExternal);
+        return;
+    }
     s->kstats[idx].bytes += bytes;
     cudaEventRecord(*a, s->stream);
 }
@@ -76,8 +93,36 @@ void prof_add_bytes(abd_scene *s, const char *name, double bytes) {
 
 void prof_end(abd_scene *s, cudaEvent_t a, cudaEvent_t b, int idx) {
     if (!a || !b) return;
+    if (capturing(s)) {
+        cudaEventRecordWithFlags(b, s->stream, cudaEventRecordExternal);
+        return;
+    }
     cudaEventRecord(b, s->stream);
     s->ev_pending.push_back({idx, {a, b}});
+}
+
+// After a replay of the iteration graph has completed: accumulate its event
+// pairs (they are overwritten by the next replay).
+void prof_graph_replayed(abd_scene *s) {
+    if (!s->prof) return;
+    for (auto &e : s->ig.ev) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+            s->kstats[e.idx].ms += ms;
+            s->kstats[e.idx].launches += 1;
+            s->kstats[e.idx].bytes += e.bytes;
+        }
+        cudaGetLastError();
+    }
+}
+
+// Return the graph's event pairs to the pool (graph re-captured or freed).
+void prof_graph_release(abd_scene *s) {
+    for (auto &e : s->ig.ev) {
+        s->ev_pool.push_back(e.a);
+        s->ev_pool.push_back(e.b);
+    }
+    s->ig.ev.clear();
 }
 
 // Resolve recorded event pairs (call after a stream synchronisation).
@@ -348,6 +393,8 @@ extern "C" int abd_scene_create(const abd_scene_desc *d, void *stream, abd_scene
 extern "C" void abd_scene_destroy(abd_scene *s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
+    if (s->ig.exec) cudaGraphExecDestroy(s->ig.exec);
+    prof_graph_release(s);
     SceneDev &D = s->dev;
     DBuf *bufs[] = {&D.q, &D.v, &D.mass, &D.S, &D.vol, &D.kappa, &D.kind, &D.voff, &D.nv, &D.toff, &D.nt,
                     &D.eoff, &D.ne, &D.xbar, &D.tri, &D.edge, &D.erest2, &D.vperm, &D.tperm, &D.eperm, &D.cbody_off, &D.crest};

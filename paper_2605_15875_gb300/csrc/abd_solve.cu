@@ -358,6 +358,7 @@ int compute_masks(abd_scene *s, double h, const std::vector<double> &box, const 
 
 // Build the slot tables of one step from the body masks (nparts partitions).
 int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
+    ++s->w.gen;
     World &w = s->w;
     w.NP = nparts;
     w.h_slot_body.clear(); w.h_slot_part.clear(); w.h_slot_mask.clear();
@@ -520,8 +521,113 @@ void grow_lists(World &w, const Counters &c, bool pcg_over) {
     };
     g(w.cap_l1, c.l1); g(w.cap_cand, c.cand); g(w.cap_act, c.act); g(w.cap_ls, c.ls); g(w.cap_cp, c.cp);
     if (pcg_over) w.ecap_mult *= 2;
+    ++w.gen;
 }
 
+
+// Enqueue one Newton iteration of every active partition (no host round
+// trip): broad phase (static on the first iteration, else the previous
+// line-search list), assembly, PCG, stopping test, CCD, two line-search
+// passes, update, and the status copy into pinned memory.
+int enqueue_iteration(Ctx &C, bool static_bp, Status *hs) {
+    abd_scene *s = C.s;
+    World &w = s->w;
+    const abd_step_params *p = C.p;
+    Counters *dc = P<Counters>(w.ctr);
+    int *d_iters = P<int>(w.pcg_sc);
+    int rc;
+    cudaMemsetAsync(&dc->bad, 0, sizeof(int), s->stream);
+    cudaMemsetAsync(d_iters, 0, sizeof(int) * (kMaxParts + 2), s->stream);
+    // active set at q: static broad phase on the first iteration, then the
+    // previous line-search list (q lies on that swept path)
+    if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x), nullptr, 0))) return rc;
+    if (static_bp) {
+        if ((rc = launch_boxes(s, false, C.half, -1, nullptr)) || (rc = launch_l1_async(s, false)) ||
+            (rc = launch_l2_async(s, false, C.half)) ||
+            (rc = launch_narrow_async(s, P<PairRec>(w.cand), &dc->cand, w.cap_cand, p->dhat)))
+            return rc;
+    } else if ((rc = launch_narrow_async(s, P<PairRec>(w.ls), &dc->ls, w.cap_ls, p->dhat))) {
+        return rc;
+    }
+    // assemble, precondition, solve
+    if ((rc = launch_assemble_async(s, C.precision, p, C.kB))) return rc;
+    if ((rc = launch_pcg_async(s, C.precision, p))) return rc;
+    // Newton stopping test before the line search
+    ABD_LAUNCH(s, k_dqmax, grid_for(w.S_dyn, 128), 128, 0, s->stream, w.S_dyn, P<int>(w.slot_part), P<double>(w.dq),
+               P<PartState>(w.part));
+    ABD_LAUNCH(s, k_newton_decide, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), 1.0 / (p->h * C.l),
+               p->newton_tol);
+    // CCD along q -> q + dq over the swept candidates; line-search list
+    if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x1), P<double>(w.dq), 1)) ||
+        (rc = launch_boxes(s, true, C.half, 1, P<double>(w.dq))) || (rc = launch_l1_async(s, true)) ||
+        (rc = launch_l2_async(s, true, C.half)) || (rc = launch_ccd_async(s, p, true)))
+        return rc;
+    // backtracking on the FP64 energy: two passes of kLS trial steps
+    ABD_LAUNCH(s, k_ls_reset, 1, 64, 0, s->stream, w.NP, P<int>(C.nh0), P<int>(C.decided));
+    for (int pass = 0; pass < 2; ++pass) {
+        cudaMemsetAsync(&dc->pending, 0, sizeof(int), s->stream);
+        ABD_LAUNCH(s, k_ls_alphas, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
+                   P<int>(C.decided), P<double>(C.alphas), p->max_halvings);
+        if ((rc = launch_energy_async(s, p, C.kB, P<double>(C.alphas)))) return rc;
+        ABD_LAUNCH(s, k_ls_select, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
+                   P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->pending);
+    }
+    ABD_LAUNCH(s, k_check_bad, 1, 1, 0, s->stream, dc, w.cap_l1, w.cap_cand, w.cap_act, w.cap_ls, w.cap_cp,
+               d_iters + kMaxParts);
+    ABD_LAUNCH(s, k_update_q, grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream, w.S_dyn,
+               P<int>(w.slot_part), P<PartState>(w.part), P<int>(C.decided), dc, P<double>(w.dq), P<double>(w.q));
+    ABD_LAUNCH(s, k_mark_updated, 1, 64, 0, s->stream, w.NP, P<int>(C.decided), dc);
+    return enqueue_status(s, hs);
+}
+
+// The steady-state iteration (static_bp false) as a CUDA graph: captured on
+// the scene's stream, re-captured when the world or a list buffer changed
+// (w.gen), and updated in place when the topology is unchanged.  Profiling
+// events become graph nodes.  Returns false when capture is not possible
+// (the legacy default stream cannot be captured).
+bool iteration_graph(Ctx &C, Status *hs) {
+    abd_scene *s = C.s;
+    IterGraph &g = s->ig;
+    if (g.disabled || !s->stream) return false;
+    if (g.exec && g.gen == s->w.gen && (s->prof == !g.ev.empty() || !s->prof)) return true;
+    prof_graph_release(s);
+    int64_t L0 = s->n_launches;
+    if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        g.disabled = true;
+        return false;
+    }
+    int rc = enqueue_iteration(C, false, hs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
+    int kernels = (int)(s->n_launches - L0);
+    s->n_launches = L0;
+    if (rc || e != cudaSuccess || !graph) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        g.disabled = true;
+        return false;
+    }
+    if (g.exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(g.exec, graph, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+    }
+    if (!g.exec && cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        g.exec = nullptr;
+        cudaGraphDestroy(graph);
+        g.disabled = true;
+        return false;
+    }
+    cudaGraphDestroy(graph);
+    g.gen = s->w.gen;
+    g.kernels = kernels;
+    return true;
+}
 
 // Projected Newton on Eq. 5 for every partition whose `run` flag is set.  One
 // iteration is enqueued without host round trips (list sizes stay on the
@@ -549,48 +655,15 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
     int it = 0;
     while (any && it < p->max_newton) {
         double t0 = now_ms();
-        cudaMemsetAsync(&dc->bad, 0, sizeof(int), s->stream);
-        cudaMemsetAsync(d_iters, 0, sizeof(int) * (kMaxParts + 2), s->stream);
-        // active set at q: static broad phase on the first iteration, then the
-        // previous line-search list (q lies on that swept path)
-        if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x), nullptr, 0))) return rc;
-        if (static_bp) {
-            if ((rc = launch_boxes(s, false, C.half, -1, nullptr)) || (rc = launch_l1_async(s, false)) ||
-                (rc = launch_l2_async(s, false, C.half)) ||
-                (rc = launch_narrow_async(s, P<PairRec>(w.cand), &dc->cand, w.cap_cand, p->dhat)))
-                return rc;
-        } else if ((rc = launch_narrow_async(s, P<PairRec>(w.ls), &dc->ls, w.cap_ls, p->dhat))) {
+        bool graphed = !static_bp && iteration_graph(C, hs);
+        if (graphed) {
+            if ((rc = cuda_check(s, cudaGraphLaunch(s->ig.exec, s->stream), "graph launch"))) return rc;
+            s->n_launches += s->ig.kernels;
+        } else if ((rc = enqueue_iteration(C, static_bp, hs))) {
             return rc;
         }
-        // assemble, precondition, solve
-        if ((rc = launch_assemble_async(s, C.precision, p, C.kB))) return rc;
-        if ((rc = launch_pcg_async(s, C.precision, p))) return rc;
-        // Newton stopping test before the line search
-        ABD_LAUNCH(s, k_dqmax, grid_for(w.S_dyn, 128), 128, 0, s->stream, w.S_dyn, P<int>(w.slot_part), P<double>(w.dq),
-                   P<PartState>(w.part));
-        ABD_LAUNCH(s, k_newton_decide, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), 1.0 / (p->h * C.l),
-                   p->newton_tol);
-        // CCD along q -> q + dq over the swept candidates; line-search list
-        if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x1), P<double>(w.dq), 1)) ||
-            (rc = launch_boxes(s, true, C.half, 1, P<double>(w.dq))) || (rc = launch_l1_async(s, true)) ||
-            (rc = launch_l2_async(s, true, C.half)) || (rc = launch_ccd_async(s, p, true)))
-            return rc;
-        // backtracking on the FP64 energy: two passes of kLS trial steps
-        ABD_LAUNCH(s, k_ls_reset, 1, 64, 0, s->stream, w.NP, P<int>(C.nh0), P<int>(C.decided));
-        for (int pass = 0; pass < 2; ++pass) {
-            cudaMemsetAsync(&dc->pending, 0, sizeof(int), s->stream);
-            ABD_LAUNCH(s, k_ls_alphas, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
-                       P<int>(C.decided), P<double>(C.alphas), p->max_halvings);
-            if ((rc = launch_energy_async(s, p, C.kB, P<double>(C.alphas)))) return rc;
-            ABD_LAUNCH(s, k_ls_select, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
-                       P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->pending);
-        }
-        ABD_LAUNCH(s, k_check_bad, 1, 1, 0, s->stream, dc, w.cap_l1, w.cap_cand, w.cap_act, w.cap_ls, w.cap_cp,
-                   d_iters + kMaxParts);
-        ABD_LAUNCH(s, k_update_q, grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream, w.S_dyn,
-                   P<int>(w.slot_part), P<PartState>(w.part), P<int>(C.decided), dc, P<double>(w.dq), P<double>(w.q));
-        ABD_LAUNCH(s, k_mark_updated, 1, 64, 0, s->stream, w.NP, P<int>(C.decided), dc);
-        if ((rc = enqueue_status(s, hs)) || (rc = sync(s))) return rc;
+        if ((rc = sync(s))) return rc;
+        if (graphed) prof_graph_replayed(s);
         if (hs->c.bad) {
             // lists outgrew their buffers: grow, restore the partition state, redo
             grow_lists(w, hs->c, hs->pcg_over != 0);

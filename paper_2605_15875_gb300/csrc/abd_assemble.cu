@@ -878,4 +878,46 @@ int launch_energy_async(abd_scene *s, const abd_step_params *p, double kB, const
     return cuda_check(s, cudaGetLastError(), "energy");
 }
 
+// Final-state check: minimum distance over the candidate pairs (FP64
+// closest-feature distance) and over dynamic vertices against the planes.
+__global__ void k_min_dist(const PairRec *__restrict__ cand, int64_t cap, const unsigned long long *__restrict__ n_dev,
+                           const double *__restrict__ x, unsigned long long *__restrict__ out) {
+    int64_t n = min((int64_t)*n_dev, cap);
+    for (int64_t base = spread_base(); base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = base + (threadIdx.x & 31);
+        if (i >= n) continue;
+        PairRec r = cand[i];
+        double X[12];
+        for (int v = 0; v < 4; ++v)
+            for (int k = 0; k < 3; ++k) X[3 * v + k] = x[3 * (int64_t)r.v[v] + k];
+        int ty;
+        double b0, b1;
+        double d = sqrt(classify<double>(r.flags & 1, X, ty, b0, b1));
+        atomicMin(out, ord(d));
+    }
+}
+
+__global__ void k_min_dist_vp(int64_t SVd, const double *__restrict__ x, Planes planes,
+                              unsigned long long *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < SVd; i += (int64_t)gridDim.x * blockDim.x) {
+        double m = 1e300;
+        for (int pl = 0; pl < planes.n; ++pl) {
+            double d = planes.sign[pl] * x[3 * i + planes.axis[pl]] - planes.offset[pl];
+            m = fmin(m, d > 0.0 ? d : 0.0);
+        }
+        if (m < 1e300) atomicMin(out, ord(m));
+    }
+}
+
+int launch_min_dist_async(abd_scene *s) {
+    World &w = s->w;
+    Counters *c = P<Counters>(w.ctr);
+    ABD_LAUNCH(s, k_min_dist, grid_for(w.cap_cand, 32, 152 * 8), 128, 0, s->stream, P<PairRec>(w.cand), w.cap_cand,
+               &c->cand, P<double>(w.x), &c->mind);
+    int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
+    if (s->planes.n > 0 && SVd > 0)
+        ABD_LAUNCH(s, k_min_dist_vp, grid_for(SVd, 256), 256, 0, s->stream, SVd, P<double>(w.x), s->planes, &c->mind);
+    return cuda_check(s, cudaGetLastError(), "min distance");
+}
+
 }  // namespace abd

@@ -185,10 +185,12 @@ __device__ __forceinline__ bool overlapf(const float *a, const float *b) {
     return !(a[0] > b[3] || b[0] > a[3] || a[1] > b[4] || b[1] > a[4] || a[2] > b[5] || b[2] > a[5]);
 }
 
-// Level 1 on FP32 boxes (same pairing rules as k_l1).
+// Level 1 on FP32 boxes (same pairing rules as k_l1).  `cross` instead pairs
+// slots of different bodies across partitions too (not two static slots): the
+// whole-scene check of the final state.
 __global__ void k_l1f(int S_all, const int *__restrict__ slot_part, const float *__restrict__ box,
                      const PartState *__restrict__ part, int2 *__restrict__ out, int64_t cap,
-                     unsigned long long *__restrict__ count) {
+                     unsigned long long *__restrict__ count, const int *__restrict__ slot_body, int cross) {
     int64_t ntile = (S_all + 31) / 32;
     int64_t total = (int64_t)S_all * ntile;
     int lane = threadIdx.x & 31;
@@ -212,7 +214,8 @@ __global__ void k_l1f(int S_all, const int *__restrict__ slot_part, const float 
             bool hit = false;
             if (act_a && b < b1) {
                 int pb = slot_part[b];
-                bool ok = (pa >= 0 && pb >= 0) ? (pa == pb) : (pa >= 0 || pb >= 0);
+                bool ok = cross ? ((pa >= 0 || pb >= 0) && slot_body[a] != slot_body[b])
+                               : ((pa >= 0 && pb >= 0) ? (pa == pb) : (pa >= 0 || pb >= 0));
                 if (ok && pb >= 0 && !part[pb].active) ok = false;
                 if (ok) {
                     float bb[6];
@@ -808,7 +811,8 @@ int launch_l1(abd_scene *s, bool swept, int64_t *count) {
         cudaMemsetAsync(&c->l1, 0, sizeof(unsigned long long), s->stream);
         int64_t ntile = (w.S_all + 31) / 32;
         ABD_LAUNCH(s, k_l1f, grid_for((int64_t)w.S_all * ntile, 256), 256, 0, s->stream, w.S_all, P<int>(w.slot_part),
-                   swept ? P<float>(w.box1) : P<float>(w.box), P<PartState>(w.part), P<int2>(w.l1), w.cap_l1, &c->l1);
+                   swept ? P<float>(w.box1) : P<float>(w.box), P<PartState>(w.part), P<int2>(w.l1), w.cap_l1, &c->l1,
+                   P<int>(w.slot_body), 0);
         int rc = cuda_check(s, cudaGetLastError(), "k_l1");
         if (rc) return rc;
         unsigned long long n = 0;
@@ -868,13 +872,14 @@ int launch_l2(abd_scene *s, int mode, bool swept, double half, int64_t n_l1, int
 // capacities once per iteration (a count above its capacity means the
 // iteration is redone with larger buffers).
 // ---------------------------------------------------------------------------
-int launch_l1_async(abd_scene *s, bool swept) {
+int launch_l1_async(abd_scene *s, bool swept, int cross) {
     World &w = s->w;
     Counters *c = P<Counters>(w.ctr);
     cudaMemsetAsync(&c->l1, 0, sizeof(unsigned long long), s->stream);
     int64_t ntile = (w.S_all + 31) / 32;
     ABD_LAUNCH(s, k_l1f, grid_for((int64_t)w.S_all * ntile, 256), 256, 0, s->stream, w.S_all, P<int>(w.slot_part),
-               swept ? P<float>(w.box1) : P<float>(w.box), P<PartState>(w.part), P<int2>(w.l1), w.cap_l1, &c->l1);
+               swept ? P<float>(w.box1) : P<float>(w.box), P<PartState>(w.part), P<int2>(w.l1), w.cap_l1, &c->l1,
+               P<int>(w.slot_body), cross);
     return cuda_check(s, cudaGetLastError(), "k_l1");
 }
 

@@ -113,6 +113,7 @@ struct PartState {
 struct Counters {
     unsigned long long l1, cand, act, ls, cp;
     unsigned long long rinf, sinf, dinf;  // ordered doubles
+    unsigned long long mind;              // ordered double: minimum distance of the final-state check
     int overflow;
     int timeout;
     unsigned long long pcg_total;
@@ -193,7 +194,7 @@ int launch_l1(abd_scene *s, bool swept, int64_t *count);
 // 1 PairRecs to w.cand (synchronous, with capacity growth)
 int launch_l2(abd_scene *s, int mode, bool swept, double half, int64_t n_l1, int32_t *out3, int64_t cap,
               int64_t *count);
-int launch_l1_async(abd_scene *s, bool swept);
+int launch_l1_async(abd_scene *s, bool swept, int cross = 0);
 int launch_l2_async(abd_scene *s, bool swept, double half);
 // ---- (abd_assemble.cu) ----
 int launch_narrow_async(abd_scene *s, const PairRec *src, const unsigned long long *src_n, int64_t src_cap,
@@ -201,6 +202,9 @@ int launch_narrow_async(abd_scene *s, const PairRec *src, const unsigned long lo
 int launch_assemble_async(abd_scene *s, int precision, const abd_step_params *p, double kB);
 int launch_ccd_async(abd_scene *s, const abd_step_params *p, bool want_ls);
 int launch_energy_async(abd_scene *s, const abd_step_params *p, double kB, const double *alphas_dev);
+// minimum unsigned distance over w.cand at w.x and vertex-plane distances of
+// dynamic slot vertices (negative plane distances count as 0) into Counters::mind
+int launch_min_dist_async(abd_scene *s);
 int launch_pcg_async(abd_scene *s, int precision, const abd_step_params *p);
 // ---- (abd_solve.cu) ----
 

@@ -754,6 +754,43 @@ int merge_check(Ctx &C, bool &ok) {
     return set_err(s, ABD_E_PAIR_OVERFLOW, "merge check: lists keep overflowing");
 }
 
+// Minimum distance of the final state (shared bodies at z), over every pair
+// of different bodies whose boxes overlap -- across partitions too -- and the
+// vertex-plane distances; 0 means touching or penetrating.
+int final_min_distance(Ctx &C, double &out) {
+    abd_scene *s = C.s;
+    World &w = s->w;
+    int rc = ensure_lists(C);
+    if (rc) return rc;
+    Status *hs = pinned_status(s);
+    if (!hs) return set_err(s, ABD_E_OOM, "pinned status");
+    std::vector<PartState> ps(w.NP);
+    for (int i = 0; i < w.NP; ++i) {
+        memset(&ps[i], 0, sizeof(PartState));
+        ps[i].active = 1;
+    }
+    Counters *dc = P<Counters>(w.ctr);
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        if ((rc = write_parts(s, ps))) return rc;
+        const unsigned long long big = 0x7FEFFFFFFFFFFFFFull;  // largest finite double
+        cudaMemcpyAsync(&dc->mind, &big, sizeof big, cudaMemcpyHostToDevice, s->stream);
+        if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x), P<double>(w.z), 2)) ||
+            (rc = launch_boxes(s, false, C.half, -2, nullptr)) || (rc = launch_l1_async(s, false, 1)) ||
+            (rc = launch_l2_async(s, false, C.half)) || (rc = launch_min_dist_async(s)) ||
+            (rc = enqueue_status(s, hs)) || (rc = sync(s)))
+            return rc;
+        if ((int64_t)hs->c.l1 > w.cap_l1 || (int64_t)hs->c.cand > w.cap_cand || (int64_t)hs->c.cp > w.cap_cp) {
+            grow_lists(w, hs->c, false);
+            if ((rc = ensure_lists(C))) return rc;
+            continue;
+        }
+        uint64_t bits = hs->c.mind;
+        memcpy(&out, &bits, sizeof out);
+        return ABD_OK;
+    }
+    return set_err(s, ABD_E_PAIR_OVERFLOW, "final check: lists keep overflowing");
+}
+
 int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool force_mono) {
     double T0 = now_ms();
     int64_t L0 = s->n_launches;
@@ -861,6 +898,7 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
         st->admm_iters = admm;
         st->status = status;
         st->pcg_iters += st2.pcg_iters;
+        st->min_distance = st2.min_distance;
         return status;
     }
     ABD_LAUNCH(s, k_merge, grid_for(s->nb, 128), 128, 0, s->stream, s->nb, P<int>(s->dev.kind), P<int>(w.body_rep),
@@ -868,6 +906,9 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
                                                         P<double>(s->dev.q), P<double>(s->dev.v));
     if ((rc = cuda_check(s, cudaGetLastError(), "merge")) || (rc = sync(s))) return rc;
     prof_flush(s);
+    double mind = 0.0;
+    if ((rc = final_min_distance(C, mind))) return rc;
+    st->min_distance = mind;
     if (maxed && status == ABD_OK) status = ABD_NEWTON_MAXITER;
     st->status = status;
     st->admm_iters = admm;

@@ -76,6 +76,7 @@ def _run_pair(sa, steps, params_g, params_o, tol, partition=None, traj_tol=1e-7)
         worst = max(worst, e)
         assert e <= tol, (k, e, sg, so)
         assert sg["status"] >= 0
+        assert sg["min_distance"] > 0.0, (k, sg)  # no penetration in the final state, across partitions
         assert (sg["admm_iters"], sg["newton_iters"]) == (so["admm_iters"], so["newton_iters"]), (k, sg, so)
     drift = rel(free.state()[0], o.state()[0])
     print(f"per-step worst {worst:.3e}, trajectory drift {drift:.3e}")

@@ -41,6 +41,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serving", action="store_true", help="skip the served and batched legs")
+    ap.add_argument("--no-fixed-rho", action="store_true", help="skip the fixed-rho comparison leg")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="scenes on the legacy default stream (direct launches, no graph replay), e.g. under ncu")
     return ap.parse_args()
 
 
@@ -121,7 +124,7 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     # a stream of its own (not the legacy default stream), so that the
     # library can capture and replay its Newton iteration as a CUDA graph
-    stream = torch.cuda.Stream()
+    stream = torch.cuda.current_stream() if args.no_graph else torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     sa = scene_arrays()
     B_ = sa.n_dynamic
@@ -191,12 +194,14 @@ def run_ours(args, rank, world):
         fp64 = B_ * args.steps * world / (sum(lat64) / 1e3)
         sc64.close()
     # the same window with a fixed penalty rho = beta m (no residual-driven adaptation)
-    scf, pf = make(abd.MIXED, abd.RHO_FIXED)
-    latf, _, statf = timed(scf, pf, args.steps, args.warmup)
-    fixed = {"value": round(B_ * args.steps * world / (sum(latf) / 1e3), 3), "unit": "body-steps/s",
-             "admm_iters_mean": float(np.mean([x["admm_iters"] for x in statf])),
-             "newton_iters_mean": float(np.mean([x["newton_iters"] for x in statf]))}
-    scf.close()
+    fixed = None
+    if not args.no_fixed_rho:
+        scf, pf = make(abd.MIXED, abd.RHO_FIXED)
+        latf, _, statf = timed(scf, pf, args.steps, args.warmup)
+        fixed = {"value": round(B_ * args.steps * world / (sum(latf) / 1e3), 3), "unit": "body-steps/s",
+                 "admm_iters_mean": float(np.mean([x["admm_iters"] for x in statf])),
+                 "newton_iters_mean": float(np.mean([x["newton_iters"] for x in statf]))}
+        scf.close()
     e2e = None
     if not args.no_e2e:
         sce, pe = make(abd.MIXED)
@@ -233,6 +238,7 @@ def run_ours(args, rank, world):
                    "slab_planes_x": PLANES, "h": pm.h, "dhat": pm.dhat, "precision": "mixed",
                    "rho": "adaptive", "pcg_rtol": pm.pcg_rtol, "newton_tol": pm.newton_tol,
                    "theta": pm.theta, "l2": "flushed between timed steps (256 MB write)",
+                   "newton_iteration_graph": not args.no_graph,
                    "window": f"steps {args.warmup}..{args.warmup + args.steps - 1} of the drop (free fall "
                              "until about step 19, then the first contacts with the box and between spheres)"},
         "p50_ms": round(float(np.percentile(lat_sorted, 50)), 4),

@@ -60,7 +60,8 @@ __device__ T classify(bool ee, const T *X, int &type, T &b0, T &b1) {
         T r0 = dot3(ap, e1), r1 = dot3(ap, e2);
         T det = G00 * G11 - G01 * G01;
         if (det > T(0)) {
-            T u = (r0 * G11 - r1 * G01) / det, v = (G00 * r1 - G01 * r0) / det;
+            T idet = T(1) / det;
+            T u = (r0 * G11 - r1 * G01) * idet, v = (G00 * r1 - G01 * r0) * idet;
             if (u >= T(0) && v >= T(0) && u + v <= T(1)) {
                 T r[3];
                 for (int k = 0; k < 3; ++k) r[k] = ap[k] - u * e1[k] - v * e2[k];
@@ -89,7 +90,8 @@ __device__ T classify(bool ee, const T *X, int &type, T &b0, T &b1) {
     T A = dot3(ea, ea), B = dot3(ea, eb), C = dot3(eb, eb), D = dot3(ea, w), E = dot3(eb, w);
     T den = A * C - B * B;
     if (den > T(1e-10) * A * C) {
-        T s = (B * E - C * D) / den, t = (A * E - B * D) / den;
+        T iden = T(1) / den;
+        T s = (B * E - C * D) * iden, t = (A * E - B * D) * iden;
         if (s >= T(0) && s <= T(1) && t >= T(0) && t <= T(1)) {
             T r[3];
             for (int k = 0; k < 3; ++k) r[k] = w[k] + s * ea[k] - t * eb[k];
@@ -209,10 +211,10 @@ __device__ T dist2_derivs(const T *X, const Feature &f, T b0, T b1, T *gs, T *Hs
 template <class T>
 __device__ __forceinline__ void barrier3(T d, T dhat, T &b, T &b1, T &b2) {
     if (d >= dhat) { b = b1 = b2 = T(0); return; }
-    T e = d - dhat, L = tlog(d / dhat);
+    T e = d - dhat, L = tlog(d / dhat), id = T(1) / d, eid = e * id;
     b = -e * e * L;
-    b1 = T(-2) * e * L - e * e / d;
-    b2 = T(-2) * L - T(4) * e / d + e * e / (d * d);
+    b1 = T(-2) * e * L - e * eid;
+    b2 = T(-2) * L - T(4) * eid + eid * eid;
 }
 
 // Edge-edge mollifier m(c), c = |(a1 - a0) x (b1 - b0)|^2, eps_x from rest lengths:
@@ -353,9 +355,11 @@ __device__ inline double pair_gradient(bool ee, const double *X, double dhat, do
     for (int v = 0; v < 4; ++v)
         for (int a = 0; a < 3; ++a) r[a] += w[v] * X[3 * v + a];
     barrier3<double>(d, dhat, P.b, P.bp, P.bpp);
-    // grad b = b' grad d, grad d = grad s / 2d = w (x) r / d
+    // grad b = b' grad d, grad d = grad s / 2d = w (x) r / d (one reciprocal:
+    // FP64 division is a long instruction sequence on this GPU)
+    const double bpd = P.bp / d;
     for (int v = 0; v < 4; ++v)
-        for (int a = 0; a < 3; ++a) g[3 * v + a] = P.bp * w[v] * r[a] / d;
+        for (int a = 0; a < 3; ++a) g[3 * v + a] = bpd * w[v] * r[a];
     P.m = 1.0;
     P.moll = false;
     if (ee) {

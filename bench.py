@@ -118,6 +118,22 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(mhz)}
 
 
+def reduce_max_ms(total_ms, world, device):
+    """Timed-region length of the slowest rank (every rank gets it)."""
+    if world == 1:
+        return float(total_ms)
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, max_ms):
+    """Whole-job throughput: units processed by all ranks over the slowest
+    rank's time (each rank runs an independent replica of the workload)."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_2605_15875_gb300 import abd, build as B
@@ -173,12 +189,8 @@ def run_ours(args, rank, world):
     sc, pm = make(abd.MIXED)
     with Clocks(dev) as clk:
         lat, launches, stats = timed(sc, pm, args.steps, args.warmup, profile=True)
-    total_ms = sum(lat)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = B_ * args.steps * world / (total_ms / 1e3)
+    total_ms = reduce_max_ms(sum(lat), world, "cuda")
+    value = job_value(B_ * args.steps, world, total_ms)
     # dominant kernel and its roofline
     names = ["pcg", "pair_moll", "pair_assemble", "slot_assemble", "l2_static", "l2_swept", "ccd", "energy"]
     ks = {n: sc.kernel_stats(n) for n in names}

@@ -144,6 +144,18 @@ struct IterGraph {
     std::vector<Ev> ev;
 };
 
+// Cluster-size autotuner of the PCG (abd_pcg.cu), one per block precision.
+struct PcgTune {
+    int key = -1;             // partition-size bucket the result belongs to
+    int best = 0;             // chosen cluster size, 0 while tuning
+    int ncand = 0, cand[4] = {0, 0, 0, 0};
+    double sum[4] = {0, 0, 0, 0};  // ms per PCG iteration, summed over trials
+    int cnt[4] = {0, 0, 0, 0};
+    int next = 0;             // next candidate to try
+    int pending = -1;         // candidate whose timed launch awaits the status read
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+
 struct abd_scene {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -169,6 +181,7 @@ struct abd_scene {
     void *pinned = nullptr;
     size_t pinned_bytes = 0;
     IterGraph ig;
+    PcgTune pcg_tune[2];  // [0] FP32 blocks, [1] FP64 blocks
     // profiling
     bool prof = false;
     int64_t n_launches = 0;
@@ -215,6 +228,10 @@ void prof_flush(abd_scene *s);
 void prof_add_bytes(abd_scene *s, const char *name, double bytes);
 int prof_index(abd_scene *s, const char *name);
 void prof_graph_replayed(abd_scene *s);
+bool stream_capturing(abd_scene *s);
+// After the status read of a Newton iteration: account the timed PCG launch
+// of the cluster-size autotuner (iterations = largest partition's count).
+void pcg_tune_observe(abd_scene *s, int64_t iterations);
 void prof_graph_release(abd_scene *s);
 
 int set_err(abd_scene *s, int code, const std::string &msg);

@@ -312,13 +312,72 @@ static int launch_T(abd_scene *s, const abd_step_params *p) {
     const size_t max_smem = lim.max_smem;
     int maxn = 0;
     for (int q = 0; q < w.NP; ++q) maxn = std::max(maxn, w.h_part_off[q + 1] - w.h_part_off[q]);
-    // cluster size: up to 16 CTAs, about 16 owned slots each
+    // default cluster size: up to 16 CTAs, about 16 owned slots each
     int CS = std::min(max_cluster, std::max(2, (maxn + 15) / 16));
     if (CS > 8 && max_cluster < 16) CS = 8;
-    int m = std::max(1, (maxn + CS - 1) / CS);
-    size_t base = pcg_base_bytes<T>(m);
-    if (base > max_smem) return set_err(s, ABD_E_UNSUPPORTED, "pcg: partition too large for the cluster");
-    size_t smem = std::max(base + 1024, std::min(max_smem, base + (size_t)m * 12 * (144 + 12 + 4) * sizeof(T)));
+    auto smem_for = [&](int cs, size_t &smem) {
+        int m = std::max(1, (maxn + cs - 1) / cs);
+        size_t base = pcg_base_bytes<T>(m);
+        smem = std::max(base + 1024, std::min(max_smem, base + (size_t)m * 12 * (144 + 12 + 4) * sizeof(T)));
+        return base <= max_smem;
+    };
+    auto config = [&](int cs, size_t smem, cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at) {
+        cfg = cudaLaunchConfig_t{};
+        cfg.gridDim = dim3(w.NP * cs);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s->stream;
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cs;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+    };
+    // cluster-size autotuner: directly launched solves (not graph captures)
+    // try each schedulable candidate twice, timed per PCG iteration; the
+    // fastest is kept for this partition-size bucket and the iteration graph
+    // is re-captured with it
+    PcgTune &tu = s->pcg_tune[sizeof(T) == 8 ? 1 : 0];
+    int key = 32 - __builtin_clz((unsigned)std::max(1, maxn));
+    const bool cap = stream_capturing(s);  // no occupancy queries or timing inside a capture
+    if (tu.key != key && !cap) {
+        cudaEvent_t ea0 = tu.a, eb0 = tu.b;
+        tu = PcgTune();
+        tu.a = ea0;
+        tu.b = eb0;
+        tu.key = key;
+        const int cands[4] = {CS, 4, 8, 16};
+        for (int c : cands) {
+            if (c < 2 || c > max_cluster || c > std::max(2, maxn)) continue;
+            bool dup = false;
+            for (int i = 0; i < tu.ncand; ++i) dup |= tu.cand[i] == c;
+            size_t sm = 0;
+            if (dup || !smem_for(c, sm)) continue;
+            cudaLaunchConfig_t cf;
+            cudaLaunchAttribute at[1];
+            config(c, sm, cf, at);
+            int nclu = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclu, k_pcg_cluster<T>, &cf) != cudaSuccess || nclu < 1) {
+                cudaGetLastError();
+                continue;
+            }
+            tu.cand[tu.ncand++] = c;
+        }
+        if (tu.ncand <= 1) tu.best = CS;
+    }
+    bool timed = false;
+    if (tu.key != key) {
+        // partition-size bucket not tuned yet (inside a capture): default size
+    } else if (tu.best) {
+        CS = tu.best;
+    } else if (tu.pending < 0 && !cap) {
+        tu.pending = tu.next % tu.ncand;
+        CS = tu.cand[tu.pending];
+        timed = true;
+    }
+    size_t smem = 0;
+    if (!smem_for(CS, smem)) return set_err(s, ABD_E_UNSUPPORTED, "pcg: partition too large for the cluster");
     PcgClArgs A = {};
     A.part_off = P<int>(w.part_off); A.part = P<PartState>(w.part);
     A.diag = w.diag.p; A.off = w.off.p;
@@ -326,24 +385,44 @@ static int launch_T(abd_scene *s, const abd_step_params *p) {
     A.g = P<double>(w.g); A.x = P<double>(w.dq);
     A.tol2 = p->pcg_rtol * p->pcg_rtol; A.max_it = p->pcg_max;
     A.iters = P<int>(w.pcg_sc);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(w.NP * CS);
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s->stream;
+    cudaLaunchConfig_t cfg;
     cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CS;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
+    config(CS, smem, cfg, at);
+    if (timed && !tu.a) {
+        cudaEventCreate(&tu.a);
+        cudaEventCreate(&tu.b);
+    }
     cudaEvent_t ea, eb;
     prof_begin(s, "pcg", 0, &ea, &eb);
+    if (timed) cudaEventRecord(tu.a, s->stream);
     cudaError_t e = cudaLaunchKernelEx(&cfg, k_pcg_cluster<T>, A, (int)smem);
+    if (timed) cudaEventRecord(tu.b, s->stream);
     prof_end(s, ea, eb, prof_index(s, "pcg"));
     ++s->n_launches;
     return cuda_check(s, e, "pcg cluster launch");
+}
+
+void pcg_tune_observe(abd_scene *s, int64_t iterations) {
+    for (PcgTune &tu : s->pcg_tune) {
+        if (tu.pending < 0) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, tu.a, tu.b) == cudaSuccess && iterations > 0) {
+            tu.sum[tu.pending] += ms / (double)iterations;
+            tu.cnt[tu.pending] += 1;
+            tu.next = tu.pending + 1;
+        }
+        cudaGetLastError();
+        tu.pending = -1;
+        bool done = tu.ncand > 0;
+        for (int i = 0; i < tu.ncand; ++i) done &= tu.cnt[i] >= 2;
+        if (done) {
+            int bi = 0;
+            for (int i = 1; i < tu.ncand; ++i)
+                if (tu.sum[i] / tu.cnt[i] < tu.sum[bi] / tu.cnt[bi]) bi = i;
+            tu.best = tu.cand[bi];
+            ++s->w.gen;  // re-capture the iteration graph with the chosen size
+        }
+    }
 }
 
 // Iterations per partition land in w.pcg_sc ([kMaxParts] ints) for the

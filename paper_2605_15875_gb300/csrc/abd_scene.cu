@@ -52,7 +52,7 @@ int prof_index(abd_scene *s, const char *name) {
     return (int)s->kstats.size() - 1;
 }
 
-static bool capturing(abd_scene *s) {
+bool stream_capturing(abd_scene *s) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (!s->stream || cudaStreamIsCapturing(s->stream, &cs) != cudaSuccess) {
         cudaGetLastError();
@@ -78,7 +78,7 @@ void prof_begin(abd_scene *s, const char *name, double bytes, cudaEvent_t *a, cu
         (k ? *b : *a) = e;
     }
     int idx = prof_index(s, name);
-    if (capturing(s)) {
+    if (stream_capturing(s)) {
         s->ig.ev.push_back({idx, bytes, *a, *b});
         cudaEventRecordWithFlags(*a, s->stream, cudaEventRecordExternal);
         return;
@@ -93,7 +93,7 @@ void prof_add_bytes(abd_scene *s, const char *name, double bytes) {
 
 void prof_end(abd_scene *s, cudaEvent_t a, cudaEvent_t b, int idx) {
     if (!a || !b) return;
-    if (capturing(s)) {
+    if (stream_capturing(s)) {
         cudaEventRecordWithFlags(b, s->stream, cudaEventRecordExternal);
         return;
     }
@@ -395,6 +395,10 @@ extern "C" void abd_scene_destroy(abd_scene *s) {
     cudaStreamSynchronize(s->stream);
     if (s->ig.exec) cudaGraphExecDestroy(s->ig.exec);
     prof_graph_release(s);
+    for (auto &t : s->pcg_tune) {
+        if (t.a) cudaEventDestroy(t.a);
+        if (t.b) cudaEventDestroy(t.b);
+    }
     SceneDev &D = s->dev;
     DBuf *bufs[] = {&D.q, &D.v, &D.mass, &D.S, &D.vol, &D.kappa, &D.kind, &D.voff, &D.nv, &D.toff, &D.nt,
                     &D.eoff, &D.ne, &D.xbar, &D.tri, &D.edge, &D.erest2, &D.vperm, &D.tperm, &D.eperm, &D.cbody_off, &D.crest};

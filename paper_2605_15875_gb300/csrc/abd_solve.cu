@@ -692,6 +692,7 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         int64_t pmax = 0;
         for (int i = 0; i < w.NP; ++i) pmax = std::max<int64_t>(pmax, hs->pcg_iters[i]);
         C.st->pcg_iters += pmax;
+        pcg_tune_observe(s, pmax);
         if (s->prof) {
             // compulsory HBM bytes of one PCG launch: diagonal and distinct
             // off-diagonal blocks, row offsets and entries read once, g read

@@ -641,6 +641,7 @@ struct EnArgs {
     const double *q, *dq, *qtil, *z, *u, *rho;
     const double *x0, *x1;
     const double *alphas;  // [NP][kLS+1], alphas[.][0] = 0
+    const int *live;       // 0: no partition has a trial step in this pass (every thread returns)
     PartState *part;
     double h, dhat, kB;
     Planes planes;
@@ -679,6 +680,7 @@ __device__ double slot_energy(const EnArgs &A, int s, double al) {
 }
 
 __global__ void k_energy_slots(EnArgs A) {
+    if (!*A.live) return;
     for (int64_t base = spread_base(); base < A.S_dyn; base += (int64_t)gridDim.x * blockDim.x) {
         int s = (int)(base + (threadIdx.x & 31));
         int p = s < A.S_dyn ? A.slot_part[s] : -1;
@@ -695,6 +697,7 @@ __global__ void k_energy_slots(EnArgs A) {
 
 __global__ void k_energy_pairs(EnArgs A, const PairRec *__restrict__ ls, int64_t n,
                                const unsigned long long *__restrict__ n_dev) {
+    if (!*A.live) return;
     if (n_dev) n = min((int64_t)*n_dev, n);
     for (int64_t base = spread_base(); base < n; base += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = base + (threadIdx.x & 31);
@@ -730,6 +733,7 @@ __global__ void k_energy_pairs(EnArgs A, const PairRec *__restrict__ ls, int64_t
 }
 
 __global__ void k_energy_vp(EnArgs A, int64_t SVd) {
+    if (!*A.live) return;
     for (int64_t base = spread_base(); base < SVd; base += (int64_t)gridDim.x * blockDim.x) {
         int64_t i = base + (threadIdx.x & 31);
         int p = -1, s = 0;
@@ -866,6 +870,7 @@ int launch_energy_async(abd_scene *s, const abd_step_params *p, double kB, const
     A.q = P<double>(w.q); A.dq = P<double>(w.dq); A.qtil = P<double>(w.qtil); A.z = P<double>(w.z);
     A.u = P<double>(w.u); A.rho = P<double>(w.rho); A.x0 = P<double>(w.x); A.x1 = P<double>(w.x1);
     A.alphas = alphas_dev; A.part = P<PartState>(w.part);
+    A.live = &c->ls_live;
     A.h = p->h; A.dhat = p->dhat; A.kB = kB; A.planes = s->planes;
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
     cudaEvent_t ea, eb;

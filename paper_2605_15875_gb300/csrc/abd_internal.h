@@ -118,6 +118,7 @@ struct Counters {
     int timeout;
     unsigned long long pcg_total;
     int pending;  // line-search passes still undecided
+    int ls_live;  // some partition has trial steps to evaluate in this line-search pass
     int bad;      // a list outgrew its buffer in this iteration
 };
 

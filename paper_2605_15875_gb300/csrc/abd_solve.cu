@@ -116,12 +116,13 @@ __global__ void k_ls_reset(int NP, int *nh0, int *decided) {
 // Line search bookkeeping: trial steps alpha_j = toi 2^-(nh0 + j - 1);
 // alphas[p][0] = -1 marks a partition with nothing left to evaluate.
 __global__ void k_ls_alphas(int NP, PartState *part, const int *nh0, const int *decided, double *alphas,
-                            int max_halv) {
+                            int max_halv, int *live) {
     for (int p = threadIdx.x; p < NP; p += blockDim.x) {
         for (int j = 0; j <= kLS; ++j) part[p].E[j] = 0.0;
         double toi = unord(part[p].toi);
         bool skip = !part[p].active || decided[p];
         alphas[(kLS + 1) * p] = skip ? -1.0 : 0.0;
+        if (!skip) *live = 1;
         for (int j = 1; j <= kLS; ++j) {
             int nh = nh0[p] + j - 1;
             alphas[(kLS + 1) * p + j] = (!skip && nh <= max_halv) ? ldexp(toi < 1.0 ? toi : 1.0, -nh) : -1.0;
@@ -566,8 +567,9 @@ int enqueue_iteration(Ctx &C, bool static_bp, Status *hs) {
     ABD_LAUNCH(s, k_ls_reset, 1, 64, 0, s->stream, w.NP, P<int>(C.nh0), P<int>(C.decided));
     for (int pass = 0; pass < 2; ++pass) {
         cudaMemsetAsync(&dc->pending, 0, sizeof(int), s->stream);
+        cudaMemsetAsync(&dc->ls_live, 0, sizeof(int), s->stream);
         ABD_LAUNCH(s, k_ls_alphas, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
-                   P<int>(C.decided), P<double>(C.alphas), p->max_halvings);
+                   P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->ls_live);
         if ((rc = launch_energy_async(s, p, C.kB, P<double>(C.alphas)))) return rc;
         ABD_LAUNCH(s, k_ls_select, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
                    P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->pending);
@@ -674,8 +676,9 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         // rare: line searches still undecided after 2 * kLS halvings
         for (int guard = 0; hs->c.pending > 0 && guard < 64; ++guard) {
             cudaMemsetAsync(&dc->pending, 0, sizeof(int), s->stream);
+            cudaMemsetAsync(&dc->ls_live, 0, sizeof(int), s->stream);
             ABD_LAUNCH(s, k_ls_alphas, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
-                       P<int>(C.decided), P<double>(C.alphas), p->max_halvings);
+                       P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->ls_live);
             if ((rc = launch_energy_async(s, p, C.kB, P<double>(C.alphas)))) return rc;
             ABD_LAUNCH(s, k_ls_select, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
                        P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->pending);

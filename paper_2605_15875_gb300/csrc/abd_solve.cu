@@ -584,7 +584,7 @@ int enqueue_iteration(Ctx &C, bool static_bp, Status *hs) {
 
 // The steady-state iteration (static_bp false) as a CUDA graph: captured on
 // the scene's stream, re-captured when the world or a list buffer changed
-// (w.gen), and updated in place when the topology is unchanged.  Profiling
+// (w.gen) and instantiated afresh.  Profiling
 // events become graph nodes.  Returns false when capture is not possible
 // (the legacy default stream cannot be captured).
 bool iteration_graph(Ctx &C, Status *hs) {
@@ -610,15 +610,14 @@ bool iteration_graph(Ctx &C, Status *hs) {
         g.disabled = true;
         return false;
     }
+    // always a fresh instantiation (the stream is idle here): an in-place
+    // update would have to carry the PCG node's cluster shape along with its
+    // grid, which change together when the cluster size changes
     if (g.exec) {
-        cudaGraphExecUpdateResultInfo info;
-        if (cudaGraphExecUpdate(g.exec, graph, &info) != cudaSuccess) {
-            cudaGetLastError();
-            cudaGraphExecDestroy(g.exec);
-            g.exec = nullptr;
-        }
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
     }
-    if (!g.exec && cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+    if (cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
         cudaGetLastError();
         g.exec = nullptr;
         cudaGraphDestroy(graph);

@@ -1,15 +1,18 @@
-// abd_broad.cu -- vertex transform and two-level broad phase on sm_103a.
+// abd_broad.cu -- vertex transform and broad phase on sm_103a.
 //
 // Level 1: slot boxes (dhat/2-inflated AABB of a replica's vertices, static or
 // swept) and all overlapping slot pairs (same partition, or a slot against a
-// static collider).  Level 2: one warp per level-1 pair streams the
-// primitives of both slots, keeps those whose box meets the other slot's box
-// (an exact filter: a primitive's box lies inside its slot's box), stages one
-// side in shared memory and tests the other side against it; hits are
-// compacted with warp ballots into the global list.  The resulting set is the
-// plain definition -- every PT (both directions) and EE pair of different
-// slots, not both static, whose dhat/2-inflated boxes overlap -- evaluated
-// with exact FP64 min/max and one rounding per bound.
+// static collider).  Level 2, solver path: stage A lists, per slot pair, the
+// pairs of primitive clusters (32 Morton-ordered primitives of one kind)
+// whose boxes overlap; stage B takes one warp per cluster pair, lane i holding
+// primitive i of each cluster, filters both sides against the other slot's
+// and cluster's box (exact filters: a primitive's box lies inside both),
+// stages the smaller kept set in shared memory and tests the other set
+// against it; hits are compacted with warp ballots.  The no-allocation query
+// keeps the older one-warp-per-slot-pair pass (k_l2) on FP64 boxes.  The
+// resulting set is the plain definition -- every PT (both directions) and EE
+// pair of different slots, not both static, whose dhat/2-inflated boxes
+// overlap -- evaluated with exact FP64 min/max and one rounding per bound.
 //
 // FP64 instructions are scarce on this GPU, so the solver's broad phase
 // filters in FP32: every vertex coordinate carries FP32 bounds rounded

@@ -76,10 +76,9 @@ struct World {
     DBuf xb, xb1;               // [SV][6] FP32 bounds (rounded down, up) of x, x1
     DBuf rep_off, rep_slot, zb, rho0, rhob, rb, sb, body_rep, body_slot;
     DBuf l1, cand, act, ls, diag, off, offflag;
-    DBuf pcg_r, pcg_z, pcg_p, pcg_ap, pcg_sc;
+    DBuf pcg_sc;  // PCG iteration counts per partition and the overflow word
     DBuf part;   // per-partition scalars (PartState)
     DBuf ctr;    // counters
-    DBuf bar;    // grid barrier words
     DBuf aabb;   // body AABBs at the step start
     DBuf part_off;  // [NP + 1] dynamic-slot range of each partition
     DBuf deferred;  // active pairs left to the full 12x12 projection

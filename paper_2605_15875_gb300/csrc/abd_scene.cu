@@ -407,8 +407,8 @@ extern "C" void abd_scene_destroy(abd_scene *s) {
     DBuf *wb[] = {&w.slot_body, &w.slot_part, &w.slot_voff, &w.slot_mask, &w.slot_rep, &w.slot_kw, &w.sv_slot,
                   &w.q, &w.qprev, &w.qtil, &w.z, &w.u, &w.rho, &w.dq, &w.g, &w.x, &w.x1, &w.dx, &w.box, &w.box1,
                   &w.rep_off, &w.rep_slot, &w.zb, &w.rho0, &w.rhob, &w.rb, &w.sb, &w.body_rep, &w.body_slot,
-                  &w.l1, &w.cand, &w.act, &w.ls, &w.diag, &w.off, &w.offflag, &w.pcg_r, &w.pcg_z,
-                  &w.pcg_p, &w.pcg_ap, &w.pcg_sc, &w.part, &w.ctr, &w.bar, &w.aabb, &w.part_off, &w.deferred, &w.rowcnt, &w.rowoff, &w.rowcur, &w.ent, &w.slot_cbase, &w.cl_info, &w.cbox, &w.cbox1, &w.cp, &w.xb, &w.xb1};
+                  &w.l1, &w.cand, &w.act, &w.ls, &w.diag, &w.off, &w.offflag,
+                  &w.pcg_sc, &w.part, &w.ctr, &w.aabb, &w.part_off, &w.deferred, &w.rowcnt, &w.rowoff, &w.rowcur, &w.ent, &w.slot_cbase, &w.cl_info, &w.cbox, &w.cbox1, &w.cp, &w.xb, &w.xb1};
     for (DBuf *b : wb) dbuf_free(*b);
     if (s->pinned) cudaFreeHost(s->pinned);
     for (auto &pe : s->ev_pending) {

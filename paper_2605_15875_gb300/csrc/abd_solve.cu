@@ -436,7 +436,6 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
               dbuf_ensure(w.box1, 48 * S) && dbuf_ensure(w.zb, 96 * NS) && dbuf_ensure(w.rho0, 8 * NS) &&
               dbuf_ensure(w.rhob, 8 * NS) && dbuf_ensure(w.rb, 8 * NS) && dbuf_ensure(w.sb, 8 * NS) &&
               dbuf_ensure(w.part, sizeof(PartState) * kMaxParts) && dbuf_ensure(w.ctr, sizeof(Counters)) &&
-              dbuf_ensure(w.bar, 64) &&
               dbuf_ensure(w.cbox, 48 * (size_t)(w.C ? w.C : 1)) && dbuf_ensure(w.cbox1, 48 * (size_t)(w.C ? w.C : 1));
     if (!ok) return set_err(s, ABD_E_OOM, "world buffers");
     if (w.S_all > 0) ABD_LAUNCH(s, k_fill_sv_slot, std::min(w.S_all, 152 * 8), 256, 0, s->stream, w.S_all, P<int64_t>(w.slot_voff), P<int>(w.sv_slot));

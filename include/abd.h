@@ -19,7 +19,12 @@
  *     vertices of every dynamic body are recentred at its centre of mass and p
  *     is shifted so that world positions are unchanged; abd_state_get/set use
  *     that centred convention.
- *   - Body kinds: ABD_DYNAMIC (12 DoFs), ABD_STATIC (fixed collider).
+ *   - Body kinds: ABD_DYNAMIC (12 DoFs), ABD_STATIC (fixed collider),
+ *     ABD_KINEMATIC (prescribed motion: still 12 DoFs of the solve, but its
+ *     predicted state is its prescribed pose -- p moved by its linear velocity,
+ *     A rotated by R(omega h) about its centre of mass, no gravity -- and its
+ *     inertia carries a weight of 1e6, so contacts cannot move it measurably off
+ *     the prescription; abd_body_props reports the weighted mass and moment).
  *   - Ground planes are axis-aligned: distance = sign * x[axis] - offset.
  *   - All pointers in the descriptors are HOST pointers owned by the caller;
  *     the library copies what it needs before returning.
@@ -67,9 +72,12 @@ typedef struct {
     const int32_t *body_mesh;      /* [B] */
     const double *body_density;    /* [B] kg/m^3 (dynamic bodies) */
     const double *body_kappa;      /* [B] orthogonality stiffness kappa of kappa V ||A A^T - I||_F^2 */
-    const int32_t *body_kind;      /* [B] ABD_DYNAMIC or ABD_STATIC */
+    const int32_t *body_kind;      /* [B] ABD_DYNAMIC, ABD_STATIC or ABD_KINEMATIC */
     const double *body_q0;         /* [B][12] initial q in the mesh frame */
     const double *body_v0;         /* [B][12] initial qdot, or NULL for zero */
+    const double *body_omega;      /* [B][3] angular velocity of ABD_KINEMATIC bodies about their centre of
+                                      mass (world frame, rad/s), or NULL; their linear velocity is
+                                      body_v0[0..3] */
     int32_t n_planes;              /* <= 8 */
     const int32_t *plane_axis;     /* [n_planes] 0, 1 or 2 */
     const double *plane_sign;      /* [n_planes] +1 or -1 */
@@ -125,8 +133,8 @@ typedef struct {
  * second moment, volume, edges).  `cuda_stream` is a cudaStream_t (NULL: the
  * legacy default stream) on which every later call on this scene enqueues
  * work; the current CUDA device becomes the scene's device.
- * Errors: ABD_E_INVALID (bad indices, open or inverted dynamic mesh, more
- * than 8 planes, kinematic body), ABD_E_OOM, ABD_E_CUDA. */
+ * Errors: ABD_E_INVALID (bad indices, open or inverted dynamic or kinematic
+ * mesh, more than 8 planes, unknown kind), ABD_E_OOM, ABD_E_CUDA. */
 int abd_scene_create(const abd_scene_desc *desc, void *cuda_stream, abd_scene **out);
 void abd_scene_destroy(abd_scene *s);
 

@@ -28,6 +28,38 @@
 
 #define ORC_INF (1.0 / 0.0)
 
+/* Kinematic bodies (reading: the paper's turntables have prescribed motion
+ * and no stated treatment).  A kinematic body stays a DOF of the solve like a
+ * dynamic one, but its predicted state q~ is its prescribed pose -- p moved by
+ * its linear velocity, A rotated by R(omega h) about the centre of mass, no
+ * gravity -- and its inertia term is weighted by ORC_KIN_WEIGHT, so contacts
+ * cannot move it measurably off the prescription while barrier and CCD keep
+ * every step penetration-free. */
+#define ORC_KIN_WEIGHT 1e6
+
+static int is_dof(int kind) { return kind != ORC_STATIC; }
+
+/* Prescribed pose after h: p + h v_p, and A rotated by the angle |omega| h
+ * about the axis omega (Rodrigues' formula R = I + sin t K + (1 - cos t) K^2,
+ * K the cross-product matrix of the unit axis), A' = R A. */
+static void kinematic_pose(const double *q, const double *v, const double *w, double h, double *out) {
+    for (int k = 0; k < 3; ++k) out[k] = q[k] + h * v[k];
+    double n = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]), R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (n > 0.0) {
+        double u[3] = {w[0] / n, w[1] / n, w[2] / n}, t = n * h, sn = sin(t), c1 = 1.0 - cos(t);
+        double K[9] = {0, -u[2], u[1], u[2], 0, -u[0], -u[1], u[0], 0};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double k2 = 0.0;
+                for (int l = 0; l < 3; ++l) k2 += K[3 * i + l] * K[3 * l + j];
+                R[3 * i + j] += sn * K[3 * i + j] + c1 * k2;
+            }
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            out[3 + 3 * i + j] = R[3 * i] * q[3 + j] + R[3 * i + 1] * q[6 + j] + R[3 * i + 2] * q[9 + j];
+}
+
 /* ------------------------------------------------------------------------ */
 /* small helpers                                                             */
 /* ------------------------------------------------------------------------ */
@@ -554,6 +586,7 @@ struct orc_scene {
     double *xbar, *erest2;
     int *tri, *edge;
     double *q, *v;
+    double *omega;   /* [B][3] kinematic angular velocity */
     int *pax;
     double *psg, *poff;
     double g[3];
@@ -593,7 +626,7 @@ void orc_scene_destroy(orc_scene *s) {
     if (!s) return;
     free(s->kind); free(s->voff); free(s->nv); free(s->toff); free(s->nt); free(s->eoff); free(s->ne);
     free(s->mass); free(s->S); free(s->vol); free(s->kappa); free(s->com);
-    free(s->xbar); free(s->erest2); free(s->tri); free(s->edge); free(s->q); free(s->v);
+    free(s->xbar); free(s->erest2); free(s->tri); free(s->edge); free(s->q); free(s->v); free(s->omega);
     free(s->pax); free(s->psg); free(s->poff);
     free(s);
 }
@@ -621,8 +654,9 @@ int orc_scene_create(const orc_scene_desc *d, orc_scene **out) {
     s->vol = (double *)calloc(nb, sizeof(double)); s->kappa = (double *)calloc(nb, sizeof(double));
     s->com = (double *)calloc(3 * (size_t)nb, sizeof(double));
     s->q = (double *)malloc(sizeof(double) * 12 * nb); s->v = (double *)malloc(sizeof(double) * 12 * nb);
+    s->omega = (double *)calloc(3 * (size_t)nb, sizeof(double));
     if (!s->kind || !s->voff || !s->nv || !s->toff || !s->nt || !s->eoff || !s->ne || !s->mass || !s->S ||
-        !s->vol || !s->kappa || !s->com || !s->q || !s->v) { rc = ORC_E_OOM; goto fail; }
+        !s->vol || !s->kappa || !s->com || !s->q || !s->v || !s->omega) { rc = ORC_E_OOM; goto fail; }
     s->voff[0] = s->toff[0] = s->eoff[0] = 0;
     for (int b = 0; b < nb; ++b) {
         int m = d->body_mesh[b];
@@ -648,12 +682,19 @@ int orc_scene_create(const orc_scene_desc *d, orc_scene **out) {
         if (d->body_v0) memcpy(s->v + 12 * b, d->body_v0 + 12 * b, sizeof(double) * 12);
         else memset(s->v + 12 * b, 0, sizeof(double) * 12);
         double com[3] = {0, 0, 0};
-        if (s->kind[b] == ORC_DYNAMIC) {
+        if (s->kind[b] != ORC_DYNAMIC && s->kind[b] != ORC_STATIC && s->kind[b] != ORC_KINEMATIC) {
+            rc = ORC_E_INVALID;
+            goto fail;
+        }
+        if (is_dof(s->kind[b])) {
             if (orc_mass_properties(s->nv[b], mx, s->nt[b], mt, d->body_density[b], &s->mass[b], com,
                                     s->S + 9 * b, &s->vol[b]) != ORC_OK) { rc = ORC_E_INVALID; goto fail; }
-        } else if (s->kind[b] != ORC_STATIC) {
-            rc = ORC_E_INVALID; /* kinematic colliders are not modelled by this oracle */
-            goto fail;
+        }
+        if (s->kind[b] == ORC_KINEMATIC) {
+            s->mass[b] *= ORC_KIN_WEIGHT;
+            for (int i = 0; i < 9; ++i) s->S[9 * b + i] *= ORC_KIN_WEIGHT;
+            if (d->body_omega)
+                for (int k = 0; k < 3; ++k) s->omega[3 * b + k] = d->body_omega[3 * b + k];
         }
         memcpy(s->com + 3 * b, com, sizeof com);
         /* recentre xbar at the centre of mass and move p so x is unchanged */
@@ -829,7 +870,7 @@ static int enumerate_pairs(const orc_scene *s, const int *bodies, int nbod, cons
     for (int i = 0; i < nbod && !rc; ++i)
         for (int j = i + 1; j < nbod && !rc; ++j) {
             int a = bodies[i], b = bodies[j];
-            if (s->kind[a] != ORC_DYNAMIC && s->kind[b] != ORC_DYNAMIC) continue;
+            if (!is_dof(s->kind[a]) && !is_dof(s->kind[b])) continue;
             if (!box_overlap(&bb[i], &bb[j])) continue;
             int nVa = 0, nTa = 0, nEa = 0, nVb = 0, nTb = 0, nEb = 0;
             for (int pass = 0; pass < 2; ++pass) {
@@ -935,8 +976,8 @@ static double kappa_b(const local_t *L, int b) { return (double)popcount64(L->ma
 
 static double kappa_c(const local_t *L, int a, int b) {
     const orc_scene *s = L->s;
-    if (s->kind[a] != ORC_DYNAMIC) return (double)popcount64(L->mask[b]);
-    if (s->kind[b] != ORC_DYNAMIC) return (double)popcount64(L->mask[a]);
+    if (!is_dof(s->kind[a])) return (double)popcount64(L->mask[b]);
+    if (!is_dof(s->kind[b])) return (double)popcount64(L->mask[a]);
     return (double)popcount64(L->mask[a] & L->mask[b]);
 }
 
@@ -1395,7 +1436,7 @@ int orc_partition(orc_scene *s, const orc_params *P, uint64_t *mask, double *w_o
     double *lo = (double *)malloc(sizeof(double) * s->nb), *hi = (double *)malloc(sizeof(double) * s->nb);
     if (!lo || !hi) { free(lo); free(hi); return ORC_E_OOM; }
     for (int b = 0; b < s->nb; ++b) {
-        if (s->kind[b] != ORC_DYNAMIC) continue;
+        if (!is_dof(s->kind[b])) continue;
         double l3[3], h3[3];
         body_aabb(s, b, s->q + 12 * b, l3, h3);
         lo[b] = l3[ax]; hi[b] = h3[ax];
@@ -1411,7 +1452,7 @@ int orc_partition(orc_scene *s, const orc_params *P, uint64_t *mask, double *w_o
     double w = dmax(P->alpha_w * vmax * P->h, wmin);
     for (int b = 0; b < s->nb; ++b) {
         mask[b] = 0;
-        if (s->kind[b] != ORC_DYNAMIC) continue;
+        if (!is_dof(s->kind[b])) continue;
         for (int i = 0; i < N; ++i) {
             double rlo = i == 0 ? -ORC_INF : gam[i] - 0.5 * w;
             double rhi = i == N - 1 ? ORC_INF : gam[i + 1] + 0.5 * w;
@@ -1438,7 +1479,7 @@ static int local_init(local_t *L, orc_scene *s, const uint64_t *mask, int part, 
     L->accd_s = P->accd_s; L->accd_c = P->accd_c; L->max_newton = P->max_newton; L->max_halv = P->max_halvings;
     int ns = 0;
     for (int b = 0; b < s->nb; ++b)
-        if (s->kind[b] == ORC_DYNAMIC && (mask[b] >> part & 1)) ++ns;
+        if (is_dof(s->kind[b]) && (mask[b] >> part & 1)) ++ns;
     L->ns = ns;
     L->body = (int *)malloc(sizeof(int) * (ns + 1));
     L->sob = (int *)malloc(sizeof(int) * s->nb);
@@ -1456,7 +1497,7 @@ static int local_init(local_t *L, orc_scene *s, const uint64_t *mask, int part, 
     int k = 0;
     for (int b = 0; b < s->nb; ++b) {
         L->sob[b] = -1;
-        if (s->kind[b] == ORC_DYNAMIC && (mask[b] >> part & 1)) {
+        if (is_dof(s->kind[b]) && (mask[b] >> part & 1)) {
             L->sob[b] = k;
             L->body[k] = b;
             memcpy(L->q + 12 * k, q_all + 12 * b, sizeof(double) * 12);
@@ -1468,7 +1509,7 @@ static int local_init(local_t *L, orc_scene *s, const uint64_t *mask, int part, 
     L->nobj = 0;
     for (int i = 0; i < ns; ++i) L->objs[L->nobj++] = L->body[i];
     for (int b = 0; b < s->nb; ++b)
-        if (s->kind[b] != ORC_DYNAMIC) L->objs[L->nobj++] = b;
+        if (!is_dof(s->kind[b])) L->objs[L->nobj++] = b;
     return ORC_OK;
 }
 
@@ -1503,7 +1544,7 @@ static double scene_min_distance(orc_scene *s, double dhat) {
         }
     }
     for (int b = 0; b < s->nb; ++b) {
-        if (s->kind[b] != ORC_DYNAMIC) continue;
+        if (!is_dof(s->kind[b])) continue;
         for (int v = 0; v < s->nv[b]; ++v)
             for (int pl = 0; pl < s->np; ++pl)
                 md = dmin(md, s->psg[pl] * x[3 * (s->voff[b] + v) + s->pax[pl]] - s->poff[pl]);
@@ -1541,6 +1582,8 @@ int orc_step(orc_scene *s, const orc_params *P, orc_stats *st) {
         for (int i = 0; i < 12; ++i) qtil[12 * b + i] = qt[12 * b + i] + P->h * s->v[12 * b + i];
         if (s->kind[b] == ORC_DYNAMIC)
             for (int k = 0; k < 3; ++k) qtil[12 * b + k] += P->h * P->h * s->g[k];
+        else if (s->kind[b] == ORC_KINEMATIC)
+            kinematic_pose(qt + 12 * b, s->v + 12 * b, s->omega + 3 * b, P->h, qtil + 12 * b);
         else memcpy(qtil + 12 * b, qt + 12 * b, sizeof(double) * 12);
         ones[b] = 1;
     }
@@ -1557,7 +1600,7 @@ int orc_step(orc_scene *s, const orc_params *P, orc_stats *st) {
     if (rc) goto out;
     int nshared = 0, nslots = 0;
     for (int b = 0; b < nb; ++b) {
-        if (s->kind[b] != ORC_DYNAMIC) continue;
+        if (!is_dof(s->kind[b])) continue;
         int c = popcount64(mask[b]);
         nslots += c;
         if (c >= 2) ++nshared;
@@ -1599,7 +1642,7 @@ int orc_step(orc_scene *s, const orc_params *P, orc_stats *st) {
                 double *rb = (double *)calloc(nb, sizeof(double));
                 if (!rb) { rc = ORC_E_OOM; goto out; }
                 for (int b = 0; b < nb; ++b) {
-                    if (s->kind[b] != ORC_DYNAMIC || popcount64(mask[b]) < 2) continue;
+                    if (!is_dof(s->kind[b]) || popcount64(mask[b]) < 2) continue;
                     double num[12] = {0}, den = 0.0;
                     for (int i = 0; i < N; ++i) {
                         int sl = parts[i].sob[b];
@@ -1649,7 +1692,7 @@ int orc_step(orc_scene *s, const orc_params *P, orc_stats *st) {
                 if (k == K + 1) { free(rb); break; }
                 if (P->rho_adaptive) {
                     for (int b = 0; b < nb; ++b) {
-                        if (s->kind[b] != ORC_DYNAMIC || popcount64(mask[b]) < 2) continue;
+                        if (!is_dof(s->kind[b]) || popcount64(mask[b]) < 2) continue;
                         double r = rb[b], sb = sbody[b], old = rhob[b], nw = old;
                         if (r > P->mu * sb) nw = old * P->tau;
                         else if (sb > P->mu * r) nw = old / P->tau;
@@ -1704,7 +1747,7 @@ int orc_step(orc_scene *s, const orc_params *P, orc_stats *st) {
         if (rc) goto out;
     }
     for (int b = 0; b < nb; ++b)
-        if (s->kind[b] == ORC_DYNAMIC)
+        if (is_dof(s->kind[b]))
             for (int i = 0; i < 12; ++i) s->v[12 * b + i] = (qnew[12 * b + i] - qt[12 * b + i]) / P->h;
     memcpy(s->q, qnew, sizeof(double) * 12 * nb);
     double md = scene_min_distance(s, P->dhat);
@@ -1739,7 +1782,7 @@ int orc_objective(orc_scene *s, const orc_params *P, const double *q, const doub
         memcpy(qa, s->q, sizeof(double) * 12 * s->nb);
         memcpy(qt, s->q, sizeof(double) * 12 * s->nb);
         for (int b = 0; b < s->nb; ++b)
-            if (s->kind[b] == ORC_DYNAMIC) {
+            if (is_dof(s->kind[b])) {
                 memcpy(qa + 12 * b, q + 12 * k, sizeof(double) * 12);
                 memcpy(qt + 12 * b, qtil + 12 * k, sizeof(double) * 12);
                 ++k;

@@ -44,6 +44,8 @@ typedef struct {
     const double *body_density, *body_kappa;
     const int32_t *body_kind;
     const double *body_q0, *body_v0; /* [B][12] */
+    const double *body_omega;        /* [B][3] angular velocity of kinematic bodies about their centre
+                                        of mass (world frame, rad/s), or NULL */
     int32_t n_planes;
     const int32_t *plane_axis;
     const double *plane_sign, *plane_offset;

@@ -26,6 +26,7 @@ class SceneDesc(C.Structure):
                 ("mesh_xbar", C.c_void_p), ("mesh_tris", C.c_void_p), ("n_bodies", C.c_int32),
                 ("body_mesh", C.c_void_p), ("body_density", C.c_void_p), ("body_kappa", C.c_void_p),
                 ("body_kind", C.c_void_p), ("body_q0", C.c_void_p), ("body_v0", C.c_void_p),
+                ("body_omega", C.c_void_p),
                 ("n_planes", C.c_int32), ("plane_axis", C.c_void_p), ("plane_sign", C.c_void_p),
                 ("plane_offset", C.c_void_p), ("gravity", C.c_double * 3)]
 
@@ -171,6 +172,7 @@ def scene_desc(sa) -> SceneDesc:
     d.n_bodies = sa.n_bodies
     d.body_mesh, d.body_density, d.body_kappa = _p(sa.body_mesh), _p(sa.body_density), _p(sa.body_kappa)
     d.body_kind, d.body_q0, d.body_v0 = _p(sa.body_kind), _p(sa.body_q0), _p(sa.body_v0)
+    d.body_omega = _p(getattr(sa, "body_omega", None))
     d.n_planes = len(sa.plane_axis)
     d.plane_axis, d.plane_sign, d.plane_offset = _p(sa.plane_axis), _p(sa.plane_sign), _p(sa.plane_offset)
     for k in range(3):

@@ -60,10 +60,14 @@ struct SceneDev {
     // rest-frame Morton order (body-local ids), chunked by 32
     DBuf vperm, tperm, eperm;
     DBuf cbody_off;  // [B + 1] first cluster of each body (vertices, triangles, edges)
+    DBuf omega;      // [B][3] angular velocity of kinematic bodies
     DBuf crest;      // [clusters][6] FP32 rest-frame box of each cluster's vertices (centre, half extent)
 };
 
 constexpr int kClusterSize = 32;
+// Inertia weight of kinematic bodies (prescribed motion through their
+// predicted state, see include/abd.h).
+constexpr double kKinematicWeight = 1e6;
 
 // Per-step workspace of the consensus solve.
 struct World {

@@ -63,7 +63,7 @@ __global__ void k_noalloc_tables(int nb, const int *__restrict__ kind, const int
         slot_voff[i] = voff[i];
         if (i == nb) continue;
         slot_body[i] = i;
-        slot_part[i] = kind[i] == ABD_DYNAMIC ? 0 : -1;
+        slot_part[i] = kind[i] != ABD_STATIC ? 0 : -1;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         PartState p = {};

@@ -260,24 +260,32 @@ extern "C" int abd_scene_create(const abd_scene_desc *d, void *stream, abd_scene
     if (s->V >= (1ll << 31) || s->T >= (1ll << 31) || s->E >= (1ll << 31)) { delete s; return ABD_E_INVALID; }
     s->xbar.resize(3 * (size_t)s->V); s->tri.resize(3 * (size_t)s->T); s->edge.resize(2 * (size_t)s->E);
     s->erest2.resize((size_t)s->E);
-    std::vector<double> q(12 * (size_t)nb), v(12 * (size_t)nb, 0.0);
+    std::vector<double> q(12 * (size_t)nb), v(12 * (size_t)nb, 0.0), omega(3 * (size_t)nb, 0.0);
     for (int b = 0; b < nb; ++b) {
         int m = d->body_mesh[b];
         s->kind[b] = d->body_kind[b];
         s->kappa[b] = d->body_kappa[b];
-        if (s->kind[b] != ABD_DYNAMIC && s->kind[b] != ABD_STATIC) {
+        if (s->kind[b] != ABD_DYNAMIC && s->kind[b] != ABD_STATIC && s->kind[b] != ABD_KINEMATIC) {
             delete s;
-            return ABD_E_INVALID;  // kinematic colliders are not supported by this build
+            return ABD_E_INVALID;
         }
         const double *mx = d->mesh_xbar + 3 * mvo[m];
         const int32_t *mt = d->mesh_tris + 3 * mto[m];
         double com[3] = {0, 0, 0};
-        if (s->kind[b] == ABD_DYNAMIC) {
+        if (s->kind[b] != ABD_STATIC) {
             if (!mesh_mass(mx, s->nv[b], mt, s->nt[b], d->body_density[b], s->mass[b], com, &s->S[9 * (size_t)b],
                            s->vol[b])) {
                 delete s;
                 return ABD_E_INVALID;
             }
+        }
+        if (s->kind[b] == ABD_KINEMATIC) {
+            // prescribed motion: inertia weighted so that contacts cannot
+            // move the body measurably off its predicted (prescribed) pose
+            s->mass[b] *= kKinematicWeight;
+            for (int i = 0; i < 9; ++i) s->S[9 * (size_t)b + i] *= kKinematicWeight;
+            if (d->body_omega)
+                for (int k = 0; k < 3; ++k) omega[3 * (size_t)b + k] = d->body_omega[3 * (size_t)b + k];
         }
         for (int k = 0; k < 3; ++k) s->com[3 * (size_t)b + k] = com[k];
         for (int i = 0; i < s->nv[b]; ++i)
@@ -380,6 +388,7 @@ extern "C" int abd_scene_create(const abd_scene_desc *d, void *stream, abd_scene
               upload(s, D.tperm, s->tperm.data(), s->tperm.size() * 4) &&
               upload(s, D.eperm, s->eperm.data(), s->eperm.size() * 4) &&
               upload(s, D.cbody_off, s->cbody_off.data(), s->cbody_off.size() * 4) &&
+              upload(s, D.omega, omega.data(), omega.size() * 8) &&
               upload(s, D.crest, std::vector<float>(s->crest.begin(), s->crest.end()).data(), s->crest.size() * 4);
     if (!ok) {
         abd_scene_destroy(s);
@@ -401,7 +410,7 @@ extern "C" void abd_scene_destroy(abd_scene *s) {
     }
     SceneDev &D = s->dev;
     DBuf *bufs[] = {&D.q, &D.v, &D.mass, &D.S, &D.vol, &D.kappa, &D.kind, &D.voff, &D.nv, &D.toff, &D.nt,
-                    &D.eoff, &D.ne, &D.xbar, &D.tri, &D.edge, &D.erest2, &D.vperm, &D.tperm, &D.eperm, &D.cbody_off, &D.crest};
+                    &D.eoff, &D.ne, &D.xbar, &D.tri, &D.edge, &D.erest2, &D.vperm, &D.tperm, &D.eperm, &D.cbody_off, &D.crest, &D.omega};
     for (DBuf *b : bufs) dbuf_free(*b);
     World &w = s->w;
     DBuf *wb[] = {&w.slot_body, &w.slot_part, &w.slot_voff, &w.slot_mask, &w.slot_rep, &w.slot_kw, &w.sv_slot,

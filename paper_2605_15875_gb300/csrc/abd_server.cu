@@ -36,7 +36,8 @@ double now_ms() {
 // may be freed once submit returns).
 struct OwnedScene {
     std::vector<int32_t> mesh_n_verts, mesh_n_tris, mesh_tris, body_mesh, body_kind, plane_axis;
-    std::vector<double> mesh_xbar, body_density, body_kappa, body_q0, body_v0, plane_sign, plane_offset, planes;
+    std::vector<double> mesh_xbar, body_density, body_kappa, body_q0, body_v0, body_omega, plane_sign, plane_offset,
+        planes;
     abd_scene_desc d{};
     abd_partition_desc p{};
     bool has_part = false;
@@ -71,6 +72,7 @@ struct OwnedScene {
         take(body_kind, s->body_kind, B);
         take(body_q0, s->body_q0, 12 * B);
         take(body_v0, s->body_v0, 12 * B);
+        take(body_omega, s->body_omega, 3 * B);
         if (P && (!s->plane_axis || !s->plane_sign || !s->plane_offset)) return ABD_E_INVALID;
         take(plane_axis, s->plane_axis, P);
         take(plane_sign, s->plane_sign, P);
@@ -86,6 +88,7 @@ struct OwnedScene {
         d.body_kind = body_kind.data();
         d.body_q0 = body_q0.data();
         d.body_v0 = body_v0.empty() ? nullptr : body_v0.data();
+        d.body_omega = body_omega.empty() ? nullptr : body_omega.data();
         d.plane_axis = P ? plane_axis.data() : nullptr;
         d.plane_sign = P ? plane_sign.data() : nullptr;
         d.plane_offset = P ? plane_offset.data() : nullptr;

@@ -51,22 +51,52 @@ __global__ void k_fill_sv_slot(int S, const int64_t *__restrict__ slot_voff, int
         for (int64_t v = slot_voff[s] + threadIdx.x; v < slot_voff[s + 1]; v += blockDim.x) sv_slot[v] = s;
 }
 
-// q^t, q~ (gravity only, Sec. 3), z = q~, u = 0, rho = beta m per slot.
+// Prescribed pose of a kinematic body after h: p + h v_p, and A rotated by the
+// angle |omega| h about the axis omega (Rodrigues' formula
+// R = I + sin t K + (1 - cos t) K^2, K the cross-product matrix of the unit
+// axis), A' = R A.
+__device__ void kinematic_pose(const double *q, const double *v, const double *w, double h, double *out) {
+    for (int k = 0; k < 3; ++k) out[k] = q[k] + h * v[k];
+    double n = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]), R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    if (n > 0.0) {
+        double u[3] = {w[0] / n, w[1] / n, w[2] / n}, t = n * h, sn = sin(t), c1 = 1.0 - cos(t);
+        double K[9] = {0, -u[2], u[1], u[2], 0, -u[0], -u[1], u[0], 0};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double k2 = 0.0;
+                for (int l = 0; l < 3; ++l) k2 += K[3 * i + l] * K[3 * l + j];
+                R[3 * i + j] += sn * K[3 * i + j] + c1 * k2;
+            }
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            out[3 + 3 * i + j] = R[3 * i] * q[3 + j] + R[3 * i + 1] * q[6 + j] + R[3 * i + 2] * q[9 + j];
+}
+
+// q^t, q~ (gravity only for dynamic bodies, Sec. 3; the prescribed pose for
+// kinematic ones), z = q~, u = 0, rho = beta m per slot.
 __global__ void k_slot_init(int S_all, int S_dyn, const int *__restrict__ slot_body, const int *__restrict__ slot_rep,
                             const double *__restrict__ qb, const double *__restrict__ vb, const double *__restrict__ mass,
-                            double h, double gx, double gy, double gz, double beta, double *__restrict__ q,
-                            double *__restrict__ qtil, double *__restrict__ z, double *__restrict__ u,
-                            double *__restrict__ rho) {
+                            const int *__restrict__ kind, const double *__restrict__ omega, double h, double gx,
+                            double gy, double gz, double beta, double *__restrict__ q, double *__restrict__ qtil,
+                            double *__restrict__ z, double *__restrict__ u, double *__restrict__ rho) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S_all; s += gridDim.x * blockDim.x) {
         int b = slot_body[s];
         for (int i = 0; i < 12; ++i) q[12 * (int64_t)s + i] = qb[12 * (int64_t)b + i];
         if (s >= S_dyn) continue;
-        double gg[3] = {gx, gy, gz};
+        double t12[12];
+        if (kind[b] == ABD_KINEMATIC) {
+            kinematic_pose(qb + 12 * (int64_t)b, vb + 12 * (int64_t)b, omega + 3 * (int64_t)b, h, t12);
+        } else {
+            double gg[3] = {gx, gy, gz};
+            for (int i = 0; i < 12; ++i) {
+                t12[i] = qb[12 * (int64_t)b + i] + h * vb[12 * (int64_t)b + i];
+                if (i < 3) t12[i] += h * h * gg[i];
+            }
+        }
         for (int i = 0; i < 12; ++i) {
-            double t = qb[12 * (int64_t)b + i] + h * vb[12 * (int64_t)b + i];
-            if (i < 3) t += h * h * gg[i];
-            qtil[12 * (int64_t)s + i] = t;
-            z[12 * (int64_t)s + i] = t;
+            qtil[12 * (int64_t)s + i] = t12[i];
+            z[12 * (int64_t)s + i] = t12[i];
             u[12 * (int64_t)s + i] = 0.0;
         }
         rho[s] = beta * mass[b];
@@ -256,7 +286,7 @@ __global__ void k_merge(int nb, const int *__restrict__ kind, const int *__restr
                         const int *__restrict__ body_slot, const double *__restrict__ zb, const double *__restrict__ q,
                         double h, double *__restrict__ qbody, double *__restrict__ vbody) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
-        if (kind[b] != ABD_DYNAMIC || (body_rep[b] < 0 && body_slot[b] < 0)) continue;
+        if (kind[b] == ABD_STATIC || (body_rep[b] < 0 && body_slot[b] < 0)) continue;
         const double *src = body_rep[b] >= 0 ? zb + 12 * (int64_t)body_rep[b] : q + 12 * (int64_t)body_slot[b];
         for (int i = 0; i < 12; ++i) {
             double qn = src[i];
@@ -324,13 +354,13 @@ int compute_masks(abd_scene *s, double h, const std::vector<double> &box, const 
     int N = s->n_slabs, ax = s->axis;
     mask.assign(s->nb, 0);
     if (N <= 1) {
-        for (int b = 0; b < s->nb; ++b) mask[b] = s->kind[b] == ABD_DYNAMIC ? 1 : 0;
+        for (int b = 0; b < s->nb; ++b) mask[b] = s->kind[b] != ABD_STATIC ? 1 : 0;
         w_out = 0.0;
         return ABD_OK;
     }
     double Lo = INFINITY, Hi = -INFINITY, vmax = 0.0, wmin = INFINITY;
     for (int b = 0; b < s->nb; ++b) {
-        if (s->kind[b] != ABD_DYNAMIC) continue;
+        if (s->kind[b] == ABD_STATIC) continue;
         const double *bx = &box[6 * (size_t)b];
         Lo = std::min(Lo, bx[ax]);
         Hi = std::max(Hi, bx[3 + ax]);
@@ -345,7 +375,7 @@ int compute_masks(abd_scene *s, double h, const std::vector<double> &box, const 
     if (s->w_min > 0.0) wmin = s->w_min;
     double w = std::max(s->alpha_w * vmax * h, wmin);
     for (int b = 0; b < s->nb; ++b) {
-        if (s->kind[b] != ABD_DYNAMIC) continue;
+        if (s->kind[b] == ABD_STATIC) continue;
         double lo = box[6 * (size_t)b + ax], hi = box[6 * (size_t)b + 3 + ax];
         for (int i = 0; i < N; ++i) {
             double rlo = i == 0 ? -INFINITY : gam[i] - 0.5 * w;
@@ -369,11 +399,11 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
     w.h_body_slot.assign(s->nb, -1);
     int nsh = 0;
     for (int b = 0; b < s->nb; ++b)
-        if (s->kind[b] == ABD_DYNAMIC && __builtin_popcountll(mask[b]) >= 2) w.h_body_rep[b] = nsh++;
+        if (s->kind[b] != ABD_STATIC && __builtin_popcountll(mask[b]) >= 2) w.h_body_rep[b] = nsh++;
     std::vector<std::vector<int>> reps(nsh);
     for (int p = 0; p < nparts; ++p)
         for (int b = 0; b < s->nb; ++b) {
-            if (s->kind[b] != ABD_DYNAMIC || !((mask[b] >> p) & 1)) continue;
+            if (s->kind[b] == ABD_STATIC || !((mask[b] >> p) & 1)) continue;
             int sl = (int)w.h_slot_body.size();
             w.h_slot_body.push_back(b);
             w.h_slot_part.push_back(p);
@@ -388,7 +418,7 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
     for (int i = 0; i < w.S_dyn; ++i) w.h_part_off[w.h_slot_part[i] + 1]++;
     for (int p = 0; p < nparts; ++p) w.h_part_off[p + 1] += w.h_part_off[p];
     for (int b = 0; b < s->nb; ++b)
-        if (s->kind[b] != ABD_DYNAMIC) {
+        if (s->kind[b] == ABD_STATIC) {
             w.h_slot_body.push_back(b);
             w.h_slot_part.push_back(-1);
             w.h_slot_mask.push_back(0);
@@ -833,7 +863,8 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
     st->n_partitions = N; st->n_shared = w.nsh; st->n_slots = w.S_dyn;
     ABD_LAUNCH(s, k_slot_init, grid_for(w.S_all, 128), 128, 0, s->stream, w.S_all, w.S_dyn, P<int>(w.slot_body), P<int>(w.slot_rep),
                                                               P<double>(s->dev.q), P<double>(s->dev.v),
-                                                              P<double>(s->dev.mass), p->h, s->g[0], s->g[1], s->g[2],
+                                                              P<double>(s->dev.mass), P<int>(s->dev.kind),
+                                                              P<double>(s->dev.omega), p->h, s->g[0], s->g[1], s->g[2],
                                                               p->beta, P<double>(w.q), P<double>(w.qtil),
                                                               P<double>(w.z), P<double>(w.u), P<double>(w.rho));
     if (w.nsh > 0)
@@ -958,7 +989,7 @@ extern "C" int abd_candidates(abd_scene *s, const double *x0, const double *x1, 
                               int64_t *n_out) {
     if (!s || !x0 || dhat <= 0 || !n_out) return ABD_E_INVALID;
     std::vector<uint64_t> mask(s->nb);
-    for (int b = 0; b < s->nb; ++b) mask[b] = s->kind[b] == ABD_DYNAMIC ? 1 : 0;
+    for (int b = 0; b < s->nb; ++b) mask[b] = s->kind[b] != ABD_STATIC ? 1 : 0;
     int rc = build_world(s, mask, 1);
     if (rc) return rc;
     World &w = s->w;

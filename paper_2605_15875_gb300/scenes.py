@@ -56,6 +56,7 @@ class SceneArrays:
     plane_offset: np.ndarray
     gravity: np.ndarray  # [3]
     name: str = ""
+    body_omega: Optional[np.ndarray] = None  # [B, 3] angular velocity of kinematic bodies
 
     @property
     def n_bodies(self) -> int:
@@ -94,7 +95,7 @@ class SceneArrays:
 
 
 def _pack(meshes: Sequence[Mesh], body_mesh, density, kappa, kind, q0, v0,
-          planes=(), gravity=(0.0, -9.8, 0.0), name="") -> SceneArrays:
+          planes=(), gravity=(0.0, -9.8, 0.0), name="", omega=None) -> SceneArrays:
     body_mesh = np.asarray(body_mesh, dtype=np.int32)
     B = body_mesh.shape[0]
     q0 = np.asarray(q0, dtype=np.float64).reshape(B, 12)
@@ -116,6 +117,8 @@ def _pack(meshes: Sequence[Mesh], body_mesh, density, kappa, kind, q0, v0,
         plane_offset=np.array([p[2] for p in planes], dtype=np.float64),
         gravity=np.asarray(gravity, dtype=np.float64),
         name=name,
+        body_omega=np.ascontiguousarray(np.zeros((B, 3)) if omega is None
+                                        else np.asarray(omega, np.float64).reshape(B, 3)),
     )
 
 
@@ -144,6 +147,12 @@ def cube_mesh(size: float = 1.0) -> Mesh:
         t.append((a, c, d))
     tris = _orient_outward(v, np.array(t, dtype=np.int32), np.zeros(3))
     return Mesh(v, tris.astype(np.int32))
+
+
+def box_mesh(ex: float, ey: float, ez: float) -> Mesh:
+    """Closed axis-aligned box centred at the origin with extents ex, ey, ez."""
+    c = cube_mesh(1.0)
+    return Mesh(c.xbar * np.array([ex, ey, ez]), c.tris.copy())
 
 
 def icosphere(level: int) -> Mesh:
@@ -321,3 +330,26 @@ def serving_requests(seed: int = 0, n_scenes: int = 256, lo: int = 8, hi: int = 
             sc = random_pile(int(seed * 1000 + i), int(s), levels=(1, 2))
         out.append((sc, steps))
     return out
+
+
+def kinematic_sweeper(seed: int = 0, n_cubes: int = 3, omega: float = 2.0, size: float = 0.1,
+                      gap: float = 0.002, density: float = 1000.0, kappa: float = 1e8) -> SceneArrays:
+    """A kinematic bar (1.0 x 0.1 x 0.1, centre 0.11 above the ground plane
+    y = 0) spinning about the vertical axis through its centre at `omega`
+    rad/s (which turns its +x end toward -z), and `n_cubes` dynamic cubes
+    resting `gap` above the plane in its sweep (radius 0.35, 0.5 + 0.5 i rad
+    ahead of the bar), positions jittered U[+-1e-3]: frictionless
+    kinematic-dynamic contact."""
+    rng = np.random.default_rng(seed)
+    meshes = [box_mesh(1.0, 0.1, 0.1), cube_mesh(size)]
+    body_mesh, kind, q0, om = [0], [KIND_KINEMATIC], [_q_at([0.0, 0.11, 0.0])], [[0.0, omega, 0.0]]
+    for i in range(n_cubes):
+        r, a = 0.35, 0.5 + 0.5 * i
+        c = np.array([r * math.cos(a), 0.5 * size + gap, -r * math.sin(a)])
+        c += rng.uniform(-1e-3, 1e-3, 3) * np.array([1.0, 0.0, 1.0])
+        body_mesh.append(1)
+        kind.append(KIND_DYNAMIC)
+        q0.append(_q_at(c))
+        om.append([0.0, 0.0, 0.0])
+    return _pack(meshes, body_mesh, density, kappa, np.array(kind, dtype=np.int32), q0, None,
+                 [(1, 1.0, 0.0)], name="kinematic_sweeper", omega=np.array(om))

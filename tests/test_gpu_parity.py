@@ -147,3 +147,27 @@ def test_sphere_pile_admm_mixed():
     e = rel(g.state()[0], o.state()[0])
     print("mixed rel err after 16 steps", e)
     assert e <= MIXED_TOL
+
+
+def test_kinematic_sweeper_fp64_parity():
+    """A kinematic bar (prescribed rotation) sweeping into cubes: FP64 path
+    within 1e-9 of the oracle every step, equal Newton counts, no penetration."""
+    sa = scenes.kinematic_sweeper()
+    worst, g, o = _run_pair(sa, 30, abd.default_params(), O.default_params(), FP64_TOL)
+    print("worst rel err", worst)
+
+
+def test_kinematic_sweeper_two_slabs_mixed():
+    """The sweeping bar straddles the slab plane (a shared kinematic body):
+    mixed path within 1e-4 of the oracle after 30 steps."""
+    sa = scenes.kinematic_sweeper()
+    g, o = abd.Scene(sa), O.Scene(sa)
+    g.partition(n_slabs=2, axis=0, planes=[0.0])
+    pg = abd.default_params(precision=abd.MIXED, pcg_rtol=1e-5)
+    for k in range(30):
+        st = g.step(pg)
+        o.step(O.default_params(n_slabs=2, axis=0, planes=[0.0]))
+        assert st["status"] >= 0 and st["min_distance"] > 0.0
+    e = rel(g.state()[0], o.state()[0])
+    print("mixed rel err after 30 steps", e)
+    assert e <= MIXED_TOL

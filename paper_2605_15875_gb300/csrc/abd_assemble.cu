@@ -189,8 +189,9 @@ __global__ void k_slot_assemble(AsmArgs A, T *__restrict__ diag) {
 
 template <class T> __device__ __forceinline__ void atomic_addT(T *a, T v) { atomicAdd(a, v); }
 
-// Per active pair: barrier gradient and projected Hessian scattered to slots.
-template <class T, bool full_path>
+// Per active pair: barrier gradient and projected Hessian scattered to slots;
+// mollified edge-edge pairs are deferred to k_pair_moll (full 12x12 projection).
+template <class T>
 __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int64_t n, const int2 *__restrict__ l1,
                                 T *__restrict__ diag, T *__restrict__ off, int *__restrict__ offflag,
                                 int64_t *__restrict__ deferred, unsigned long long *__restrict__ n_deferred,
@@ -199,9 +200,7 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
     for (int64_t ib = spread_base(); ib < n; ib += (int64_t)gridDim.x * blockDim.x) {
         int64_t ii = ib + (threadIdx.x & 31);
         if (ii >= n) continue;
-        // full_path: process the deferred (mollified edge-edge) pairs with the
-        // 12x12 projection; otherwise every active pair, deferring those
-        int64_t i = full_path ? deferred[ii] : ii;
+        const int64_t i = ii;
         PairRec r = act[i];
         int sa, sb;
         pair_slots(r, A.sv_slot, sa, sb);
@@ -217,7 +216,7 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
         double d = pair_gradient(ee, Xd, A.dhat, A.kB, r.eps, PG, gx);
         if (!(d < A.dhat) || !(d > 0.0)) continue;
         const bool moll = ee && PG.moll;
-        if (!full_path && moll) {
+        if (moll) {
             unsigned long long pos = atomicAdd(n_deferred, 1ull);
             deferred[pos] = i;  // capacity n: one slot per active pair
             continue;
@@ -245,7 +244,7 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
         // slot sides: PT = {point} | {triangle}, EE = {edge a} | {edge b}
         const int nA = ee ? 2 : 1;
         int ss[2] = {sa < A.S_dyn ? sa : -1, sb < A.S_dyn ? sb : -1};
-        if (!full_path) {
+        {
             // exact low-rank projection: PSD(H) = B PSD(K) B^T, J^T PSD(H) J = P_s K+ P_t^T
             T K[25], wh[4], chat[2][4], rh[3];
             int n = pair_hessian_lowrank<T>(ee, X, PG, T(d), T(A.kB), K, wh, chat, rh);
@@ -299,7 +298,6 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
                                 }
                         }
                 }
-            continue;
         }
     }
 }
@@ -820,7 +818,7 @@ static int assemble_async_T(abd_scene *s, const abd_step_params *p, double kB) {
     unsigned long long *ndef = (unsigned long long *)(defl + w.cap_act);
     cudaMemsetAsync(ndef, 0, 8, s->stream);
     prof_begin(s, "pair_assemble", 0.0, &ea, &eb);
-    ABD_LAUNCH(s, (k_pair_assemble<T, false>), grid_for(w.cap_act, 128, 152 * 8), 128, 0, s->stream, A,
+    ABD_LAUNCH(s, k_pair_assemble<T>, grid_for(w.cap_act, 128, 152 * 8), 128, 0, s->stream, A,
                P<PairRec>(w.act), w.cap_act, P<int2>(w.l1), P<T>(w.diag), P<T>(w.off), P<int>(w.offflag), defl, ndef,
                &c->act);
     prof_end(s, ea, eb, prof_index(s, "pair_assemble"));

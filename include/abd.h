@@ -97,6 +97,15 @@ typedef struct {
     const double *planes;          /* [n_slabs - 1] or NULL */
     double alpha;                  /* 2 in the paper */
     double w_min;
+    /* Control-based load balancing (Sec. 5.2):
+     * after every step each plane between slabs i and i+1 moves by
+     * -(pd_kp T + pd_kd (T - T_prev)) along the axis, T = (tau_i - tau_{i+1}) /
+     * (tau_i + tau_{i+1}) from the smoothed work tau of the two slabs, so the
+     * slower slab shrinks (abd_pd_update).  Work of a slab in a step = its Newton
+     * iterations x its slots (its partitions share every launch on this GPU,
+     * so they have no separate clocks).  Smoothing tau <- pd_smooth tau_prev +
+     * (1 - pd_smooth) tau_step.  pd_kp = pd_kd = 0: planes fixed (default). */
+    double pd_kp, pd_kd, pd_smooth;
 } abd_partition_desc;
 
 /* Step parameters.  Defaults: abd_step_params_default(). */
@@ -194,6 +203,18 @@ int abd_candidates(abd_scene *s, const double *x0, const double *x1, double dhat
  *   in abd_last_error().  Blocks until done. */
 int abd_candidates_noalloc(abd_scene *s, const double *x0, const double *x1, double dhat, int32_t *out, int64_t cap,
                            int64_t *n_out);
+
+/* Slab planes the next step will use (the explicit or load-balanced planes,
+ * else the equal-width planes of the last step): up to `cap` values into
+ * `planes`, the count (n_slabs - 1) in *n. */
+int abd_partition_planes(const abd_scene *s, double *planes, int32_t cap, int32_t *n);
+
+/* The load-balancing law alone (pure host function, no device work): for the
+ * n_slabs - 1 planes, T[i] = (tau[i] - tau[i+1]) / (tau[i] + tau[i+1]) (0 when
+ * both are 0) and delta[i] = -(kp T[i] + kd (T[i] - T_prev[i])), the plane
+ * shift along the axis.  T_prev may be NULL (zeros). */
+int abd_pd_update(int32_t n_slabs, const double *tau, const double *T_prev, double kp, double kd, double *delta,
+                  double *T);
 
 /* Membership of partition `part` as the last abd_step built it (Sec. 4: a
  * dynamic body belongs to every slab its w-inflated box meets).  `bodies`

@@ -33,7 +33,7 @@ class SceneDesc(C.Structure):
 
 class PartitionDesc(C.Structure):
     _fields_ = [("axis", C.c_int32), ("n_slabs", C.c_int32), ("planes", C.c_void_p), ("alpha", C.c_double),
-                ("w_min", C.c_double)]
+                ("w_min", C.c_double), ("pd_kp", C.c_double), ("pd_kd", C.c_double), ("pd_smooth", C.c_double)]
 
 
 class StepParams(C.Structure):
@@ -82,7 +82,7 @@ EXPORTS = ["abd_scene_create", "abd_scene_destroy", "abd_scene_counts", "abd_bod
            "abd_candidates", "abd_profile", "abd_kernel_stats", "abd_step_params_default", "abd_status_string",
            "abd_last_error", "abd_candidates_noalloc", "abd_partition_get", "abd_server_create",
            "abd_server_submit", "abd_server_poll", "abd_server_wait", "abd_server_result", "abd_server_latencies",
-           "abd_server_error", "abd_server_destroy"]
+           "abd_server_error", "abd_server_destroy", "abd_partition_planes", "abd_pd_update"]
 
 _lib = None
 
@@ -120,6 +120,8 @@ def load(path: Optional[str] = None):
     L.abd_last_error.restype = C.c_char_p
     i32p = C.POINTER(C.c_int32)
     L.abd_partition_get.argtypes = [vp, C.c_int32, vp, C.c_int32, i32p, vp, C.c_int32, i32p]
+    L.abd_partition_planes.argtypes = [vp, vp, C.c_int32, i32p]
+    L.abd_pd_update.argtypes = [C.c_int32, vp, vp, C.c_double, C.c_double, vp, vp]
     L.abd_server_create.argtypes = [C.POINTER(ServerDesc), C.POINTER(vp)]
     L.abd_server_submit.argtypes = [vp, C.POINTER(SceneDesc), vp, vp, C.c_int32, C.POINTER(i64)]
     L.abd_server_poll.argtypes = [vp, i64, C.POINTER(RequestInfo)]
@@ -215,8 +217,9 @@ class Scene:
                            f"{self.L.abd_last_error(self.h).decode()}")
         return rc
 
-    def partition(self, n_slabs=1, axis=0, planes=None, alpha=2.0, w_min=0.0):
-        d = PartitionDesc(axis=axis, n_slabs=n_slabs, planes=None, alpha=alpha, w_min=w_min)
+    def partition(self, n_slabs=1, axis=0, planes=None, alpha=2.0, w_min=0.0, pd_kp=0.0, pd_kd=0.0, pd_smooth=0.0):
+        d = PartitionDesc(axis=axis, n_slabs=n_slabs, planes=None, alpha=alpha, w_min=w_min, pd_kp=pd_kp,
+                          pd_kd=pd_kd, pd_smooth=pd_smooth)
         arr = None
         if planes is not None:
             arr = np.ascontiguousarray(planes, dtype=np.float64)
@@ -228,6 +231,12 @@ class Scene:
         w = C.c_double()
         self._check(self.L.abd_partition_masks(self.h, h, _p(m), C.byref(w)), "abd_partition_masks")
         return m, w.value
+
+    def partition_planes(self):
+        n = C.c_int32()
+        out = np.zeros(64)
+        self._check(self.L.abd_partition_planes(self.h, _p(out), 64, C.byref(n)), "abd_partition_planes")
+        return out[:n.value].copy()
 
     def partition_get(self, part):
         n, ns = C.c_int32(), C.c_int32()
@@ -361,3 +370,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def pd_update(tau, T_prev=None, kp=0.0, kd=0.0):
+    """The load-balancing law of abd_pd_update: (plane shifts, T)."""
+    tau = np.ascontiguousarray(tau, dtype=np.float64)
+    n = len(tau)
+    Tp = None if T_prev is None else np.ascontiguousarray(T_prev, dtype=np.float64)
+    delta, T = np.zeros(max(1, n - 1)), np.zeros(max(1, n - 1))
+    rc = load().abd_pd_update(n, _p(tau), _p(Tp), kp, kd, _p(delta), _p(T))
+    if rc != 0:
+        raise AbdError(f"abd_pd_update: {rc}")
+    return delta[:n - 1], T[:n - 1]

@@ -178,6 +178,10 @@ struct abd_scene {
     int axis = 0, n_slabs = 1;
     std::vector<double> slab_planes;
     double alpha_w = 2.0, w_min = 0.0;
+    // control-based load balancing (Sec. 5.2)
+    double pd_kp = 0.0, pd_kd = 0.0, pd_smooth = 0.0;
+    std::vector<double> pd_tau, pd_T;   // smoothed work and last imbalance per plane
+    std::vector<double> last_planes;    // planes the last step used
     // device
     abd::SceneDev dev;
     abd::World w;

@@ -453,6 +453,36 @@ extern "C" int abd_partition(abd_scene *s, const abd_partition_desc *d) {
         for (int i = 0; i + 1 < d->n_slabs; ++i) s->slab_planes.push_back(d->planes[i]);
     s->alpha_w = d->alpha;
     s->w_min = d->w_min;
+    s->pd_kp = d->pd_kp;
+    s->pd_kd = d->pd_kd;
+    s->pd_smooth = d->pd_smooth;
+    s->pd_tau.clear();
+    s->pd_T.clear();
+    s->last_planes.clear();
+    return ABD_OK;
+}
+
+extern "C" int abd_partition_planes(const abd_scene *s, double *planes, int32_t cap, int32_t *n) {
+    if (!s || !n || cap < 0) return ABD_E_INVALID;
+    const std::vector<double> &src = s->slab_planes.size() == (size_t)std::max(0, s->n_slabs - 1) && s->n_slabs > 1
+                                         ? s->slab_planes
+                                         : s->last_planes;
+    *n = (int32_t)src.size();
+    if (planes)
+        for (int i = 0; i < std::min((int)src.size(), (int)cap); ++i) planes[i] = src[i];
+    return ABD_OK;
+}
+
+extern "C" int abd_pd_update(int32_t n_slabs, const double *tau, const double *T_prev, double kp, double kd,
+                             double *delta, double *T) {
+    if (n_slabs < 1 || !tau || (n_slabs > 1 && (!delta || !T))) return ABD_E_INVALID;
+    for (int i = 0; i + 1 < n_slabs; ++i) {
+        // (eta - 1) / (eta + 1) with eta = tau_i / tau_{i+1}, written without the quotient
+        double sum = tau[i] + tau[i + 1];
+        T[i] = sum > 0.0 ? (tau[i] - tau[i + 1]) / sum : 0.0;
+        double tp = T_prev ? T_prev[i] : 0.0;
+        delta[i] = -(kp * T[i] + kd * (T[i] - tp));
+    }
     return ABD_OK;
 }
 

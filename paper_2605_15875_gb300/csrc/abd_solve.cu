@@ -313,6 +313,7 @@ struct Ctx {
     int precision;
     DBuf alphas, nh0, decided, pending;
     double t_coll = 0, t_solve = 0, t_sync = 0;
+    std::vector<int64_t> part_newton;  // Newton iterations per partition over the step
 };
 
 double u2d(unsigned long long u) {
@@ -372,6 +373,7 @@ int compute_masks(abd_scene *s, double h, const std::vector<double> &box, const 
     std::vector<double> gam(N + 1);
     for (int i = 1; i < N; ++i)
         gam[i] = s->slab_planes.size() == (size_t)(N - 1) ? s->slab_planes[i - 1] : Lo + (Hi - Lo) * (double)i / (double)N;
+    s->last_planes.assign(gam.begin() + 1, gam.begin() + N);
     if (s->w_min > 0.0) wmin = s->w_min;
     double w = std::max(s->alpha_w * vmax * h, wmin);
     for (int b = 0; b < s->nb; ++b) {
@@ -748,6 +750,8 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         C.t_solve += now_ms() - t0;
     }
     for (int i = 0; i < w.NP; ++i) newton_total += ps[i].newton_it;
+    if ((int)C.part_newton.size() < w.NP) C.part_newton.resize(w.NP, 0);
+    for (int i = 0; i < w.NP; ++i) C.part_newton[i] += ps[i].newton_it;
     if (any) maxed = 1;
     return ABD_OK;
 }
@@ -821,6 +825,31 @@ int final_min_distance(Ctx &C, double &out) {
         return ABD_OK;
     }
     return set_err(s, ABD_E_PAIR_OVERFLOW, "final check: lists keep overflowing");
+}
+
+// Control-based load balancing (Sec. 5.2) after a step on N slabs: work of
+// a slab = its Newton iterations x its slots, smoothed; every plane moves by
+// abd_pd_update's shift (the slower slab shrinks); planes stay ordered.
+void pd_balance(abd_scene *s, const Ctx &C, int N) {
+    World &w = s->w;
+    if (N < 2 || w.NP != N || (int)s->last_planes.size() != N - 1) return;
+    std::vector<double> tau(N);
+    for (int i = 0; i < N; ++i) {
+        double slots = (double)(w.h_part_off[i + 1] - w.h_part_off[i]);
+        double nit = i < (int)C.part_newton.size() ? (double)C.part_newton[i] : 0.0;
+        tau[i] = nit * slots;
+    }
+    if ((int)s->pd_tau.size() != N) s->pd_tau = tau;
+    else
+        for (int i = 0; i < N; ++i) s->pd_tau[i] = s->pd_smooth * s->pd_tau[i] + (1.0 - s->pd_smooth) * tau[i];
+    std::vector<double> delta(N - 1), T(N - 1);
+    abd_pd_update(N, s->pd_tau.data(), (int)s->pd_T.size() == N - 1 ? s->pd_T.data() : nullptr, s->pd_kp, s->pd_kd,
+                  delta.data(), T.data());
+    std::vector<double> planes = s->last_planes;
+    for (int i = 0; i < N - 1; ++i) planes[i] += delta[i];
+    for (int i = 1; i < N - 1; ++i) planes[i] = std::max(planes[i], planes[i - 1] + 1e-6);
+    s->slab_planes = planes;
+    s->pd_T = T;
 }
 
 int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool force_mono) {
@@ -950,6 +979,7 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
     st->t_coll_ms = C.t_coll; st->t_solve_ms = C.t_solve; st->t_sync_ms = C.t_sync;
     st->t_total_ms = now_ms() - T0;
     st->kernel_launches = s->n_launches - L0;
+    if (!force_mono && (s->pd_kp != 0.0 || s->pd_kd != 0.0)) pd_balance(s, C, N);
     return status;
 }
 

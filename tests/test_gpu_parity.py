@@ -171,3 +171,26 @@ def test_kinematic_sweeper_two_slabs_mixed():
     e = rel(g.state()[0], o.state()[0])
     print("mixed rel err after 30 steps", e)
     assert e <= MIXED_TOL
+
+
+def test_load_balanced_planes_fp64_parity():
+    """PD load balancing on two slabs starting from an uneven plane: every step
+    the CUDA scene moves the plane toward balance; handing the oracle the same
+    plane each step keeps FP64 per-step parity."""
+    sa = scenes.cube_stack(nx=4, ny=2, nz=1)
+    g, o = abd.Scene(sa), O.Scene(sa)
+    g.partition(n_slabs=2, axis=0, planes=[-1.0], pd_kp=0.1, pd_kd=0.02, pd_smooth=0.5)
+    planes = []
+    for k in range(12):
+        pl = g.partition_planes()
+        planes.append(float(pl[0]))
+        qo, vo = o.state()
+        g.set_state(qo, vo)
+        sg = g.step(abd.default_params())
+        so = o.step(O.default_params(n_slabs=2, axis=0, planes=[float(pl[0])]))
+        e = rel(g.state()[0], o.state()[0])
+        assert e <= FP64_TOL, (k, e)
+        assert (sg["admm_iters"], sg["newton_iters"]) == (so["admm_iters"], so["newton_iters"])
+    print("planes", planes)
+    # slab 0 starts with one column of cubes, slab 1 with three: the plane moves up
+    assert planes[-1] > planes[0] + 0.05

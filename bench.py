@@ -202,7 +202,10 @@ def run_ours(args, rank, world):
             "frac": round(achieved / peak, 4), "traffic": TRAFFIC.get(dom), "peak_source": peak_kind,
             "launches": n_l, "avg_launch_us": round(1e3 * ms_l / max(1, n_l), 3),
             "share_of_step": round(ms_l / total_ms, 4) if total_ms else None,
-            "kernels_ms": {n: round(v[1], 3) for n, v in ks.items()}}
+            "kernels_ms": {n: round(v[1], 3) for n, v in ks.items()},
+            # every instrumented kernel: compulsory bytes over its live CUDA-event time
+            "kernels_gbs": {n: (round(v[2] / (v[1] / 1e3) / 1e9, 2) if v[1] > 0 and v[2] > 0 else None)
+                            for n, v in ks.items()}}
     fp64 = None
     if not args.no_fp64:
         sc64, p64 = make(abd.FP64)

@@ -353,3 +353,112 @@ def kinematic_sweeper(seed: int = 0, n_cubes: int = 3, omega: float = 2.0, size:
         om.append([0.0, 0.0, 0.0])
     return _pack(meshes, body_mesh, density, kappa, np.array(kind, dtype=np.int32), q0, None,
                  [(1, 1.0, 0.0)], name="kinematic_sweeper", omega=np.array(om))
+
+
+def perforated_disk_mesh(radius: float = 1.4, thickness: float = 0.05, cell: float = 0.07,
+                         hole_radius: float = 0.09, rings: int = 3) -> Mesh:
+    """Closed perforated turntable: the square cells of side `cell` whose
+    centres lie inside the disk and outside every hole, extruded to
+    `thickness` (centred on y = 0), as one watertight outward mesh (caps of
+    every kept cell, walls wherever a kept cell meets a dropped one).  Holes:
+    1 + 6 + 12 + ... centres of a hexagonal pattern with `rings` rings (37 for
+    3 rings) spaced to fill the disk.  Volume = kept cells x cell^2 x thickness."""
+    n = int(math.ceil(radius / cell))
+    pitch = (radius - hole_radius) / (rings + 0.5)
+    holes = [(0.0, 0.0)]
+    for r in range(1, rings + 1):
+        for k in range(6):
+            a0, a1 = math.pi / 3 * k, math.pi / 3 * (k + 1)
+            p0 = np.array([math.cos(a0), math.sin(a0)]) * r * pitch
+            p1 = np.array([math.cos(a1), math.sin(a1)]) * r * pitch
+            for j in range(r):
+                holes.append(tuple(p0 + (p1 - p0) * j / r))
+    holes = np.array(holes)
+
+    def kept(i, j):
+        if not (-n <= i < n and -n <= j < n):
+            return False
+        cx, cz = (i + 0.5) * cell, (j + 0.5) * cell
+        if cx * cx + cz * cz > radius * radius:
+            return False
+        return bool(np.min((holes[:, 0] - cx) ** 2 + (holes[:, 1] - cz) ** 2) > hole_radius ** 2)
+
+    keep = {(i, j) for i in range(-n, n) for j in range(-n, n) if kept(i, j)}
+    vid, verts, tris = {}, [], []
+    h = 0.5 * thickness
+
+    def v(i, j, top):
+        key = (i, j, top)
+        if key not in vid:
+            vid[key] = len(verts)
+            verts.append((i * cell, h if top else -h, j * cell))
+        return vid[key]
+
+    def quad(a, b, c, d, normal):
+        for t in ((a, b, c), (a, c, d)):
+            p = [np.array(verts[x]) for x in t]
+            if np.dot(np.cross(p[1] - p[0], p[2] - p[0]), normal) < 0:
+                t = (t[0], t[2], t[1])
+            tris.append(t)
+
+    for (i, j) in sorted(keep):
+        quad(v(i, j, 1), v(i + 1, j, 1), v(i + 1, j + 1, 1), v(i, j + 1, 1), (0, 1, 0))
+        quad(v(i, j, 0), v(i + 1, j, 0), v(i + 1, j + 1, 0), v(i, j + 1, 0), (0, -1, 0))
+        if (i - 1, j) not in keep:
+            quad(v(i, j, 0), v(i, j + 1, 0), v(i, j + 1, 1), v(i, j, 1), (-1, 0, 0))
+        if (i + 1, j) not in keep:
+            quad(v(i + 1, j, 0), v(i + 1, j + 1, 0), v(i + 1, j + 1, 1), v(i + 1, j, 1), (1, 0, 0))
+        if (i, j - 1) not in keep:
+            quad(v(i, j, 0), v(i + 1, j, 0), v(i + 1, j, 1), v(i, j, 1), (0, 0, -1))
+        if (i, j + 1) not in keep:
+            quad(v(i, j + 1, 0), v(i + 1, j + 1, 0), v(i + 1, j + 1, 1), v(i, j + 1, 1), (0, 0, 1))
+    m = Mesh(np.array(verts, dtype=np.float64), np.array(tris, dtype=np.int32))
+    m.n_cells = len(keep)  # kept cells, for the volume closed form
+    return m
+
+
+def funnel_mesh(top_radius: float = 1.5, neck_radius: float = 0.35, top_y: float = 3.4, neck_y: float = 2.2,
+                segments: int = 48) -> Mesh:
+    """Static open funnel: the lateral surface of a truncated cone from the
+    neck ring (neck_y, neck_radius) to the top ring (top_y, top_radius)."""
+    verts, tris = [], []
+    for k in range(segments):
+        a = 2.0 * math.pi * k / segments
+        verts.append((neck_radius * math.cos(a), neck_y, neck_radius * math.sin(a)))
+        verts.append((top_radius * math.cos(a), top_y, top_radius * math.sin(a)))
+    for k in range(segments):
+        a0, a1, b0, b1 = 2 * k, 2 * ((k + 1) % segments), 2 * k + 1, 2 * ((k + 1) % segments) + 1
+        tris.append((a0, a1, b1))
+        tris.append((a0, b1, b0))
+    return Mesh(np.array(verts, dtype=np.float64), np.array(tris, dtype=np.int32))
+
+
+def funnel_scene(seed: int = 0, n_bodies: int = 5000, level: int = 3, radius: float = 0.05,
+                 omega: float = 1.0, density: float = 1000.0, kappa: float = 1e8) -> SceneArrays:
+    """Funnel-and-turntables workload: `n_bodies` noisy icospheres (radial
+    factor U[0.9, 1.1]) on a jittered lattice inside radius 1.25 above a
+    static open funnel (top radius 1.5 at y = 3.4, neck radius 0.35 at
+    y = 2.2, 48 segments), falling into a static open chamber 3 x 2 x 3 with
+    two kinematic perforated turntables (radius 1.4, 37 holes) at y = 0.6 and
+    y = 1.3 turning at +omega and -omega about the vertical axis."""
+    rng = np.random.default_rng(seed)
+    meshes = [open_box_mesh(3.0, 2.0, 3.0), funnel_mesh(), perforated_disk_mesh()]
+    body_mesh = [0, 1, 2, 2]
+    kind = [KIND_STATIC, KIND_STATIC, KIND_KINEMATIC, KIND_KINEMATIC]
+    q0 = [_q_at([0.0, 0.0, 0.0]), _q_at([0.0, 0.0, 0.0]), _q_at([0.0, 0.6, 0.0]), _q_at([0.0, 1.3, 0.0])]
+    om = [[0.0, 0.0, 0.0], [0.0, 0.0, 0.0], [0.0, omega, 0.0], [0.0, -omega, 0.0]]
+    pitch = 2.0 * radius * 1.1 * 1.15
+    per_layer = [(ix, iz) for ix in range(-12, 13) for iz in range(-12, 13)
+                 if (ix * pitch) ** 2 + (iz * pitch) ** 2 <= 1.25 ** 2]
+    for k in range(n_bodies):
+        ix, iz = per_layer[k % len(per_layer)]
+        layer = k // len(per_layer)
+        c = np.array([ix * pitch, 3.5 + radius * 1.2 + layer * pitch, iz * pitch])
+        c += rng.uniform(-0.05, 0.05, 3) * radius
+        meshes.append(noisy_icosphere(rng, level, radius))
+        body_mesh.append(len(meshes) - 1)
+        kind.append(KIND_DYNAMIC)
+        q0.append(_q_at(c))
+        om.append([0.0, 0.0, 0.0])
+    return _pack(meshes, body_mesh, density, kappa, np.array(kind, dtype=np.int32), q0, None, [],
+                 name=f"funnel_{n_bodies}", omega=np.array(om))

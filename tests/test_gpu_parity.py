@@ -194,3 +194,12 @@ def test_load_balanced_planes_fp64_parity():
     print("planes", planes)
     # slab 0 starts with one column of cubes, slab 1 with three: the plane moves up
     assert planes[-1] > planes[0] + 0.05
+
+
+def test_funnel_crop_fp64_parity():
+    """A crop of the funnel workload (static funnel and chamber, two kinematic
+    perforated turntables, a few spheres), two slabs: FP64 per-step parity."""
+    sa = scenes.funnel_scene(n_bodies=8, level=1)
+    worst, g, o = _run_pair(sa, 4, abd.default_params(), O.default_params(n_slabs=2, axis=0, planes=[0.0]),
+                            FP64_TOL, partition=dict(n_slabs=2, axis=0, planes=[0.0]))
+    print("worst rel err", worst)

@@ -517,3 +517,34 @@ def test_kinematic_sweeper_pushes_without_penetration():
     assert np.abs(A - _rot_y(2.0 * p.h * n) @ q0[0, 3:].reshape(3, 3)).max() < 1e-6
     # and it pushed the first cube
     assert np.linalg.norm(q[1, :3] - q0[1, :3]) > 0.05
+
+
+def test_perforated_turntable_mesh_closed_form_volume():
+    """The perforated turntable is a watertight outward mesh whose volume is
+    kept cells x cell^2 x thickness (divergence theorem in the oracle's mass
+    properties), and the oracle weights its inertia as a kinematic body."""
+    m = scenes.perforated_disk_mesh()
+    sa = scenes.funnel_scene(n_bodies=1, level=1)
+    o = O.Scene(sa)
+    mass, com, S, V = o.body_props(2)
+    assert abs(V - m.n_cells * 0.07 ** 2 * 0.05) < 1e-12
+    assert abs(mass - 1000.0 * V * 1e6) < 1e-6 * mass
+    assert np.abs(com).max() < 1e-12  # symmetric hole pattern
+
+
+def test_funnel_crop_turntables_and_free_fall():
+    """A crop of the funnel workload: the two turntables turn by +-omega h per
+    step and the spheres, not yet in contact, fall as the closed form says."""
+    sa = scenes.funnel_scene(n_bodies=8, level=1)
+    o = O.Scene(sa)
+    p = O.default_params()
+    q0, _ = o.state()
+    n = 4
+    for _ in range(n):
+        o.step(p)
+    q, _ = o.state()
+    for b, sgn in ((2, 1.0), (3, -1.0)):
+        R = _rot_y(sgn * 1.0 * p.h * n)
+        assert np.abs(q[b, 3:].reshape(3, 3) - R @ q0[b, 3:].reshape(3, 3)).max() < 1e-6
+    g = -9.8 * p.h ** 2 * n * (n + 1) / 2
+    assert np.abs(q[4:, 1] - q0[4:, 1] - g).max() < 1e-12

@@ -63,3 +63,22 @@ def test_ctypes_struct_layouts_match_the_header(tmp_path):
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     mirrors = [abd.SceneDesc, abd.PartitionDesc, abd.StepParams, abd.StepStats, abd.ServerDesc, abd.RequestInfo]
     assert got == [ctypes.sizeof(m) for m in mirrors]
+
+
+def test_server_and_partition_calls_reject_bad_arguments():
+    """Argument checks of the serving and partition calls happen before any
+    device work, so they answer on a machine without a GPU."""
+    import ctypes
+    from paper_2605_15875_gb300 import abd, build
+    build.build()
+    L = abd.load()
+    h = ctypes.c_void_p()
+    bad = abd.ServerDesc(device=0, n_streams=0, hbm_budget_bytes=0)
+    assert L.abd_server_create(ctypes.byref(bad), ctypes.byref(h)) == -1
+    bad = abd.ServerDesc(device=0, n_streams=2, hbm_budget_bytes=-5)
+    assert L.abd_server_create(ctypes.byref(bad), ctypes.byref(h)) == -1
+    t = ctypes.c_int64()
+    assert L.abd_server_submit(None, None, None, None, 1, ctypes.byref(t)) == -1
+    n = ctypes.c_int32()
+    assert L.abd_partition_planes(None, None, 0, ctypes.byref(n)) == -1
+    assert L.abd_pd_update(0, None, None, 0.0, 0.0, None, None) == -1

@@ -548,3 +548,21 @@ def test_funnel_crop_turntables_and_free_fall():
         assert np.abs(q[b, 3:].reshape(3, 3) - R @ q0[b, 3:].reshape(3, 3)).max() < 1e-6
     g = -9.8 * p.h ** 2 * n * (n + 1) / 2
     assert np.abs(q[4:, 1] - q0[4:, 1] - g).max() < 1e-12
+
+
+def test_kinematic_sweeper_two_slabs_invariants():
+    """The sweeping bar straddles the slab plane (replicated on both slabs):
+    consensus keeps it on its prescription and every step stays apart."""
+    sa = scenes.kinematic_sweeper()
+    o = O.Scene(sa)
+    p = O.default_params(n_slabs=2, axis=0, planes=[0.0])
+    q0, _ = o.state()
+    n = 30
+    shared = 0
+    for _ in range(n):
+        st = o.step(p)
+        assert st["min_distance"] > 0.0 and st["status"] >= 0
+        shared = max(shared, st["n_shared"])
+    q, _ = o.state()
+    assert shared >= 1
+    assert np.abs(q[0, 3:].reshape(3, 3) - _rot_y(2.0 * p.h * n) @ q0[0, 3:].reshape(3, 3)).max() < 1e-6

@@ -50,6 +50,7 @@ enum {
     ABD_ADMM_MAXITER = 1,       /* K ADMM rounds without convergence; merge check passed, z accepted */
     ABD_NEWTON_MAXITER = 2,     /* some local solve hit max_newton */
     ABD_FELL_BACK_MONOLITHIC = 3, /* K rounds and the merge check failed: step re-solved on one partition */
+    ABD_DT_SPLIT = 4,           /* a blocked merge was retaken as two steps of h/2 (dt_split_max > 0) */
     ABD_E_INVALID = -1,
     ABD_E_OOM = -2,
     ABD_E_CUDA = -3,
@@ -122,6 +123,10 @@ typedef struct {
     double pcg_rtol;               /* relative residual of the block-Jacobi PCG */
     int32_t pcg_max;
     double accd_s, accd_c;         /* additive CCD gap fraction and step factor */
+    int32_t dt_split_max;          /* adaptive time stepping (Sec. 4.2, Fig. 4): when the merge check
+                                      blocks after K rounds, retake the step from the same state as two
+                                      steps of h/2, recursively up to this depth, before the one-partition
+                                      fallback; 0 (default) disables it */
 } abd_step_params;
 
 typedef struct {

@@ -48,7 +48,8 @@ class Params(C.Structure):
                 ("theta", C.c_double), ("newton_tol", C.c_double), ("max_admm", C.c_int32),
                 ("max_newton", C.c_int32), ("max_halvings", C.c_int32), ("accd_s", C.c_double),
                 ("accd_c", C.c_double), ("n_slabs", C.c_int32), ("axis", C.c_int32),
-                ("planes", C.c_void_p), ("alpha_w", C.c_double), ("w_min", C.c_double)]
+                ("planes", C.c_void_p), ("alpha_w", C.c_double), ("w_min", C.c_double),
+                ("dt_split_max", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -185,7 +186,7 @@ def default_params(**kw) -> Params:
     p = Params(h=1e-2, dhat=1e-3, kappa_barrier=0.0, rho_adaptive=1, beta=1.0, tau=2.0, mu=5.0,
                sigma_min=1e-3, sigma_max=1e3, theta=1e-3, newton_tol=1e-6, max_admm=200,
                max_newton=100, max_halvings=40, accd_s=0.1, accd_c=0.9, n_slabs=1, axis=0,
-               planes=None, alpha_w=2.0, w_min=0.0)
+               planes=None, alpha_w=2.0, w_min=0.0, dt_split_max=0)
     planes = kw.pop("planes", None)
     for k, v in kw.items():
         setattr(p, k, v)

@@ -1562,7 +1562,9 @@ static double scene_min_distance(orc_scene *s, double dhat) {
  *   local solves (Eq. 5).  Without shared bodies each partition solves once.
  *   After K rounds: accept z when the merge check passes (ADMM_MAXITER), else
  *   re-solve the step on one partition (FELL_BACK). */
-int orc_step(orc_scene *s, const orc_params *P, orc_stats *st) {
+#define ORC_SPLIT_REQUEST 100 /* internal: the step is to be retaken as two half steps */
+
+static int step_once(orc_scene *s, const orc_params *P, orc_stats *st) {
     int nb = s->nb, rc = ORC_OK;
     orc_stats zero;
     memset(&zero, 0, sizeof zero);
@@ -1736,6 +1738,20 @@ int orc_step(orc_scene *s, const orc_params *P, orc_stats *st) {
         if (parts[i].cand_peak > cpk) cpk = parts[i].cand_peak;
         if (parts[i].act_peak > apk) apk = parts[i].act_peak;
     }
+    if (status == ORC_FELL_BACK && P->dt_split_max > 0) {
+        /* adaptive time stepping on a blocked merge (reading of Sec. 4.2, Fig. 4:
+         * a smaller step lets the replicas merge): leave the state untouched and
+         * let orc_step retake the step as two steps of h/2 */
+        if (st) {
+            st->status = status; st->admm_iters = admm; st->n_shared = nshared; st->n_slots = nslots;
+            st->merge_ok = merge_ok; st->l = l; st->kappa_barrier = kB; st->w = w;
+            int nt = 0;
+            for (int i = 0; i < N; ++i) nt += parts[i].newton_iters;
+            st->newton_iters = nt;
+        }
+        rc = ORC_SPLIT_REQUEST;
+        goto out;
+    }
     if (status == ORC_FELL_BACK) {
         local_t M;
         rc = local_init(&M, s, ones, 0, qt, qtil, P, kB, l);
@@ -1764,6 +1780,32 @@ out:
     free(parts); free(qprev);
     free(qt); free(qtil); free(qnew); free(z); free(zprev); free(rho0); free(rhob); free(sbody); free(mask); free(ones);
     return rc;
+}
+
+int orc_step(orc_scene *s, const orc_params *P, orc_stats *st) {
+    orc_stats first;
+    int rc = step_once(s, P, &first);
+    if (rc != ORC_SPLIT_REQUEST) {
+        if (st) *st = first;
+        return rc;
+    }
+    orc_params H = *P;
+    H.h = 0.5 * P->h;
+    H.dt_split_max = P->dt_split_max - 1;
+    orc_stats a, b;
+    rc = orc_step(s, &H, &a);
+    if (rc < 0) return rc;
+    rc = orc_step(s, &H, &b);
+    if (rc < 0) return rc;
+    if (st) {
+        *st = b;
+        st->status = ORC_DT_SPLIT;
+        st->admm_iters = first.admm_iters + a.admm_iters + b.admm_iters;
+        st->newton_iters = first.newton_iters + a.newton_iters + b.newton_iters;
+        if (a.n_candidates_peak > st->n_candidates_peak) st->n_candidates_peak = a.n_candidates_peak;
+        if (a.n_active_peak > st->n_active_peak) st->n_active_peak = a.n_active_peak;
+    }
+    return ORC_DT_SPLIT;
 }
 
 /* Monolithic objective of Eq. 1 (one partition, kappa = 1, no consensus term)

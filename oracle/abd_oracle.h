@@ -31,7 +31,7 @@ extern "C" {
 #endif
 
 enum { ORC_DYNAMIC = 0, ORC_STATIC = 1, ORC_KINEMATIC = 2 };
-enum { ORC_OK = 0, ORC_ADMM_MAXITER = 1, ORC_FELL_BACK = 3,
+enum { ORC_OK = 0, ORC_ADMM_MAXITER = 1, ORC_FELL_BACK = 3, ORC_DT_SPLIT = 4,
        ORC_E_INVALID = -1, ORC_E_OOM = -2, ORC_E_NOT_SPD = -3, ORC_E_PENETRATION = -6 };
 
 typedef struct {
@@ -63,6 +63,7 @@ typedef struct {
     int32_t n_slabs, axis;
     const double *planes;            /* n_slabs-1 offsets, or NULL: equal widths over the dynamic AABB */
     double alpha_w, w_min;           /* w = max(alpha_w v_max h, w_min); w_min <= 0: smallest body AABB diagonal */
+    int32_t dt_split_max;            /* blocked merge: retake the step as two h/2 steps, this deep (0: off) */
 } orc_params;
 
 typedef struct {

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libabd.so")
 DYNAMIC, STATIC, KINEMATIC = 0, 1, 2
 FP64, MIXED = 0, 1
 RHO_FIXED, RHO_ADAPTIVE = 0, 1
-OK, ADMM_MAXITER, NEWTON_MAXITER, FELL_BACK_MONOLITHIC = 0, 1, 2, 3
+OK, ADMM_MAXITER, NEWTON_MAXITER, FELL_BACK_MONOLITHIC, DT_SPLIT = 0, 1, 2, 3, 4
 
 
 class SceneDesc(C.Structure):
@@ -42,7 +42,7 @@ class StepParams(C.Structure):
                 ("mu", C.c_double), ("sigma_min", C.c_double), ("sigma_max", C.c_double), ("theta", C.c_double),
                 ("newton_tol", C.c_double), ("max_admm", C.c_int32), ("max_newton", C.c_int32),
                 ("max_halvings", C.c_int32), ("pcg_rtol", C.c_double), ("pcg_max", C.c_int32),
-                ("accd_s", C.c_double), ("accd_c", C.c_double)]
+                ("accd_s", C.c_double), ("accd_c", C.c_double), ("dt_split_max", C.c_int32)]
 
 
 class StepStats(C.Structure):

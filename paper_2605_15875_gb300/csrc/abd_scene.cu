@@ -543,6 +543,7 @@ extern "C" abd_step_params abd_step_params_default(void) {
     p.max_admm = 200; p.max_newton = 100; p.max_halvings = 40;
     p.pcg_rtol = 1e-12; p.pcg_max = 5000;
     p.accd_s = 0.1; p.accd_c = 0.9;
+    p.dt_split_max = 0;
     return p;
 }
 
@@ -552,6 +553,7 @@ extern "C" const char *abd_status_string(int c) {
         case ABD_ADMM_MAXITER: return "ADMM reached max_admm; merge check passed";
         case ABD_NEWTON_MAXITER: return "a local solve reached max_newton";
         case ABD_FELL_BACK_MONOLITHIC: return "ADMM did not converge; step re-solved on one partition";
+        case ABD_DT_SPLIT: return "merge blocked; step taken as two half steps";
         case ABD_E_INVALID: return "invalid argument";
         case ABD_E_OOM: return "out of device memory";
         case ABD_E_CUDA: return "CUDA error";

@@ -951,6 +951,28 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
         }
         if (!converged) status = merge_ok ? ABD_ADMM_MAXITER : ABD_FELL_BACK_MONOLITHIC;
     }
+    if (status == ABD_FELL_BACK_MONOLITHIC && p->dt_split_max > 0) {
+        // adaptive time stepping on a blocked merge (reading of Sec. 4.2,
+        // Fig. 4: a smaller step lets the replicas merge): the body state is
+        // still that of the step start, so retake it as two steps of h/2
+        abd_step_params hp = *p;
+        hp.h = 0.5 * p->h;
+        hp.dt_split_max = p->dt_split_max - 1;
+        abd_step_stats a, b;
+        memset(&a, 0, sizeof a);
+        memset(&b, 0, sizeof b);
+        if ((rc = step_impl(s, &hp, &a, false)) < 0) return rc;
+        if ((rc = step_impl(s, &hp, &b, false)) < 0) return rc;
+        *st = b;
+        st->status = ABD_DT_SPLIT;
+        st->admm_iters = admm + a.admm_iters + b.admm_iters;
+        st->newton_iters = newton + a.newton_iters + b.newton_iters;
+        st->pcg_iters += a.pcg_iters;
+        st->n_candidates_peak = std::max(st->n_candidates_peak, a.n_candidates_peak);
+        st->n_active_peak = std::max(st->n_active_peak, a.n_active_peak);
+        st->kernel_launches = s->n_launches - L0;
+        return ABD_DT_SPLIT;
+    }
     if (status == ABD_FELL_BACK_MONOLITHIC) {
         abd_step_stats st2;
         memset(&st2, 0, sizeof st2);

@@ -203,3 +203,23 @@ def test_funnel_crop_fp64_parity():
     worst, g, o = _run_pair(sa, 4, abd.default_params(), O.default_params(n_slabs=2, axis=0, planes=[0.0]),
                             FP64_TOL, partition=dict(n_slabs=2, axis=0, planes=[0.0]))
     print("worst rel err", worst)
+
+
+def test_blocked_merges_split_fp64_parity():
+    """One ADMM round allowed on a contact-rich two-slab pile with adaptive time
+    stepping: blocked merges are retaken as two half steps, on the GPU as in the
+    oracle (same statuses and counts, FP64 per-step parity)."""
+    sa = _sphere_admm_scene()
+    g, o = abd.Scene(sa), O.Scene(sa)
+    g.partition(n_slabs=2, axis=0)
+    splits = 0
+    for k in range(26):
+        qo, vo = o.state()
+        g.set_state(qo, vo)
+        sg = g.step(abd.default_params(max_admm=1, dt_split_max=1))
+        so = o.step(O.default_params(max_admm=1, dt_split_max=1, n_slabs=2, axis=0))
+        assert rel(g.state()[0], o.state()[0]) <= FP64_TOL, k
+        assert (sg["status"], sg["admm_iters"], sg["newton_iters"]) == (so["status"], so["admm_iters"],
+                                                                       so["newton_iters"]), (k, sg, so)
+        splits += sg["status"] == abd.DT_SPLIT
+    assert splits >= 1

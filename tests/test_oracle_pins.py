@@ -566,3 +566,31 @@ def test_kinematic_sweeper_two_slabs_invariants():
     q, _ = o.state()
     assert shared >= 1
     assert np.abs(q[0, 3:].reshape(3, 3) - _rot_y(2.0 * p.h * n) @ q0[0, 3:].reshape(3, 3)).max() < 1e-6
+
+
+def test_blocked_merge_retaken_as_two_half_steps():
+    """With one ADMM round allowed, some steps of a contact-rich two-slab pile
+    end with a blocked merge (fallback); with dt_split_max = 1 those steps are
+    taken as two steps of h/2 instead, each penetration-free, and the result
+    equals stepping twice with h/2 from the same state."""
+    sa = scenes.sphere_grid_in_box(n=4, ny=2, nz=2, level=1, lowest=0.12, spacing=0.25)
+    base = dict(max_admm=1, n_slabs=2, axis=0)
+    o0, o1 = O.Scene(sa), O.Scene(sa)
+    split_steps = []
+    for k in range(24):
+        q, v = o1.state()
+        s0 = o0.step(O.default_params(**base))
+        s1 = o1.step(O.default_params(dt_split_max=1, **base))
+        if s0["status"] == 3:
+            assert s1["status"] == 4 and s1["min_distance"] > 0.0
+            split_steps.append(k)
+            # the same step by hand: two steps of h/2 from the same state
+            o2 = O.Scene(sa)
+            o2.set_state(q, v)
+            half = O.default_params(**base)
+            half.h = 0.5 * half.h
+            o2.step(half)
+            o2.step(half)
+            assert np.array_equal(o2.state()[0], o1.state()[0])
+        o0.set_state(*o1.state())
+    assert split_steps, "no blocked merge in the window"

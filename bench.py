@@ -355,7 +355,7 @@ def run_reference(args, rank, world):
             break
     n = len(lat)
     value = sa.n_dynamic * n / (sum(lat) / 1e3)
-    sample = (f"steps {args.warmup}..{args.warmup + n} of the same scene on one host core"
+    sample = (f"steps {args.warmup}..{args.warmup + n - 1} of the same scene on one host core"
               + ("" if n == args.steps else f" (stopped after {budget:.0f} s)"))
     return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "body-steps/s",
             "n_gpus": world, "steps": n, "warmup": args.warmup, "ms_per_step": round(sum(lat) / n, 3),

@@ -9,7 +9,13 @@ same q^t (the paper's q* comparison); with --trajectory both run freely and
 the error is taken after the last step (dominated by the pile's chaotic
 divergence).
 
+With --hetero it runs the material-heterogeneity comparison instead (Sec. 6.2,
+Table 2): the 200-body pile with three (mass, stiffness) groups against its
+uniform baseline, on two slabs and on one partition, FP64, reporting the mean
+ADMM rounds and Newton iterations per step.
+
   python -m paper_2605_15875_gb300.experiments [--steps 30] [--quick] [--trajectory]
+  python -m paper_2605_15875_gb300.experiments --hetero [--steps 40]
 
 Prints one JSON object per configuration and a summary line."""
 from __future__ import annotations
@@ -64,17 +70,39 @@ def run_per_step(sa, steps, params, ref_params):
     return float(np.mean(mse)), float(np.mean(admm)), float(np.mean(newton)), worst
 
 
+def hetero_table(steps):
+    """Table 2's four cases: {two slabs, one partition} x {heterogeneous, uniform}."""
+    from . import abd, scenes
+    rows = []
+    for hetero in (True, False):
+        sa = scenes.heterogeneous_pile(hetero=hetero)
+        for n_slabs in (2, 1):
+            _, admm, newton, worst = run(sa, steps, abd.default_params(precision=abd.FP64), n_slabs)
+            row = {"case": f"{n_slabs}W, {'hetero.' if hetero else 'uniform'}", "bodies": sa.n_dynamic,
+                   "steps": steps, "admm_iters_mean": round(admm, 2) if n_slabs > 1 else None,
+                   "newton_iters_mean": round(newton, 2), "worst_status": worst}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--quick", action="store_true", help="three betas, two densities")
     ap.add_argument("--trajectory", action="store_true", help="free runs, error after the last step")
+    ap.add_argument("--hetero", action="store_true", help="material-heterogeneity comparison (Table 2)")
     a = ap.parse_args()
     import torch
     from . import abd, build
     build.build()
     abd.load()
     torch.cuda.set_device(0)
+    if a.hetero:
+        t0 = time.perf_counter()
+        hetero_table(a.steps)
+        print(json.dumps({"wall_s": round(time.perf_counter() - t0, 1)}))
+        return
     betas = [0.1, 1.0, 10.0] if a.quick else [0.01, 0.1, 1.0, 10.0, 100.0]
     densities = [100.0, 10000.0] if a.quick else [10.0, 100.0, 1000.0, 10000.0, 100000.0]
     rows = []

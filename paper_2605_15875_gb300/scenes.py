@@ -268,6 +268,50 @@ def sphere_grid_in_box(seed: int = 0, n: int = 8, level: int = 2, radius: float 
                  name=f"sphere_grid_{n}x{ny}x{nz}_L{level}")
 
 
+def mesh_volume(m: Mesh) -> float:
+    """Enclosed volume of a closed, outward-oriented triangle mesh (sum of
+    signed tetrahedra against the origin)."""
+    a, b, c = (m.xbar[m.tris[:, k]] for k in range(3))
+    return float(np.einsum("ij,ij->i", a, np.cross(b, c)).sum() / 6.0)
+
+
+# (mass, orthogonality stiffness) of the three groups of the heterogeneity
+# experiment (Sec. 6.2, Table 2), and of its uniform baseline
+HETERO_GROUPS = ((1.0, 1e8), (100.0, 1e10), (1e4, 1e12))
+UNIFORM_GROUP = (100.0, 1e10)
+
+
+def heterogeneous_pile(seed: int = 0, nx: int = 5, ny: int = 8, nz: int = 5, hetero: bool = True,
+                       level: int = 1, radius: float = 0.1, spacing: float = 0.25, lowest: float = 0.15,
+                       box=(2.4, 3.0, 2.4)) -> SceneArrays:
+    """Material-heterogeneity workload (Sec. 6.2, Table 2): nx*ny*nz noisy
+    icospheres (200 by default) on a grid in a static open box, split into
+    three groups by a seeded shuffle, group g having body mass m_g and
+    orthogonality stiffness kappa_g = E_g from HETERO_GROUPS; with
+    hetero=False every body takes UNIFORM_GROUP.  Each body's density is
+    m_g / (its own mesh volume), so its mass is m_g exactly."""
+    rng = np.random.default_rng(seed)
+    B = nx * ny * nz
+    meshes, q0 = [], []
+    for ix in range(nx):
+        for iy in range(ny):
+            for iz in range(nz):
+                meshes.append(noisy_icosphere(rng, level, radius))
+                q0.append(_q_at([(ix - (nx - 1) / 2) * spacing, lowest + iy * spacing,
+                                 (iz - (nz - 1) / 2) * spacing]))
+    group = np.empty(B, dtype=np.int32)
+    group[rng.permutation(B)] = np.arange(B) % 3
+    mk = np.array([HETERO_GROUPS[g] if hetero else UNIFORM_GROUP for g in group])
+    density = mk[:, 0] / np.array([mesh_volume(m) for m in meshes])
+    meshes.append(open_box_mesh(*box))
+    q0.append(IDENTITY_Q.copy())
+    kind = [KIND_DYNAMIC] * B + [KIND_STATIC]
+    sa = _pack(meshes, list(range(B)) + [B], np.append(density, 1000.0), np.append(mk[:, 1], 1e8),
+               kind, q0, None, [], name=f"hetero_pile_{B}" if hetero else f"uniform_pile_{B}")
+    sa.body_group = group
+    return sa
+
+
 def random_pile(seed: int, n_bodies: int, levels=(1, 2, 3), radius: float = 0.05,
                 density_range=(1e2, 1e4), kappa: float = 1e8, cell: float = 1.2) -> SceneArrays:
     """Loose random pile of noisy icospheres over a ground plane: bodies on a

@@ -168,7 +168,15 @@ int abd_partition(abd_scene *s, const abd_partition_desc *desc);
  * receives the overlap width. Host buffers. */
 int abd_partition_masks(abd_scene *s, double h, uint64_t *mask, double *w_out);
 
-/* Advance one time step.  Blocks until the step is complete. */
+/* Advance one time step of p->h (Eq. 1 by consensus ADMM over the current
+ * partition, Eq. 5-10).  Blocks until the step is complete.  Returns a
+ * status: 0, a positive warning (the step was taken) or a negative error
+ * (the step did not complete; abd_last_error describes it).  With
+ * p->dt_split_max > 0, a step whose merge check fails after K rounds is
+ * retaken from its start state as two steps of h/2 (each with
+ * dt_split_max - 1) and returns ABD_DT_SPLIT;
+ * stats then sum the ADMM rounds and Newton iterations of every attempt and
+ * report the second half step's residuals and minimum distance. */
 int abd_step(abd_scene *s, const abd_step_params *p, abd_step_stats *stats);
 
 /* Host copies of the state (q, qdot), [B][12] each; either may be NULL. */

@@ -126,7 +126,7 @@ typedef struct {
     int32_t dt_split_max;          /* adaptive time stepping (Sec. 4.2, Fig. 4): when the merge check
                                       blocks after K rounds, retake the step from the same state as two
                                       steps of h/2, recursively up to this depth, before the one-partition
-                                      fallback; 0 (default) disables it */
+                                      fallback; 0 (default) disables it; at most 16 */
 } abd_step_params;
 
 typedef struct {

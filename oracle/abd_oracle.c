@@ -1783,6 +1783,7 @@ out:
 }
 
 int orc_step(orc_scene *s, const orc_params *P, orc_stats *st) {
+    if (!s || !P || P->dt_split_max < 0 || P->dt_split_max > 16) return ORC_E_INVALID;
     orc_stats first;
     int rc = step_once(s, P, &first);
     if (rc != ORC_SPLIT_REQUEST) {

@@ -63,7 +63,7 @@ typedef struct {
     int32_t n_slabs, axis;
     const double *planes;            /* n_slabs-1 offsets, or NULL: equal widths over the dynamic AABB */
     double alpha_w, w_min;           /* w = max(alpha_w v_max h, w_min); w_min <= 0: smallest body AABB diagonal */
-    int32_t dt_split_max;            /* blocked merge: retake the step as two h/2 steps, this deep (0: off) */
+    int32_t dt_split_max;            /* blocked merge: retake the step as two h/2 steps, this deep (0: off, at most 16) */
 } orc_params;
 
 typedef struct {

@@ -67,6 +67,8 @@ struct SceneDev {
 constexpr int kClusterSize = 32;
 // Inertia weight of kinematic bodies (prescribed motion through their
 // predicted state, see include/abd.h).
+// deepest adaptive time-step split a step may request (2^16 sub-steps)
+constexpr int kMaxDtSplit = 16;
 constexpr double kKinematicWeight = 1e6;
 
 // Per-step workspace of the consensus solve.

@@ -1008,7 +1008,8 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
 }  // namespace
 
 extern "C" int abd_step(abd_scene *s, const abd_step_params *p, abd_step_stats *st) {
-    if (!s || !p || p->h <= 0 || p->dhat <= 0) return ABD_E_INVALID;
+    if (!s || !p || p->h <= 0 || p->dhat <= 0 || p->dt_split_max < 0 || p->dt_split_max > kMaxDtSplit)
+        return ABD_E_INVALID;
     abd_step_stats local;
     if (!st) st = &local;
     memset(st, 0, sizeof *st);

@@ -635,3 +635,16 @@ def test_heterogeneous_crop_steps_penetration_free():
     for b in range(sa.n_dynamic):
         A = q[b, 3:].reshape(3, 3)
         assert np.abs(A @ A.T - np.eye(3)).max() < 1e-3
+
+
+def test_dt_split_depth_is_bounded():
+    """A negative or over-deep split request is rejected before any work
+    (at most 2^16 sub-steps per step)."""
+    sa = scenes.cube_stack(nx=1, ny=1, nz=1)
+    o = O.Scene(sa)
+    q0 = o.state()[0].copy()
+    for bad in (-1, 17):
+        with pytest.raises(RuntimeError, match="failed: -1 "):
+            o.step(O.default_params(dt_split_max=bad))
+    assert np.array_equal(o.state()[0], q0)
+    assert o.step(O.default_params(dt_split_max=16))["status"] >= 0

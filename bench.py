@@ -317,6 +317,32 @@ def serve_legs(abd):
     return serving, batched
 
 
+def host_cpu():
+    """The host the oracle ran on: architecture, logical cores, CPU model where
+    the kernel reports one."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":", 1)[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:  # Arm kernels list implementer/part codes only; lscpu names the core
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return {"machine": platform.machine(), "nproc": os.cpu_count(), "model": model}
+
+
 def cpu_baseline(seconds):
     """The FP64 oracle as it stands, on one host core, over the first steps of
     the same workload (stops after `seconds` of CPU work, at least one step)."""
@@ -332,6 +358,7 @@ def cpu_baseline(seconds):
             break
     dt = time.process_time() - t0
     return {"value": round(sa.n_dynamic * n / dt, 4), "unit": "body-steps/s", "cores": 1, "kind": "oracle",
+            "host": host_cpu(),
             "sample": f"first {n} steps of the same scene (512 bodies, 4 slabs), single thread, "
                       f"{dt:.1f} s CPU; early steps are pre-contact free fall"}
 
@@ -362,7 +389,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "bodies": sa.n_dynamic, "partitions": 4},
             "cpu_baseline": {"value": round(value, 4), "unit": "body-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "host": host_cpu()},
             "e2e": {"value": round(value, 4), "unit": "body-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 

@@ -18,7 +18,7 @@ _SO = os.path.join(_HERE, "libabd_oracle.so")
 _SRC = os.path.join(_HERE, "abd_oracle.c")
 
 DYNAMIC, STATIC, KINEMATIC = 0, 1, 2
-OK, ADMM_MAXITER, FELL_BACK = 0, 1, 3
+OK, ADMM_MAXITER, NEWTON_MAXITER, FELL_BACK, DT_SPLIT = 0, 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:

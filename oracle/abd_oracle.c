@@ -969,6 +969,7 @@ typedef struct {
     int max_newton, max_halv;
     double *x0, *x1;   /* [V][3] scratch */
     int newton_iters;
+    int maxed;          /* some solve ran max_newton iterations without meeting eps_N */
     int64_t cand_peak, act_peak;
 } local_t;
 
@@ -1365,9 +1366,12 @@ static double local_toi(local_t *L, const double *x0, const double *x1, int64_t 
  *   active set at q, g and PSD-projected H, solve H dq = -g;
  *   stop when |dq|_inf / (h l) < eps_N (before the line search);
  *   alpha = min(1, TOI along q -> q + dq); halve while E(q + alpha dq) > E(q);
- *   q <- q + alpha dq. */
+ *   q <- q + alpha dq.
+ * A solve that spends max_newton iterations without meeting eps_N marks the
+ * partition (the step then reports ORC_NEWTON_MAXITER unless a worse status
+ * applies). */
 static int local_solve(local_t *L) {
-    int n = 12 * L->ns, rc = ORC_OK;
+    int n = 12 * L->ns, rc = ORC_OK, converged = 0;
     if (n == 0) return ORC_OK;
     double *g = (double *)malloc(sizeof(double) * n), *dq = (double *)malloc(sizeof(double) * n);
     double *qn = (double *)malloc(sizeof(double) * n);
@@ -1383,7 +1387,7 @@ static int local_solve(local_t *L) {
         L->newton_iters++;
         double dmax_ = 0.0;
         for (int i = 0; i < n; ++i) dmax_ = dmax(dmax_, fabs(dq[i]));
-        if (dmax_ / (L->h * L->l) < L->epsN) break;
+        if (dmax_ / (L->h * L->l) < L->epsN) { converged = 1; break; }
         for (int i = 0; i < n; ++i) qn[i] = L->q[i] + dq[i];
         local_positions(L, L->q, L->x0);
         local_positions(L, qn, L->x1);
@@ -1397,6 +1401,7 @@ static int local_solve(local_t *L) {
         }
         memcpy(L->q, qn, sizeof(double) * n);
     }
+    if (rc == ORC_OK && !converged) L->maxed = 1;
 done:
     free(g); free(dq); free(qn); free(H.diag); free(H.rowhead); free(H.off); free(H.next);
     return rc;
@@ -1731,10 +1736,11 @@ static int step_once(orc_scene *s, const orc_params *P, orc_stats *st) {
             if (parts[i].shared[sl]) memcpy(qnew + 12 * b, z + 12 * b, sizeof(double) * 12);
             else memcpy(qnew + 12 * b, parts[i].q + 12 * sl, sizeof(double) * 12);
         }
-    int newton = 0;
+    int newton = 0, maxed = 0;
     int64_t cpk = 0, apk = 0;
     for (int i = 0; i < N; ++i) {
         newton += parts[i].newton_iters;
+        maxed |= parts[i].maxed;
         if (parts[i].cand_peak > cpk) cpk = parts[i].cand_peak;
         if (parts[i].act_peak > apk) apk = parts[i].act_peak;
     }
@@ -1767,6 +1773,7 @@ static int step_once(orc_scene *s, const orc_params *P, orc_stats *st) {
             for (int i = 0; i < 12; ++i) s->v[12 * b + i] = (qnew[12 * b + i] - qt[12 * b + i]) / P->h;
     memcpy(s->q, qnew, sizeof(double) * 12 * nb);
     double md = scene_min_distance(s, P->dhat);
+    if (maxed && status == ORC_OK) status = ORC_NEWTON_MAXITER;
     if (st) {
         st->status = status; st->admm_iters = admm; st->newton_iters = newton; st->n_shared = nshared;
         st->n_slots = nslots; st->merge_ok = merge_ok; st->n_candidates_peak = cpk; st->n_active_peak = apk;

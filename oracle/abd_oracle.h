@@ -31,7 +31,7 @@ extern "C" {
 #endif
 
 enum { ORC_DYNAMIC = 0, ORC_STATIC = 1, ORC_KINEMATIC = 2 };
-enum { ORC_OK = 0, ORC_ADMM_MAXITER = 1, ORC_FELL_BACK = 3, ORC_DT_SPLIT = 4,
+enum { ORC_OK = 0, ORC_ADMM_MAXITER = 1, ORC_NEWTON_MAXITER = 2, ORC_FELL_BACK = 3, ORC_DT_SPLIT = 4,
        ORC_E_INVALID = -1, ORC_E_OOM = -2, ORC_E_NOT_SPD = -3, ORC_E_PENETRATION = -6 };
 
 typedef struct {

@@ -648,3 +648,22 @@ def test_dt_split_depth_is_bounded():
             o.step(O.default_params(dt_split_max=bad))
     assert np.array_equal(o.state()[0], q0)
     assert o.step(O.default_params(dt_split_max=16))["status"] >= 0
+
+
+def test_newton_cap_status_boundary():
+    """A step whose local solve meets eps_N at its n-th Newton solve is OK with
+    max_newton = n and reports NEWTON_MAXITER with max_newton = n - 1 (the
+    state is still advanced by the n - 1 iterations taken)."""
+    sa = scenes.cube_stack()
+    o = O.Scene(sa)
+    for _ in range(40):  # the first step with contact Newton work
+        q0, v0 = o.state()
+        st = o.step(O.default_params())
+        n = st["newton_iters"]
+        if n > 2:
+            break
+    assert st["status"] == O.OK and n > 2
+    for cap, status in ((n, O.OK), (n - 1, O.NEWTON_MAXITER)):
+        o.set_state(q0, v0)
+        s2 = o.step(O.default_params(max_newton=cap))
+        assert (s2["status"], s2["newton_iters"]) == (status, cap)

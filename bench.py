@@ -295,10 +295,66 @@ def _serve(abd, reqs, n_streams, params):
             "queue_ms_p99": round(float(np.percentile([i["queue_ms"] for i in infos], 99)), 3)}
 
 
+def poisson_arrivals(rate, n, seed):
+    """Arrival times (s after the first possible arrival) of n requests of a
+    Poisson process with `rate` requests per second."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=n))
+
+
+def open_loop(server, reqs, params, arrivals, clock=time.perf_counter, sleep=time.sleep):
+    """Open-loop serving: request i is submitted at arrival time arrivals[i]
+    whether or not earlier requests are done (they keep running on the
+    server's workers meanwhile), then every request is waited for.  Response
+    time = queue + run of a request (submit to done); step latency = each
+    abd_step call of each request.  The server is closed on return."""
+    lags, ts = [], []
+    try:
+        t0 = clock()
+        for (sa, k), ta in zip(reqs, arrivals):
+            d = t0 + ta - clock()
+            if d > 0:
+                sleep(d)
+            lags.append(clock() - (t0 + ta))
+            ts.append(server.submit(sa, k, params))
+        infos = [server.wait(t) for t in ts]
+        span = clock() - t0
+        lat = np.concatenate([server.latencies(t) for t in ts])
+    finally:
+        server.close()
+    resp = [i["queue_ms"] + i["run_ms"] for i in infos]
+    bs = sum(sa.n_dynamic * k for sa, k in reqs)
+    return {"value": round(bs / span, 2), "unit": "body-steps/s", "span_s": round(span, 4),
+            "p50_step_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_step_ms": round(float(np.percentile(lat, 99)), 3),
+            "p50_response_ms": round(float(np.percentile(resp, 50)), 3),
+            "p99_response_ms": round(float(np.percentile(resp, 99)), 3),
+            "queue_ms_p99": round(float(np.percentile([i["queue_ms"] for i in infos], 99)), 3),
+            "submit_lag_ms_max": round(1e3 * max(lags), 3),
+            "worst_status": int(max(i["status"] for i in infos))}
+
+
+def poisson_sweep(make_server, reqs, params, capacity_rps, fractions=(0.25, 0.5, 1.0, 2.0), seed=1):
+    """The serving workload under Poisson arrivals at rates lambda = f x the
+    server's measured closed-batch capacity (requests/s), one open-loop run
+    per rate; a run that raises reports its error instead of a number."""
+    out = []
+    for f in fractions:
+        lam = f * capacity_rps
+        row = {"fraction_of_capacity": f, "lambda_rps": round(lam, 3)}
+        try:
+            row.update(open_loop(make_server(), reqs, params, poisson_arrivals(lam, len(reqs), seed)))
+        except Exception as e:  # keep the benchmark line; say what failed
+            row["error"] = f"{type(e).__name__}: {e}"
+        out.append(row)
+    return out
+
+
 def serve_legs(abd):
     """Served and batched legs (bounded samples of the serving and
-    uneven-subdomain workloads), mixed precision, every request submitted at
-    once to the serving runtime (closed batch, continuous admission)."""
+    uneven-subdomain workloads), mixed precision: every request submitted at
+    once to the serving runtime (closed batch, continuous admission), then
+    the same requests under Poisson arrivals at four rates."""
     from paper_2605_15875_gb300 import scenes
     p = abd.default_params(precision=abd.MIXED, pcg_rtol=1e-5)
     p64 = abd.default_params(precision=abd.FP64, pcg_rtol=1e-12)
@@ -308,6 +364,10 @@ def serve_legs(abd):
     serving["plain_fp64_one_at_a_time"] = plain["value"]
     serving["speedup_vs_plain_fp64"] = round(serving["value"] / plain["value"], 3)
     serving["sample"] = "64 requests: scenes of 8-512 bodies (log-uniform; cube stacks and sphere piles), 1-10 steps"
+    cap_rps = len(reqs) / serving["wall_s"]
+    serving["poisson"] = poisson_sweep(lambda: abd.Server(n_streams=4), reqs, p, cap_rps)
+    serving["poisson_note"] = ("open loop, 4 streams, the same 64 requests; lambda relative to the closed-batch "
+                               "capacity above (requests/s)")
     subs = [(sa, 10) for sa in scenes.batched_subdomains(seed=0, n_scenes=16, lo=16, hi=512, levels=(1, 2))]
     batched = _serve(abd, subs, 8, p)
     plain = _serve(abd, subs, 1, p64)
@@ -350,17 +410,30 @@ def cpu_baseline(seconds):
     sa = scene_arrays()
     sc = O.Scene(sa)
     p = O.default_params(n_slabs=4, axis=0, planes=PLANES)
-    n, t0 = 0, time.process_time()
+    # CPU time of this thread alone: the oracle runs here, while idle numpy
+    # worker threads spinning elsewhere in the process would inflate
+    # process_time()
+    n, t0 = 0, time.thread_time()
     while True:
         sc.step(p)
         n += 1
-        if time.process_time() - t0 > seconds:
+        if time.thread_time() - t0 > seconds:
             break
-    dt = time.process_time() - t0
+    dt = time.thread_time() - t0
+    # the 8-cube stack of the plain single-partition workload, all 100 steps
+    from paper_2605_15875_gb300 import scenes
+    cs = scenes.cube_stack()
+    oc, pc = O.Scene(cs), O.default_params()
+    t1 = time.thread_time()
+    for _ in range(100):
+        oc.step(pc)
+    dc = time.thread_time() - t1
     return {"value": round(sa.n_dynamic * n / dt, 4), "unit": "body-steps/s", "cores": 1, "kind": "oracle",
             "host": host_cpu(),
             "sample": f"first {n} steps of the same scene (512 bodies, 4 slabs), single thread, "
-                      f"{dt:.1f} s CPU; early steps are pre-contact free fall"}
+                      f"{dt:.1f} s CPU; early steps are pre-contact free fall",
+            "cube_stack_8": {"value": round(cs.n_dynamic * 100 / dc, 2), "unit": "body-steps/s",
+                             "sample": f"8 stacked unit cubes on a plane, one partition, 100 steps, {dc:.2f} s CPU"}}
 
 
 def run_reference(args, rank, world):

@@ -65,10 +65,10 @@ struct SceneDev {
 };
 
 constexpr int kClusterSize = 32;
+// Deepest adaptive time-step split a step may request (2^16 sub-steps).
+constexpr int kMaxDtSplit = 16;
 // Inertia weight of kinematic bodies (prescribed motion through their
 // predicted state, see include/abd.h).
-// deepest adaptive time-step split a step may request (2^16 sub-steps)
-constexpr int kMaxDtSplit = 16;
 constexpr double kKinematicWeight = 1e6;
 
 // Per-step workspace of the consensus solve.

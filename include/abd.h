@@ -176,7 +176,9 @@ int abd_partition_masks(abd_scene *s, double h, uint64_t *mask, double *w_out);
  * retaken from its start state as two steps of h/2 (each with
  * dt_split_max - 1) and returns ABD_DT_SPLIT;
  * stats then sum the ADMM rounds and Newton iterations of every attempt and
- * report the second half step's residuals and minimum distance. */
+ * report the second half step's residuals and minimum distance.  A scene
+ * whose bodies are all static has no unknowns: the step returns 0 at once
+ * (one ADMM round, no Newton iteration) and changes no state. */
 int abd_step(abd_scene *s, const abd_step_params *p, abd_step_stats *stats);
 
 /* Host copies of the state (q, qdot), [B][12] each; either may be NULL. */

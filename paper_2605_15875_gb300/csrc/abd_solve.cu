@@ -866,19 +866,29 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
         return rc;
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     double msum = 0.0;
-    int nd = 0;
+    int nd = 0, ndof = 0;
     for (int b = 0; b < s->nb; ++b) {
         for (int k = 0; k < 3; ++k) {
             lo[k] = std::min(lo[k], box[6 * (size_t)b + k]);
             hi[k] = std::max(hi[k], box[6 * (size_t)b + 3 + k]);
         }
         if (s->kind[b] == ABD_DYNAMIC) { msum += s->mass[b]; ++nd; }
+        if (s->kind[b] != ABD_STATIC) ++ndof;
     }
     C.l = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
                     (hi[2] - lo[2]) * (hi[2] - lo[2]));
     C.kB = p->kappa_barrier > 0.0 ? p->kappa_barrier
                                   : 10.0 * (nd ? msum / nd : 1.0) *
                                         std::sqrt(s->g[0] * s->g[0] + s->g[1] * s->g[1] + s->g[2] * s->g[2]) / p->dhat;
+    if (ndof == 0) {
+        // every body is static: the step has no unknowns and nothing moves
+        st->l = C.l; st->kappa_barrier = C.kB; st->n_partitions = 1;
+        st->admm_iters = 1;
+        st->status = ABD_OK;
+        st->t_total_ms = now_ms() - T0;
+        st->kernel_launches = s->n_launches - L0;
+        return ABD_OK;
+    }
     std::vector<uint64_t> mask;
     double wov = 0.0;
     int saved = s->n_slabs;

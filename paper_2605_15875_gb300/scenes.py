@@ -241,6 +241,16 @@ def cube_stack(seed: int = 0, nx: int = 2, ny: int = 2, nz: int = 2, spacing: fl
                  name=f"cube_stack_{nx}x{ny}x{nz}")
 
 
+def static_only(gap: float = 5e-4) -> SceneArrays:
+    """Degenerate scene without unknowns: two static unit cubes side by side,
+    `gap` apart (inside the usual activation distance), 0.1 above the ground
+    plane y = 0.  Pairs of static bodies are never candidates, so a step has
+    nothing to solve."""
+    q0 = [_q_at([-0.5 - 0.5 * gap, 0.6, 0.0]), _q_at([0.5 + 0.5 * gap, 0.6, 0.0])]
+    return _pack([cube_mesh(1.0)], [0, 0], 1000.0, 1e8, KIND_STATIC, q0, None, [(1, 1.0, 0.0)],
+                 name="static_only")
+
+
 def sphere_grid_in_box(seed: int = 0, n: int = 8, level: int = 2, radius: float = 0.1,
                        spacing: float = 0.25, lowest: float = 0.3, box=(2.4, 3.0, 2.4),
                        density: float = 1000.0, kappa: float = 1e8, ny: Optional[int] = None,

@@ -85,6 +85,23 @@ def test_free_fall_closed_form():
         assert st["status"] == 0 and st["admm_iters"] == 1
 
 
+def test_static_only_scene_has_nothing_to_solve():
+    """Degenerate case: no dynamic or kinematic body, so Eq. 1 has no
+    unknowns; static pairs are excluded even within dhat, the state stays bit
+    for bit, and a four-slab partition changes nothing."""
+    sa = scenes.static_only()
+    for slabs in (1, 4):
+        sc = O.Scene(sa)
+        q0, v0 = sc.state()
+        p = O.default_params(n_slabs=slabs, axis=0)
+        for _ in range(3):
+            st = sc.step(p)
+            assert st["status"] == 0 and st["newton_iters"] == 0 and st["n_slots"] == 0
+            assert st["n_candidates_peak"] == 0 and st["n_active_peak"] == 0
+        q, v = sc.state()
+        assert np.array_equal(q, q0) and np.array_equal(v, v0)
+
+
 # --------------------------------------------------------------------------- O3
 
 def test_orthogonality_fd_and_rotation_invariance():

@@ -1870,3 +1870,58 @@ int orc_objective(orc_scene *s, const orc_params *P, const double *q, const doub
     free(ones); free(qa); free(qt);
     return rc;
 }
+
+/* The local objectives F_i of Eq. 3 (partition i's share of Eq. 1: inertia and
+ * orthogonality of each slot weighted 1/kappa_b, each contact 1/kappa_c, each
+ * plane contact 1/kappa_b) at a consensus point, where every replica sits at
+ * the body's own q (z = q, u = 0: the augmented term of Eq. 5 vanishes).
+ * Partition membership is the slab rule at the scene's current state; q and
+ * qtil give every DOF body ([n_dof][12], body order); barrier stiffness
+ * P->kappa_barrier.  E_parts[i] receives F_i (up to cap partitions),
+ * g_sum[n_dof][12] the sum over partitions of the gradients of F_i scattered
+ * to the bodies.  Returns the number of partitions, or a negative status. */
+int orc_local_objectives(orc_scene *s, const orc_params *P, const double *q, const double *qtil, double *E_parts,
+                         int cap, double *g_sum) {
+    int N = P->n_slabs < 1 ? 1 : P->n_slabs;
+    uint64_t *mask = (uint64_t *)malloc(sizeof(uint64_t) * s->nb);
+    int *dof = (int *)malloc(sizeof(int) * s->nb);
+    double *qa = (double *)calloc(12 * (size_t)s->nb, sizeof(double)), *qt = (double *)calloc(12 * (size_t)s->nb, sizeof(double));
+    int rc = (!mask || !dof || !qa || !qt) ? ORC_E_OOM : ORC_OK, k = 0;
+    if (!rc) rc = orc_partition(s, P, mask, NULL);
+    if (!rc) {
+        memcpy(qa, s->q, sizeof(double) * 12 * s->nb);
+        memcpy(qt, s->q, sizeof(double) * 12 * s->nb);
+        for (int b = 0; b < s->nb; ++b) {
+            dof[b] = -1;
+            if (is_dof(s->kind[b])) {
+                memcpy(qa + 12 * b, q + 12 * k, sizeof(double) * 12);
+                memcpy(qt + 12 * b, qtil + 12 * k, sizeof(double) * 12);
+                dof[b] = k++;
+            }
+        }
+        if (g_sum) memset(g_sum, 0, sizeof(double) * 12 * (size_t)k);
+    }
+    for (int i = 0; !rc && i < N; ++i) {
+        local_t L;
+        rc = local_init(&L, s, mask, i, qa, qt, P, P->kappa_barrier, 1.0);
+        if (!rc) {
+            memcpy(L.z, L.q, sizeof(double) * 12 * (size_t)L.ns);
+            for (int sl = 0; sl < L.ns; ++sl) L.rho[sl] = 1.0;
+            if (i < cap && E_parts) E_parts[i] = local_energy(&L, L.q);
+            if (g_sum) {
+                int n = 12 * L.ns;
+                double *gg = (double *)malloc(sizeof(double) * (n ? n : 1));
+                bsr_t H = {0};
+                H.diag = (double *)malloc(sizeof(double) * 144 * (size_t)(L.ns ? L.ns : 1));
+                H.rowhead = (int *)malloc(sizeof(int) * (L.ns ? L.ns : 1));
+                rc = (!gg || !H.diag || !H.rowhead) ? ORC_E_OOM : local_assemble(&L, L.q, gg, &H);
+                for (int sl = 0; !rc && sl < L.ns; ++sl)
+                    for (int j = 0; j < 12; ++j) g_sum[12 * dof[L.body[sl]] + j] += gg[12 * sl + j];
+                free(gg); free(H.diag); free(H.rowhead); free(H.off); free(H.next);
+            }
+        }
+        local_free(&L);
+    }
+    free(mask); free(dof); free(qa); free(qt);
+    return rc ? rc : N;
+}

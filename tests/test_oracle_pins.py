@@ -462,6 +462,33 @@ def test_admm_free_flight_converges_to_prediction():
     assert np.abs(q[:, :3] - pred).max() < 1e-12
 
 
+@pytest.mark.parametrize("slabs", [2, 3])
+def test_local_objectives_sum_to_global_at_consensus(slabs):
+    """Eq. 3's weights split Eq. 1 exactly: at a consensus point (every
+    replica at the body's q, so the augmented term is zero) the partitions'
+    objectives sum to the single-partition objective, and so do their
+    gradients.  A touching row of six cubes (gaps 5e-4 < dhat, resting 5e-4 above
+    the plane) puts contacts between a shared and an internal body, between
+    two shared bodies and on the plane, so a wrong kappa_b or kappa_c (e.g.
+    counting partitions holding either body instead of both) fails."""
+    sa = scenes.cube_stack(nx=6, ny=1, nz=1, spacing=1.0005, bottom_gap=5e-4, jitter=0.0)
+    sc = O.Scene(sa)
+    p = O.default_params(n_slabs=slabs, axis=0, kappa_barrier=1e5)
+    m, _ = sc.partition(p)
+    assert any(bin(int(x)).count("1") >= 2 for x in m) and any(bin(int(x)).count("1") == 1 for x in m)
+    q, _ = sc.state()
+    qd = q[sa.body_kind == scenes.KIND_DYNAMIC]
+    qt = qd + 1e-3 * np.random.default_rng(0).normal(size=qd.shape)
+    Ep, gs = sc.local_objectives(p, qd, qt)
+    E, g, _ = sc.objective(p, qd, qt, want_hess=False)
+    assert len(Ep) == slabs and np.all(Ep > 0)
+    # the barrier terms are active: the objective differs from inertia + orthogonality alone
+    E_free, _, _ = sc.objective(O.default_params(kappa_barrier=1e-30), qd, qt, want_hess=False)
+    assert E - E_free > 1e-3 * E
+    assert abs(Ep.sum() - E) <= 1e-12 * abs(E)
+    assert np.abs(gs - g.reshape(gs.shape)).max() <= 1e-12 * np.abs(g).max()
+
+
 def test_admm_tracks_monolithic_per_step():
     """The converged consensus state lies within O(theta h l) of the
     single-partition solution from the same start (the q* comparison)."""

@@ -56,7 +56,7 @@ enum {
     ABD_E_CUDA = -3,
     ABD_E_PAIR_OVERFLOW = -4,
     ABD_E_DEVICE_TIMEOUT = -5,
-    ABD_E_PENETRATION = -6,
+    ABD_E_PENETRATION = -6,     /* the step ended with a pair at distance <= 0 */
     ABD_E_UNSUPPORTED = -7
 };
 
@@ -178,7 +178,10 @@ int abd_partition_masks(abd_scene *s, double h, uint64_t *mask, double *w_out);
  * stats then sum the ADMM rounds and Newton iterations of every attempt and
  * report the second half step's residuals and minimum distance.  A scene
  * whose bodies are all static has no unknowns: the step returns 0 at once
- * (one ADMM round, no Newton iteration) and changes no state. */
+ * (one ADMM round, no Newton iteration) and changes no state.
+ * ABD_E_PENETRATION: the state after the step has a contact pair or a
+ * vertex-plane pair at distance <= 0 (stats->min_distance); the state is
+ * kept as computed, so the caller can inspect or restore it. */
 int abd_step(abd_scene *s, const abd_step_params *p, abd_step_stats *stats);
 
 /* Host copies of the state (q, qdot), [B][12] each; either may be NULL. */

@@ -1004,6 +1004,7 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
     if ((rc = final_min_distance(C, mind))) return rc;
     st->min_distance = mind;
     if (maxed && status == ABD_OK) status = ABD_NEWTON_MAXITER;
+    if (mind <= 0.0) status = set_err(s, ABD_E_PENETRATION, "a contact pair or plane is at distance <= 0 after the step");
     st->status = status;
     st->admm_iters = admm;
     st->newton_iters = newton;

@@ -206,21 +206,29 @@ def run_ours(args, rank, world):
             # every instrumented kernel: compulsory bytes over its live CUDA-event time
             "kernels_gbs": {n: (round(v[2] / (v[1] / 1e3) / 1e9, 2) if v[1] > 0 and v[2] > 0 else None)
                             for n, v in ks.items()}}
+    errors = {}  # a comparison leg that fails reports here; the headline stays
     fp64 = None
     if not args.no_fp64:
-        sc64, p64 = make(abd.FP64)
-        lat64, _, _ = timed(sc64, p64, args.steps, args.warmup)
-        fp64 = B_ * args.steps * world / (sum(lat64) / 1e3)
-        sc64.close()
+        try:
+            sc64, p64 = make(abd.FP64)
+            lat64, _, _ = timed(sc64, p64, args.steps, args.warmup)
+            fp64 = B_ * args.steps * world / (sum(lat64) / 1e3)
+            sc64.close()
+        except Exception as e:
+            errors["fp64"] = f"{type(e).__name__}: {e}"
     # the same window with a fixed penalty rho = beta m (no residual-driven adaptation)
     fixed = None
     if not args.no_fixed_rho:
-        scf, pf = make(abd.MIXED, abd.RHO_FIXED)
-        latf, _, statf = timed(scf, pf, args.steps, args.warmup)
-        fixed = {"value": round(B_ * args.steps * world / (sum(latf) / 1e3), 3), "unit": "body-steps/s",
-                 "admm_iters_mean": float(np.mean([x["admm_iters"] for x in statf])),
-                 "newton_iters_mean": float(np.mean([x["newton_iters"] for x in statf]))}
-        scf.close()
+        try:
+            scf, pf = make(abd.MIXED, abd.RHO_FIXED)
+            latf, _, statf = timed(scf, pf, args.steps, args.warmup)
+            fixed = {"value": round(B_ * args.steps * world / (sum(latf) / 1e3), 3), "unit": "body-steps/s",
+                     "admm_iters_mean": float(np.mean([x["admm_iters"] for x in statf])),
+                     "newton_iters_mean": float(np.mean([x["newton_iters"] for x in statf])),
+                     "min_distance_min": float(min(x["min_distance"] for x in statf))}
+            scf.close()
+        except Exception as e:
+            errors["fixed_rho"] = f"{type(e).__name__}: {e}"
     e2e = None
     if not args.no_e2e:
         sce, pe = make(abd.MIXED)
@@ -245,7 +253,10 @@ def run_ours(args, rank, world):
         sce.close()
     serving = batched = None
     if not args.no_serving:
-        serving, batched = serve_legs(abd)
+        try:
+            serving, batched = serve_legs(abd)
+        except Exception as e:
+            errors["serving"] = f"{type(e).__name__}: {e}"
     cpu = cpu_baseline(args.cpu_seconds) if (rank == 0 and world == 1) else None
     lat_sorted = sorted(lat)
     out = {
@@ -274,6 +285,8 @@ def run_ours(args, rank, world):
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if errors:
+        out["leg_errors"] = errors
     sc.close()
     return out
 

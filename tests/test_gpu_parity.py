@@ -96,25 +96,6 @@ def test_free_fall_closed_form_gpu():
         assert np.abs(q[:, 3:] - q0[:, 3:]).max() == 0.0
 
 
-def test_static_only_scene_matches_oracle():
-    """Degenerate case: every body static, so a step has no unknowns; both
-    sides report OK without Newton work and leave the state bit for bit."""
-    sa = scenes.static_only()
-    for slabs in (1, 4):
-        g, o = abd.Scene(sa), O.Scene(sa)
-        g.partition(n_slabs=slabs, axis=0)
-        q0, v0 = g.state()
-        for _ in range(3):
-            sg = g.step(abd.default_params())
-            so = o.step(O.default_params(n_slabs=slabs, axis=0))
-            for k in ("status", "admm_iters", "newton_iters", "min_distance"):
-                assert sg[k] == so[k], (k, sg, so)
-        q, v = g.state()
-        assert np.array_equal(q, q0) and np.array_equal(v, v0)
-        assert np.array_equal(q, o.state()[0])
-        g.close()
-
-
 def test_cube_stack_fp64_parity_100_steps():
     sa = scenes.cube_stack()
     worst, g, o = _run_pair(sa, 100, abd.default_params(), O.default_params(), FP64_TOL)

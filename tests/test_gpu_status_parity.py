@@ -1,7 +1,8 @@
 """Step statuses through the C ABI against the oracle: the Newton iteration
 cap (a local solve that spends max_newton iterations without meeting
 Eq. 8's epsilon_N reports NEWTON_MAXITER; one that meets it on its last
-allowed iteration is OK)."""
+allowed iteration is OK), and a scene without unknowns (every body static)
+that steps to itself."""
 import numpy as np
 import pytest
 
@@ -39,3 +40,22 @@ def test_newton_cap_status_matches_oracle():
         assert np.abs(qg - qo).max() / max(1.0, np.abs(qo).max()) <= 1e-9
     assert sg["status"] == abd.NEWTON_MAXITER
     g.close()
+
+
+def test_static_only_scene_matches_oracle():
+    """Degenerate case: every body static, so a step has no unknowns; both
+    sides report OK without Newton work and leave the state bit for bit."""
+    sa = scenes.static_only()
+    for slabs in (1, 4):
+        g, o = abd.Scene(sa), O.Scene(sa)
+        g.partition(n_slabs=slabs, axis=0)
+        q0, v0 = g.state()
+        for _ in range(3):
+            sg = g.step(abd.default_params())
+            so = o.step(O.default_params(n_slabs=slabs, axis=0))
+            for k in ("status", "admm_iters", "newton_iters", "min_distance"):
+                assert sg[k] == so[k], (k, sg, so)
+        q, v = g.state()
+        assert np.array_equal(q, q0) and np.array_equal(v, v0)
+        assert np.array_equal(q, o.state()[0])
+        g.close()

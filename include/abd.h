@@ -137,7 +137,13 @@ typedef struct {
     int64_t pcg_iters;             /* PCG iterations summed over Newton iterations */
     int64_t n_candidates_peak, n_active_peak;
     double r_inf, s_inf, delta_inf, min_distance, l, kappa_barrier, w;
-    double t_solve_ms, t_coll_ms, t_sync_ms, t_total_ms; /* host wall clock split (Table 1 columns) */
+    /* host wall clock split after Table 1's columns: t_solve_ms = the local
+     * Newton solves, including their broad phase, narrow phase and CCD, which
+     * run inside each Newton iteration (and its CUDA graph); t_coll_ms is
+     * therefore 0 (abd_kernel_stats splits device time by kernel instead);
+     * t_sync_ms = consensus, residuals and the merge check; t_total_ms =
+     * the whole step */
+    double t_solve_ms, t_coll_ms, t_sync_ms, t_total_ms;
     int64_t kernel_launches;       /* kernels of this library launched by the step */
 } abd_step_stats;
 

@@ -82,3 +82,25 @@ def test_server_and_partition_calls_reject_bad_arguments():
     n = ctypes.c_int32()
     assert L.abd_partition_planes(None, None, 0, ctypes.byref(n)) == -1
     assert L.abd_pd_update(0, None, None, 0.0, 0.0, None, None) == -1
+
+
+def test_every_status_code_has_its_own_text_and_null_arguments_are_rejected():
+    """Each status the header enumerates maps to a distinct message; calls
+    given NULL handles fail with ABD_E_INVALID before any device work."""
+    import ctypes
+    import re
+    from paper_2605_15875_gb300 import abd, build
+    build.build()
+    L = abd.load()
+    hdr = open(os.path.join(ROOT, "include", "abd.h")).read()
+    codes = {int(v) for v in re.findall(r"ABD_(?:E_)?[A-Z_]+ = (-?\d+),?\s*(?:/\*[^*]*\*/)?\s*\n", hdr[hdr.index("ABD_OK = 0"):])}
+    codes.add(0)
+    assert {0, 1, 2, 3, 4, -1, -2, -3, -4, -5, -6, -7} <= codes
+    texts = {c: L.abd_status_string(c).decode() for c in codes}
+    assert len(set(texts.values())) == len(codes) and "unknown status" not in texts.values()
+    assert L.abd_status_string(12345).decode() == "unknown status"
+    st = abd.StepStats()
+    p = abd.default_params()
+    assert L.abd_step(None, ctypes.byref(p), ctypes.byref(st)) == -1
+    assert L.abd_state_get(None, None, None, 0) == -1
+    assert L.abd_candidates_noalloc(None, None, None, 1e-3, None, 0, None) == -1

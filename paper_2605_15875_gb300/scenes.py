@@ -241,6 +241,19 @@ def cube_stack(seed: int = 0, nx: int = 2, ny: int = 2, nz: int = 2, spacing: fl
                  name=f"cube_stack_{nx}x{ny}x{nz}")
 
 
+def colliding_pair(size: float = 0.2) -> SceneArrays:
+    """Two cubes of edge `size` and densities 1000 and 3000 flying at each
+    other without gravity or planes (velocities (2, 0, 0) and (-1, 0.3, 0)),
+    the second offset by (0.05, 0.02) across the line of approach so that the
+    impact is off-centre: only contact forces act, and they are internal."""
+    q0 = [_q_at([-0.75 * size, 0.0, 0.0]), _q_at([0.75 * size, 0.25 * size, 0.1 * size])]
+    v0 = np.zeros((2, 12))
+    v0[0, :3] = [2.0, 0.0, 0.0]
+    v0[1, :3] = [-1.0, 0.3, 0.0]
+    return _pack([cube_mesh(size)], [0, 0], [1000.0, 3000.0], 1e8, KIND_DYNAMIC, q0, v0, [],
+                 gravity=(0.0, 0.0, 0.0), name="colliding_pair")
+
+
 def static_only(gap: float = 5e-4) -> SceneArrays:
     """Degenerate scene without unknowns: two static unit cubes side by side,
     `gap` apart (inside the usual activation distance), 0.1 above the ground

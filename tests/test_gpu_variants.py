@@ -1,0 +1,85 @@
+"""CUDA path vs the FP64 oracle on configurations the other parity tests do
+not reach: zero gravity without planes (an off-centre impact of two unequal
+cubes, where only contact forces act and linear momentum is conserved), and a
+static mesh in a non-identity pose (the sphere pile and its box rotated about
+the gravity axis and translated)."""
+import copy
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2605_15875_gb300 import abd, scenes
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-9  # relative in q per step (FP64 path)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2605_15875_gb300 import build
+    build.build()
+    abd.load()
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(1.0, np.abs(b).max()))
+
+
+def _per_step(sa, steps, slabs, kappa_barrier=0.0):
+    """Before every step the CUDA scene takes the oracle's state; each step
+    must agree within the FP64 bound, with equal ADMM and Newton counts."""
+    g, o = abd.Scene(sa), O.Scene(sa)
+    g.partition(n_slabs=slabs, axis=0)
+    pg = abd.default_params(kappa_barrier=kappa_barrier)
+    po = O.default_params(n_slabs=slabs, axis=0, kappa_barrier=kappa_barrier)
+    active = 0
+    for k in range(steps):
+        qo, vo = o.state()
+        g.set_state(qo, vo)
+        sg, so = g.step(pg), o.step(po)
+        assert sg["status"] >= 0 and sg["min_distance"] > 0.0, (k, sg)
+        assert (sg["admm_iters"], sg["newton_iters"]) == (so["admm_iters"], so["newton_iters"]), (k, sg, so)
+        assert _rel(g.state()[0], o.state()[0]) <= FP64_TOL, k
+        active = max(active, so["n_active_peak"])
+    g.close()
+    return active
+
+
+@pytest.mark.parametrize("slabs", [1, 2])
+def test_zero_gravity_impact_fp64_parity_and_momentum(slabs):
+    sa = scenes.colliding_pair()
+    assert _per_step(sa, 12, slabs, kappa_barrier=1e3) > 0
+    # the CUDA path alone over the impact: total linear momentum stays put,
+    # within what the per-step q bound allows for v = (q_new - q_old) / h
+    # (2e-9 / h per coordinate, times the total mass of 32, against |P0| = 8)
+    g = abd.Scene(sa)
+    g.partition(n_slabs=slabs, axis=0)
+    m = np.array([g.body_props(b)[0] for b in range(2)])
+    P0 = (m[:, None] * g.state()[1][:, :3]).sum(0)
+    for _ in range(12):
+        g.step(abd.default_params(kappa_barrier=1e3))
+        P = (m[:, None] * g.state()[1][:, :3]).sum(0)
+        assert np.abs(P - P0).max() <= 1e-6 * np.abs(P0).max()
+    g.close()
+
+
+def _moved(sa, R, t):
+    sb = copy.deepcopy(sa)
+    q, v = sb.body_q0.copy(), sb.body_v0.copy()
+    for b in range(sb.n_bodies):
+        q[b, :3] = R @ q[b, :3] + t
+        q[b, 3:] = (R @ q[b, 3:].reshape(3, 3)).ravel()
+        v[b, :3] = R @ v[b, :3]
+        v[b, 3:] = (R @ v[b, 3:].reshape(3, 3)).ravel()
+    sb.body_q0, sb.body_v0 = np.ascontiguousarray(q), np.ascontiguousarray(v)
+    return sb
+
+
+def test_rotated_static_mesh_fp64_parity():
+    sa = scenes.sphere_grid_in_box(n=2, ny=2, nz=2, level=1, lowest=0.12, spacing=0.25)
+    R = np.array([[0.0, 0.0, 1.0], [0.0, 1.0, 0.0], [-1.0, 0.0, 0.0]])
+    sb = _moved(sa, R, np.array([0.375, 0.5, -1.25]))
+    assert len(sb.plane_offset) == 0
+    assert _per_step(sb, 16, 1) > 0

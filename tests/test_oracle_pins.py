@@ -457,6 +457,33 @@ def test_objective_gradient_fd_and_assembly_rebuilt_in_numpy():
     assert np.linalg.eigvalsh(H).min() > 0
 
 
+def test_step_ends_at_a_newton_stationary_point_of_the_objective():
+    """The state a single-partition step returns is where projected Newton
+    on Eq. 1 stops: a Newton step computed outside the solver -- numpy's
+    dense solve with the objective's own gradient and projected Hessian at
+    the returned state and the step's q~ -- is below epsilon_N h l, while at
+    the step's start state it is not (free fall and stacking contact)."""
+    sa = scenes.cube_stack()
+    sc = O.Scene(sa)
+    p = O.default_params(kappa_barrier=1e5)
+    dyn = sa.body_kind == scenes.KIND_DYNAMIC
+    contact = 0
+    for _ in range(14):
+        q0, v0 = sc.state()
+        st = sc.step(p)
+        assert st["status"] == 0
+        contact = max(contact, st["n_active_peak"])
+        q1, _ = sc.state()
+        qt = q0 + p.h * v0
+        qt[:, :3] += p.h * p.h * sa.gravity
+        tol = p.newton_tol * p.h * st["l"]
+        _, g1, H1 = sc.objective(p, q1[dyn], qt[dyn])
+        _, g0, H0 = sc.objective(p, q0[dyn], qt[dyn])
+        assert np.abs(np.linalg.solve(H1, g1)).max() < tol
+        assert np.abs(np.linalg.solve(H0, g0)).max() > 100 * tol
+    assert contact > 0
+
+
 def test_cube_resting_on_plane_balances_weight():
     """Vertex-plane equilibrium: at rest, -kB * sum_c b'(d_c) = m |g|."""
     sa = scenes.cube_stack(nx=1, ny=1, nz=1, bottom_gap=2e-4, jitter=0.0)

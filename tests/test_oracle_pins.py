@@ -457,18 +457,22 @@ def test_objective_gradient_fd_and_assembly_rebuilt_in_numpy():
     assert np.linalg.eigvalsh(H).min() > 0
 
 
-def test_step_ends_at_a_newton_stationary_point_of_the_objective():
+@pytest.mark.parametrize("solver,dims,steps", [("dense", (2, 2, 2), 14), ("pcg", (6, 5, 6), 8)])
+def test_step_ends_at_a_newton_stationary_point_of_the_objective(solver, dims, steps):
     """The state a single-partition step returns is where projected Newton
     on Eq. 1 stops: a Newton step computed outside the solver -- numpy's
     dense solve with the objective's own gradient and projected Hessian at
     the returned state and the step's q~ -- is below epsilon_N h l, while at
-    the step's start state it is not (free fall and stacking contact)."""
-    sa = scenes.cube_stack()
+    the step's start state it is not (free fall and stacking contact).  The
+    180-cube stack (2160 unknowns) takes the oracle's block-Jacobi PCG branch
+    (above 2000 unknowns), the 8-cube stack its dense Cholesky."""
+    sa = scenes.cube_stack(nx=dims[0], ny=dims[1], nz=dims[2])
+    assert (12 * sa.n_dynamic > 2000) == (solver == "pcg")
     sc = O.Scene(sa)
     p = O.default_params(kappa_barrier=1e5)
     dyn = sa.body_kind == scenes.KIND_DYNAMIC
     contact = 0
-    for _ in range(14):
+    for _ in range(steps):
         q0, v0 = sc.state()
         st = sc.step(p)
         assert st["status"] == 0

@@ -81,3 +81,17 @@ def test_sweep_reports_errors_without_raising():
     assert [r["fraction_of_capacity"] for r in rows] == [0.5, 2.0]
     assert [r["lambda_rps"] for r in rows] == [500.0, 2000.0]
     assert all(r["error"] == "RuntimeError: no device" for r in rows)
+
+
+def test_clock_summary_reads_reasons_and_median():
+    """The nvidia-smi sampler's summary: median SM clock under load, the
+    maximum clock, and every throttle reason seen active."""
+    import bench
+    c = bench.Clocks(0)
+    c.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 1900, 2070, 1398.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2000, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line"]
+    s = c.summary()
+    assert s["sm_mhz"] == 2000.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]

@@ -104,3 +104,42 @@ def test_every_status_code_has_its_own_text_and_null_arguments_are_rejected():
     assert L.abd_step(None, ctypes.byref(p), ctypes.byref(st)) == -1
     assert L.abd_state_get(None, None, None, 0) == -1
     assert L.abd_candidates_noalloc(None, None, None, 1e-3, None, 0, None) == -1
+
+
+def test_plain_c_program_links_and_calls_the_library(tmp_path):
+    """A C program built with gcc against include/abd.h links libabd.so and
+    calls its host-only entry points (no GPU needed): default parameters, the
+    load-balancing law, status texts, and an argument check."""
+    import subprocess
+    from paper_2605_15875_gb300 import build
+    lib = build.build()
+    src = tmp_path / "use.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "abd.h"
+int main(void) {
+    abd_step_params p = abd_step_params_default();
+    double tau[3] = {3.0, 1.0, 1.0}, delta[2], T[2];
+    int rc = abd_pd_update(3, tau, NULL, 0.5, 0.0, delta, T);
+    printf("%g %g %d %d\n", p.h, p.dhat, p.max_admm, rc);
+    printf("%.17g %.17g %.17g %.17g\n", T[0], T[1], delta[0], delta[1]);
+    printf("%s|%s\n", abd_status_string(ABD_OK), abd_status_string(ABD_E_PENETRATION));
+    printf("%d\n", abd_step(NULL, &p, NULL));
+    return 0;
+}
+''')
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(lib)
+    r = subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                        "-L", libdir, "-labd", f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    lines = out.stdout.splitlines()
+    assert lines[0].split() == ["0.01", "0.001", "200", "0"]
+    T0, T1, d0, d1 = map(float, lines[1].split())
+    assert T0 == 0.5 and T1 == 0.0  # (3 - 1) / (3 + 1), (1 - 1) / (1 + 1)
+    assert d0 == -0.25 and d1 == 0.0  # -(kp T): the plane moves toward the slower slab
+    assert lines[2] == "ok|penetration detected"
+    assert lines[3] == "-1"

@@ -113,6 +113,27 @@ def test_collision_conserves_linear_momentum(slabs):
     assert np.abs(q[:, 3:] - q0[:, 3:]).max() > 1e-4  # the off-centre hit rotates the bodies
 
 
+def test_frictionless_plane_keeps_tangential_velocity():
+    """Eq. 1 has no friction term and a ground-plane contact acts along the
+    plane's normal only: a cube landing on y = 0 while sliding at (0.5, 0.3)
+    in x and z keeps those velocities to rounding while its vertical
+    velocity goes to zero (a plane gradient leaking into another axis, or any
+    tangential drag, fails)."""
+    sa = scenes.cube_stack(nx=1, ny=1, nz=1, jitter=0.0)
+    v = np.zeros((1, 12))
+    v[0, 0], v[0, 2] = 0.5, 0.3
+    sa.body_v0 = np.ascontiguousarray(v)
+    sc = O.Scene(sa)
+    p = O.default_params()
+    active = 0
+    for _ in range(25):
+        st = sc.step(p)
+        active = max(active, st["n_active_peak"])
+        _, vv = sc.state()
+        assert abs(vv[0, 0] - 0.5) < 1e-12 and abs(vv[0, 2] - 0.3) < 1e-12
+    assert active > 0 and abs(vv[0, 1]) < 1e-9
+
+
 def _moved(sa, R, t):
     """The scene rigidly moved by x -> R x + t (R a signed axis permutation,
     so axis-aligned planes stay axis-aligned): q = (R p + t, R A), velocities

@@ -589,15 +589,21 @@ def test_admm_free_flight_converges_to_prediction():
 
 
 @pytest.mark.parametrize("slabs", [2, 3])
-def test_local_objectives_sum_to_global_at_consensus(slabs):
+@pytest.mark.parametrize("static_base", [False, True])
+def test_local_objectives_sum_to_global_at_consensus(slabs, static_base):
     """Eq. 3's weights split Eq. 1 exactly: at a consensus point (every
     replica at the body's q, so the augmented term is zero) the partitions'
     objectives sum to the single-partition objective, and so do their
-    gradients.  A touching row of six cubes (gaps 5e-4 < dhat, resting 5e-4 above
-    the plane) puts contacts between a shared and an internal body, between
-    two shared bodies and on the plane, so a wrong kappa_b or kappa_c (e.g.
-    counting partitions holding either body instead of both) fails."""
-    sa = scenes.cube_stack(nx=6, ny=1, nz=1, spacing=1.0005, bottom_gap=5e-4, jitter=0.0)
+    gradients.  A touching row of six cubes (gaps 5e-4 < dhat, resting 5e-4
+    above the plane) puts contacts between a shared and an internal body,
+    between two shared bodies and on the plane; with `static_base` a second
+    row rests on it and the first row is static, so contacts pair dynamic
+    and static bodies in both orders (static vertex on a dynamic face and the
+    reverse).  A wrong kappa_b or kappa_c (e.g. counting partitions holding
+    either body instead of both) fails."""
+    sa = scenes.cube_stack(nx=6, ny=2 if static_base else 1, nz=1, spacing=1.0005, bottom_gap=5e-4, jitter=0.0)
+    if static_base:
+        sa.body_kind = np.where(sa.body_q0[:, 1] < 1.0, scenes.KIND_STATIC, scenes.KIND_DYNAMIC).astype(np.int32)
     sc = O.Scene(sa)
     p = O.default_params(n_slabs=slabs, axis=0, kappa_barrier=1e5)
     m, _ = sc.partition(p)
@@ -611,6 +617,28 @@ def test_local_objectives_sum_to_global_at_consensus(slabs):
     # the barrier terms are active: the objective differs from inertia + orthogonality alone
     E_free, _, _ = sc.objective(O.default_params(kappa_barrier=1e-30), qd, qt, want_hess=False)
     assert E - E_free > 1e-3 * E
+    assert abs(Ep.sum() - E) <= 1e-12 * abs(E)
+    assert np.abs(gs - g.reshape(gs.shape)).max() <= 1e-12 * np.abs(g).max()
+
+
+def test_local_objectives_sum_to_global_with_static_mesh_contacts():
+    """The same split on the 16-sphere pile settled in its static box over
+    two slabs: contacts between spheres and with the box, where a pair with
+    a static body is weighted by the partitions holding the dynamic one."""
+    sa = scenes.sphere_grid_in_box(n=4, ny=2, nz=2, level=1, lowest=0.12, spacing=0.25)
+    sc = O.Scene(sa)
+    p = O.default_params(n_slabs=2, axis=0)
+    for _ in range(16):
+        st = sc.step(p)
+    assert st["n_shared"] > 0 and st["n_active_peak"] > 0
+    pk = O.default_params(n_slabs=2, axis=0, kappa_barrier=st["kappa_barrier"])
+    q, _ = sc.state()
+    qd = q[sa.body_kind == scenes.KIND_DYNAMIC]
+    qt = qd + 1e-4 * np.random.default_rng(0).normal(size=qd.shape)
+    Ep, gs = sc.local_objectives(pk, qd, qt)
+    E, g, _ = sc.objective(pk, qd, qt, want_hess=False)
+    E_free, _, _ = sc.objective(O.default_params(kappa_barrier=1e-30), qd, qt, want_hess=False)
+    assert E - E_free > 0.5 * E  # the barrier terms dominate
     assert abs(Ep.sum() - E) <= 1e-12 * abs(E)
     assert np.abs(gs - g.reshape(gs.shape)).max() <= 1e-12 * np.abs(g).max()
 

@@ -102,7 +102,7 @@ def lib():
         L.orc_candidates.restype = C.c_int64
         L.orc_objective.argtypes = [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_void_p, dp, C.c_void_p, C.c_void_p]
         L.orc_local_objectives.argtypes = [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_void_p,
-                                           C.c_int, C.c_void_p]
+                                           C.c_int, C.c_void_p, C.c_void_p]
         L.orc_mollifier.argtypes = [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
         L.orc_mollifier.restype = C.c_double
         _lib = L
@@ -286,18 +286,20 @@ class Scene:
             raise RuntimeError(f"objective failed: {rc}")
         return E.value, g, H
 
-    def local_objectives(self, params: Params, q_dyn, qtil_dyn):
+    def local_objectives(self, params: Params, q_dyn, qtil_dyn, want_hess=False):
         """Per-partition objectives F_i of Eq. 3 at the consensus point where
         every replica equals q_dyn (membership from the slab rule at the
-        scene's current state), and the sum of their gradients scattered to
-        the bodies.  Returns (E_parts [N], g_sum [n_dof, 12])."""
+        scene's current state), the sum of their gradients scattered to the
+        bodies and, with want_hess, the sum of their projected Hessians.
+        Returns (E_parts [N], g_sum [n_dof, 12], H_sum [12 n_dof]^2 or None)."""
         q, qt = _f64(q_dyn), _f64(qtil_dyn)
         E = np.zeros(64)
         g = np.zeros(q.shape)
-        n = lib().orc_local_objectives(self.h, C.byref(params), _p(q), _p(qt), _p(E), 64, _p(g))
+        H = np.zeros((q.size, q.size)) if want_hess else None
+        n = lib().orc_local_objectives(self.h, C.byref(params), _p(q), _p(qt), _p(E), 64, _p(g), _p(H))
         if n < 0:
             raise RuntimeError(f"local objectives failed: {n}")
-        return E[:n], g
+        return E[:n], g, H
 
     def step(self, params: Params):
         st = Stats()

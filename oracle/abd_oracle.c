@@ -1879,9 +1879,11 @@ int orc_objective(orc_scene *s, const orc_params *P, const double *q, const doub
  * qtil give every DOF body ([n_dof][12], body order); barrier stiffness
  * P->kappa_barrier.  E_parts[i] receives F_i (up to cap partitions),
  * g_sum[n_dof][12] the sum over partitions of the gradients of F_i scattered
- * to the bodies.  Returns the number of partitions, or a negative status. */
+ * to the bodies, H_sum (dense, 12 n_dof square, or NULL) the sum of their
+ * projected Hessians (rho = 0 here, so the augmented term adds nothing to
+ * any of them).  Returns the number of partitions, or a negative status. */
 int orc_local_objectives(orc_scene *s, const orc_params *P, const double *q, const double *qtil, double *E_parts,
-                         int cap, double *g_sum) {
+                         int cap, double *g_sum, double *H_sum) {
     int N = P->n_slabs < 1 ? 1 : P->n_slabs;
     uint64_t *mask = (uint64_t *)malloc(sizeof(uint64_t) * s->nb);
     int *dof = (int *)malloc(sizeof(int) * s->nb);
@@ -1900,23 +1902,40 @@ int orc_local_objectives(orc_scene *s, const orc_params *P, const double *q, con
             }
         }
         if (g_sum) memset(g_sum, 0, sizeof(double) * 12 * (size_t)k);
+        if (H_sum) memset(H_sum, 0, sizeof(double) * 144 * (size_t)k * k);
     }
+    size_t nd = 12 * (size_t)k;
     for (int i = 0; !rc && i < N; ++i) {
         local_t L;
         rc = local_init(&L, s, mask, i, qa, qt, P, P->kappa_barrier, 1.0);
         if (!rc) {
             memcpy(L.z, L.q, sizeof(double) * 12 * (size_t)L.ns);
-            for (int sl = 0; sl < L.ns; ++sl) L.rho[sl] = 1.0;
+            for (int sl = 0; sl < L.ns; ++sl) L.rho[sl] = 0.0;
             if (i < cap && E_parts) E_parts[i] = local_energy(&L, L.q);
-            if (g_sum) {
+            if (g_sum || H_sum) {
                 int n = 12 * L.ns;
                 double *gg = (double *)malloc(sizeof(double) * (n ? n : 1));
                 bsr_t H = {0};
                 H.diag = (double *)malloc(sizeof(double) * 144 * (size_t)(L.ns ? L.ns : 1));
                 H.rowhead = (int *)malloc(sizeof(int) * (L.ns ? L.ns : 1));
                 rc = (!gg || !H.diag || !H.rowhead) ? ORC_E_OOM : local_assemble(&L, L.q, gg, &H);
-                for (int sl = 0; !rc && sl < L.ns; ++sl)
+                for (int sl = 0; !rc && g_sum && sl < L.ns; ++sl)
                     for (int j = 0; j < 12; ++j) g_sum[12 * dof[L.body[sl]] + j] += gg[12 * sl + j];
+                if (!rc && H_sum) {
+                    for (int sl = 0; sl < L.ns; ++sl) {
+                        size_t r0 = 12 * (size_t)dof[L.body[sl]];
+                        for (int a = 0; a < 12; ++a)
+                            for (int c = 0; c < 12; ++c) H_sum[(r0 + a) * nd + r0 + c] += H.diag[144 * sl + 12 * a + c];
+                    }
+                    for (int o = 0; o < H.noff; ++o) {
+                        size_t ra = 12 * (size_t)dof[L.body[H.off[o].a]], rb = 12 * (size_t)dof[L.body[H.off[o].b]];
+                        for (int a = 0; a < 12; ++a)
+                            for (int c = 0; c < 12; ++c) {
+                                H_sum[(ra + a) * nd + rb + c] += H.off[o].blk[12 * a + c];
+                                H_sum[(rb + c) * nd + ra + a] += H.off[o].blk[12 * a + c];
+                            }
+                    }
+                }
                 free(gg); free(H.diag); free(H.rowhead); free(H.off); free(H.next);
             }
         }

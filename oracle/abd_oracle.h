@@ -87,10 +87,10 @@ int  orc_step(orc_scene *s, const orc_params *p, orc_stats *st);
 int  orc_partition(orc_scene *s, const orc_params *p, uint64_t *mask /* [B] */, double *w_out);
 int  orc_objective(orc_scene *s, const orc_params *p, const double *q, const double *qtil, double *E, double *g,
                    double *Hdense);
-/* per-partition objectives F_i (Eq. 3) at a consensus point and the sum of
- * their gradients; returns the partition count */
+/* per-partition objectives F_i (Eq. 3) at a consensus point and the sums of
+ * their gradients and projected Hessians; returns the partition count */
 int  orc_local_objectives(orc_scene *s, const orc_params *p, const double *q, const double *qtil, double *E_parts,
-                          int cap, double *g_sum);
+                          int cap, double *g_sum, double *H_sum);
 
 /* building blocks, exposed for the pins */
 int    orc_mass_properties(int nv, const double *xbar, int nt, const int32_t *tris, double density,

@@ -594,7 +594,7 @@ def test_local_objectives_sum_to_global_at_consensus(slabs, static_base):
     """Eq. 3's weights split Eq. 1 exactly: at a consensus point (every
     replica at the body's q, so the augmented term is zero) the partitions'
     objectives sum to the single-partition objective, and so do their
-    gradients.  A touching row of six cubes (gaps 5e-4 < dhat, resting 5e-4
+    gradients and projected Hessians.  A touching row of six cubes (gaps 5e-4 < dhat, resting 5e-4
     above the plane) puts contacts between a shared and an internal body,
     between two shared bodies and on the plane; with `static_base` a second
     row rests on it and the first row is static, so contacts pair dynamic
@@ -611,14 +611,15 @@ def test_local_objectives_sum_to_global_at_consensus(slabs, static_base):
     q, _ = sc.state()
     qd = q[sa.body_kind == scenes.KIND_DYNAMIC]
     qt = qd + 1e-3 * np.random.default_rng(0).normal(size=qd.shape)
-    Ep, gs = sc.local_objectives(p, qd, qt)
-    E, g, _ = sc.objective(p, qd, qt, want_hess=False)
+    Ep, gs, Hs = sc.local_objectives(p, qd, qt, want_hess=True)
+    E, g, H = sc.objective(p, qd, qt)
     assert len(Ep) == slabs and np.all(Ep > 0)
     # the barrier terms are active: the objective differs from inertia + orthogonality alone
     E_free, _, _ = sc.objective(O.default_params(kappa_barrier=1e-30), qd, qt, want_hess=False)
     assert E - E_free > 1e-3 * E
     assert abs(Ep.sum() - E) <= 1e-12 * abs(E)
     assert np.abs(gs - g.reshape(gs.shape)).max() <= 1e-12 * np.abs(g).max()
+    assert np.abs(Hs - H).max() <= 1e-12 * np.abs(H).max()
 
 
 def test_local_objectives_sum_to_global_with_static_mesh_contacts():
@@ -635,12 +636,13 @@ def test_local_objectives_sum_to_global_with_static_mesh_contacts():
     q, _ = sc.state()
     qd = q[sa.body_kind == scenes.KIND_DYNAMIC]
     qt = qd + 1e-4 * np.random.default_rng(0).normal(size=qd.shape)
-    Ep, gs = sc.local_objectives(pk, qd, qt)
-    E, g, _ = sc.objective(pk, qd, qt, want_hess=False)
+    Ep, gs, Hs = sc.local_objectives(pk, qd, qt, want_hess=True)
+    E, g, H = sc.objective(pk, qd, qt)
     E_free, _, _ = sc.objective(O.default_params(kappa_barrier=1e-30), qd, qt, want_hess=False)
     assert E - E_free > 0.5 * E  # the barrier terms dominate
     assert abs(Ep.sum() - E) <= 1e-12 * abs(E)
     assert np.abs(gs - g.reshape(gs.shape)).max() <= 1e-12 * np.abs(g).max()
+    assert np.abs(Hs - H).max() <= 1e-12 * np.abs(H).max()
 
 
 def test_admm_tracks_monolithic_per_step():

@@ -645,6 +645,19 @@ def test_local_objectives_sum_to_global_with_static_mesh_contacts():
     assert np.abs(Hs - H).max() <= 1e-12 * np.abs(H).max()
 
 
+def test_admm_rounds_grow_with_the_partition_count():
+    """Paper behaviour (Sec. 6, Multi-worker Scaling), not parity: more
+    partitions mean more shared bodies to agree on, so the 16-sphere pile
+    landing in its box needs more ADMM rounds in total on 4 slabs than on 2,
+    and a single partition needs exactly one round per step."""
+    sa = scenes.sphere_grid_in_box(n=4, ny=2, nz=2, level=1, lowest=0.12, spacing=0.25)
+    rounds = {}
+    for n in (1, 2, 4):
+        sc = O.Scene(sa)
+        rounds[n] = sum(sc.step(O.default_params(n_slabs=n, axis=0))["admm_iters"] for _ in range(16))
+    assert rounds[1] == 16 and rounds[1] < rounds[2] < rounds[4]
+
+
 def test_admm_tracks_monolithic_per_step():
     """The converged consensus state lies within O(theta h l) of the
     single-partition solution from the same start (the q* comparison)."""

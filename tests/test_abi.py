@@ -45,6 +45,17 @@ def test_oracle_is_not_imported_by_the_product():
                 assert "import oracle" not in txt and "from oracle" not in txt and "abd_oracle" not in txt, f
 
 
+def test_oracle_shares_no_code_with_the_library():
+    """The oracle includes only its own header and the C library, and its
+    Python wrapper imports nothing from the product package."""
+    odir = os.path.join(ROOT, "oracle")
+    c = open(os.path.join(odir, "abd_oracle.c")).read() + open(os.path.join(odir, "abd_oracle.h")).read()
+    includes = set(re.findall(r'#include\s*[<"]([^>"]+)[>"]', c))
+    assert includes <= {"abd_oracle.h", "math.h", "stdio.h", "stdlib.h", "string.h", "stdint.h"}, includes
+    py = open(os.path.join(odir, "__init__.py")).read()
+    assert "paper_2605_15875_gb300" not in py and "libabd.so" not in py
+
+
 def test_ctypes_struct_layouts_match_the_header(tmp_path):
     """Sizes of the ABI structs as gcc lays them out from include/abd.h equal
     the ctypes mirrors used by the binding."""

@@ -30,8 +30,7 @@ WORKLOAD = "admm4_slabs_512_icosphereL2_open_box"
 PLANES = [-0.6, 0.0, 0.6]
 METRIC = "ABD-IPC body-steps/s vs plain FP64 GPU at oracle tol; p50/p99 step latency"
 # DRAM bytes (read + write) per launch from one ncu capture of the kernel as it
-# stands (profiles/hot_kernels_admm4_512_icosphere_contact_step21.md); a kernel
-# changed since its capture has no entry.
+# stands; a kernel changed since its capture has no entry.
 TRAFFIC = {"l2_swept": 15.626496e6}
 
 

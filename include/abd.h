@@ -150,7 +150,12 @@ typedef struct {
 /* --- scene ---------------------------------------------------------------- */
 
 /* Copy the description to the device and compute per-body constants (mass,
- * second moment, volume, edges).  `cuda_stream` is a cudaStream_t (NULL: the
+ * second moment, volume, edges).  The affine degrees of freedom q = (p, A),
+ * x = A xbar + p, and the mass matrix of each body follow Sec. 3 (the
+ * affine-body setting of Eq. 1, whose inertia term uses M): mass and second
+ * moment are integrated over the closed mesh, and the rest vertices are
+ * recentred at the centre of mass so that M = diag(m I3, S, S, S) in q order.
+ * `cuda_stream` is a cudaStream_t (NULL: the
  * legacy default stream) on which every later call on this scene enqueues
  * work; the current CUDA device becomes the scene's device.
  * Errors: ABD_E_INVALID (bad indices, open or inverted dynamic or kinematic
@@ -190,7 +195,13 @@ int abd_partition_masks(abd_scene *s, double h, uint64_t *mask, double *w_out);
  * kept as computed, so the caller can inspect or restore it. */
 int abd_step(abd_scene *s, const abd_step_params *p, abd_step_stats *stats);
 
-/* Host copies of the state (q, qdot), [B][12] each; either may be NULL. */
+/* Host copies of the state (q, qdot), [B][12] each; either may be NULL.  This
+ * is the state at the end of a frame of Alg. 1: shared bodies at their
+ * consensus z, internal bodies at their only replica, and the velocity
+ * qdot = (q^{t+1} - q^t) / h of the merge.  Arrays are caller-owned host
+ * memory of n_bodies rows (ABD_E_INVALID when n_bodies differs from the
+ * scene's body count); abd_state_set copies the caller's arrays to the device
+ * and takes effect at the next step. */
 int abd_state_get(const abd_scene *s, double *q, double *v, int64_t n_bodies);
 int abd_state_set(abd_scene *s, const double *q, const double *v, int64_t n_bodies);
 
@@ -222,9 +233,13 @@ int abd_candidates(abd_scene *s, const double *x0, const double *x1, double dhat
  *   first call on a device looks up that array's address; make that first call
  *   before any stream capture on the device.  All calls share the array: calls
  *   whose work overlaps on the GPU (other host threads, other streams) race.
- *   Limits: at most 131072 bodies (ABD_E_INVALID beyond) and about 4 million
- *   overlapping body pairs (ABD_E_PAIR_OVERFLOW beyond), each with a message
- *   in abd_last_error().  Blocks until done. */
+ *   Limits: at most 131072 bodies (ABD_E_INVALID beyond) and
+ *   (32 MiB - 64 B x bodies - about 1.5 KiB of headers) / 8 overlapping body
+ *   pairs (ABD_E_PAIR_OVERFLOW beyond): about 4.19 million for small scenes,
+ *   3.1 million at the body limit; each error comes with a message in
+ *   abd_last_error().  When more than `cap` candidates exist, the first `cap`
+ *   found are written, *n_out receives the full count and the call returns
+ *   ABD_OK.  Blocks until done. */
 int abd_candidates_noalloc(abd_scene *s, const double *x0, const double *x1, double dhat, int32_t *out, int64_t cap,
                            int64_t *n_out);
 

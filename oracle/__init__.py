@@ -105,6 +105,13 @@ def lib():
                                            C.c_int, C.c_void_p, C.c_void_p]
         L.orc_mollifier.argtypes = [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
         L.orc_mollifier.restype = C.c_double
+        L.orc_rho_update.argtypes = [C.c_double] * 8 + [dp]
+        L.orc_rho_update.restype = C.c_double
+        L.orc_local_gradient.argtypes = [C.c_void_p, C.POINTER(Params), C.c_int, C.c_void_p, C.c_void_p, dp,
+                                         C.c_void_p]
+        L.orc_admm_trace.argtypes = [C.c_void_p, C.c_void_p, C.c_int64]
+        L.orc_admm_trace_count.argtypes = [C.c_void_p]
+        L.orc_admm_trace_count.restype = C.c_int64
         _lib = L
     return _lib
 
@@ -180,6 +187,17 @@ def ccd(is_ee, X, dX, s=0.1, c=0.9):
 
 def ccd_plane(d0, dd, s=0.1):
     return lib().orc_ccd_plane(d0, dd, s)
+
+
+def rho_update(r, s, rho, rho0, tau=2.0, mu=5.0, sigma_min=1e-3, sigma_max=1e3):
+    """Residual-driven penalty of one shared body (Sec. 4.3): (rho_new,
+    u_scale), u_scale = rho / rho_new being the factor of the scaled dual."""
+    sc = C.c_double()
+    nw = lib().orc_rho_update(r, s, rho, rho0, tau, mu, sigma_min, sigma_max, C.byref(sc))
+    return nw, sc.value
+
+
+TRACE_REC = 68  # doubles per ADMM trace record (oracle/abd_oracle.h)
 
 
 # ---------------------------------------------------------------- scene + step
@@ -300,6 +318,33 @@ class Scene:
         if n < 0:
             raise RuntimeError(f"local objectives failed: {n}")
         return E[:n], g, H
+
+    def local_gradient(self, params: Params, part, q_dyn, qtil_dyn):
+        """(F_i, dF_i/dq [n_dof, 12]) of partition `part` (Eq. 3, no consensus
+        term) at the replica configuration q_dyn; barrier stiffness
+        params.kappa_barrier, membership from the slab rule at the current
+        state."""
+        q, qt = _f64(q_dyn), _f64(qtil_dyn)
+        E = C.c_double()
+        g = np.zeros(q.shape)
+        rc = lib().orc_local_gradient(self.h, C.byref(params), int(part), _p(q), _p(qt), C.byref(E), _p(g))
+        if rc != 0:
+            raise RuntimeError(f"local gradient failed: {rc}")
+        return E.value, g
+
+    def step_traced(self, params: Params, cap: int = 20000):
+        """One step with the ADMM trace on: (stats, records [n, TRACE_REC]),
+        one record per (continuing round, shared body, replica)."""
+        buf = np.zeros((cap, TRACE_REC))
+        lib().orc_admm_trace(self.h, _p(buf), cap)
+        try:
+            st = self.step(params)
+            n = lib().orc_admm_trace_count(self.h)
+        finally:
+            lib().orc_admm_trace(self.h, None, 0)
+        if n > cap:
+            raise RuntimeError(f"trace of {n} records exceeds cap {cap}")
+        return st, buf[:n].copy()
 
     def step(self, params: Params):
         st = Stats()

@@ -591,6 +591,9 @@ struct orc_scene {
     double *psg, *poff;
     double g[3];
     int64_t V, T, E;
+    /* optional ADMM trace (orc_admm_trace): ORC_TRACE_REC doubles per record */
+    double *trace;
+    int64_t trace_cap, trace_n;
 };
 
 static int cmp_edge(const void *a, const void *b) {
@@ -1558,6 +1561,63 @@ static double scene_min_distance(orc_scene *s, double dhat) {
     return md;
 }
 
+/* Residual-driven penalty of one shared body (Sec. 4.3).  r is its primal
+ * residual (Eq. 9) and s its dual residual (Eq. 10): rho grows by the factor
+ * tau when r > mu s, shrinks by tau when s > mu r, and stays otherwise (the
+ * equality cases included); the result is clamped to
+ * [sigma_min rho0, sigma_max rho0], rho0 = beta m being the body's initial
+ * penalty.  The scaled dual u = y / rho must carry the unscaled dual y across
+ * the change (Boyd et al. 2011, Sec. 3.4.1), so the caller multiplies every
+ * replica's u by *u_scale = rho / rho_new. */
+double orc_rho_update(double r, double s, double rho, double rho0, double tau, double mu, double sigma_min,
+                      double sigma_max, double *u_scale) {
+    double nw = rho;
+    if (r > mu * s) nw = rho * tau;
+    else if (s > mu * r) nw = rho / tau;
+    nw = dmin(dmax(nw, sigma_min * rho0), sigma_max * rho0);
+    if (u_scale) *u_scale = rho / nw;
+    return nw;
+}
+
+int orc_admm_trace(orc_scene *s, double *buf, int64_t cap) {
+    if (!s || cap < 0 || (cap > 0 && !buf)) return ORC_E_INVALID;
+    s->trace = buf;
+    s->trace_cap = cap;
+    s->trace_n = 0;
+    return ORC_OK;
+}
+
+int64_t orc_admm_trace_count(const orc_scene *s) { return s ? s->trace_n : 0; }
+
+/* Trace records of one round (see orc_admm_trace): with b >= 0 one record
+ * per replica of shared body b (its residuals, the penalty before and after
+ * the update, its z of this and the previous round, u before and after the
+ * rescale); with b < 0 one record per internal slot of every partition (q
+ * only), so that a record set holds each partition's whole configuration. */
+static void admm_trace_round(orc_scene *s, local_t *parts, int N, int k, int b, double r, double sb, double nw,
+                             double scale, const double *zprev, const double *z) {
+    for (int i = 0; i < N; ++i)
+        for (int sl = 0; sl < parts[i].ns; ++sl) {
+            int body = parts[i].body[sl];
+            if (b >= 0 ? body != b : parts[i].shared[sl]) continue;
+            if (s->trace_n < s->trace_cap) {
+                double *rec = s->trace + ORC_TRACE_REC * s->trace_n;
+                memset(rec, 0, sizeof(double) * ORC_TRACE_REC);
+                rec[0] = k; rec[1] = body; rec[2] = i; rec[3] = b >= 0;
+                memcpy(rec + 8, parts[i].q + 12 * sl, sizeof(double) * 12);
+                if (b >= 0) {
+                    const double *u = parts[i].u + 12 * sl;
+                    rec[4] = parts[i].rho[sl]; rec[5] = nw; rec[6] = r; rec[7] = sb;
+                    memcpy(rec + 20, zprev + 12 * b, sizeof(double) * 12);
+                    memcpy(rec + 32, z + 12 * b, sizeof(double) * 12);
+                    memcpy(rec + 44, u, sizeof(double) * 12);
+                    for (int j = 0; j < 12; ++j) rec[56 + j] = u[j] * scale;
+                }
+            }
+            ++s->trace_n;
+        }
+}
+
 /* One time step (Alg. 1 with every partition on this thread):
  *   q~ (O2); partition (O7); z = q~, u = 0, rho = beta m;
  *   k = 1..K+1: for k > 1 consensus z (Eq. 6), dual u (Eq. 7), residuals
@@ -1697,22 +1757,23 @@ static int step_once(orc_scene *s, const orc_params *P, orc_stats *st) {
                 double tol = P->theta * P->h * l;
                 if (dinf < tol && rinf < tol && sinf < tol && merge_ok) { converged = 1; free(rb); break; }
                 if (k == K + 1) { free(rb); break; }
-                if (P->rho_adaptive) {
-                    for (int b = 0; b < nb; ++b) {
-                        if (!is_dof(s->kind[b]) || popcount64(mask[b]) < 2) continue;
-                        double r = rb[b], sb = sbody[b], old = rhob[b], nw = old;
-                        if (r > P->mu * sb) nw = old * P->tau;
-                        else if (sb > P->mu * r) nw = old / P->tau;
-                        nw = dmin(dmax(nw, P->sigma_min * rho0[b]), P->sigma_max * rho0[b]);
-                        rhob[b] = nw;
-                        for (int i = 0; i < N; ++i) {
-                            int sl = parts[i].sob[b];
-                            if (sl < 0) continue;
-                            for (int j = 0; j < 12; ++j) parts[i].u[12 * sl + j] *= old / nw;
-                            parts[i].rho[sl] = nw;
-                        }
+                /* rho update (Sec. 4.3) per shared body, recorded first when tracing */
+                for (int b = 0; b < nb; ++b) {
+                    if (!is_dof(s->kind[b]) || popcount64(mask[b]) < 2) continue;
+                    double scale = 1.0;
+                    double nw = P->rho_adaptive ? orc_rho_update(rb[b], sbody[b], rhob[b], rho0[b], P->tau, P->mu,
+                                                                 P->sigma_min, P->sigma_max, &scale)
+                                                : rhob[b];
+                    if (s->trace) admm_trace_round(s, parts, N, k, b, rb[b], sbody[b], nw, scale, zprev, z);
+                    rhob[b] = nw;
+                    for (int i = 0; i < N; ++i) {
+                        int sl = parts[i].sob[b];
+                        if (sl < 0) continue;
+                        for (int j = 0; j < 12; ++j) parts[i].u[12 * sl + j] *= scale;
+                        parts[i].rho[sl] = nw;
                     }
                 }
+                if (s->trace) admm_trace_round(s, parts, N, k, -1, 0.0, 0.0, 0.0, 1.0, zprev, z);
                 free(rb);
                 for (int i = 0; i < N; ++i)
                     for (int sl = 0; sl < parts[i].ns; ++sl)
@@ -1943,4 +2004,56 @@ int orc_local_objectives(orc_scene *s, const orc_params *P, const double *q, con
     }
     free(mask); free(dof); free(qa); free(qt);
     return rc ? rc : N;
+}
+
+/* Gradient of partition `part`'s local objective F_i (Eq. 3: inertia and
+ * orthogonality of each of its slots weighted 1/kappa_b, contacts 1/kappa_c,
+ * plane contacts 1/kappa_b; no consensus term) at the replica configuration
+ * q ([n_dof][12], body order: bodies of the partition take their rows, the
+ * others are ignored), with predicted state qtil and barrier stiffness
+ * P->kappa_barrier.  Membership is the slab rule at the scene's current
+ * state.  g receives [n_dof][12], zero rows for bodies outside the partition;
+ * *E the value of F_i (either may be NULL). */
+int orc_local_gradient(orc_scene *s, const orc_params *P, int part, const double *q, const double *qtil, double *E,
+                       double *g) {
+    int N = P->n_slabs < 1 ? 1 : P->n_slabs;
+    if (part < 0 || part >= N) return ORC_E_INVALID;
+    uint64_t *mask = (uint64_t *)malloc(sizeof(uint64_t) * s->nb);
+    int *dof = (int *)malloc(sizeof(int) * s->nb);
+    double *qa = (double *)calloc(12 * (size_t)s->nb, sizeof(double)), *qt = (double *)calloc(12 * (size_t)s->nb, sizeof(double));
+    int rc = (!mask || !dof || !qa || !qt) ? ORC_E_OOM : ORC_OK, k = 0;
+    if (!rc) rc = orc_partition(s, P, mask, NULL);
+    if (!rc) {
+        memcpy(qa, s->q, sizeof(double) * 12 * s->nb);
+        memcpy(qt, s->q, sizeof(double) * 12 * s->nb);
+        for (int b = 0; b < s->nb; ++b) {
+            dof[b] = -1;
+            if (is_dof(s->kind[b])) {
+                memcpy(qa + 12 * b, q + 12 * k, sizeof(double) * 12);
+                memcpy(qt + 12 * b, qtil + 12 * k, sizeof(double) * 12);
+                dof[b] = k++;
+            }
+        }
+        if (g) memset(g, 0, sizeof(double) * 12 * (size_t)k);
+        local_t L;
+        rc = local_init(&L, s, mask, part, qa, qt, P, P->kappa_barrier, 1.0);
+        if (!rc) {
+            for (int sl = 0; sl < L.ns; ++sl) L.rho[sl] = 0.0;
+            if (E) *E = local_energy(&L, L.q);
+            if (g) {
+                int n = 12 * L.ns;
+                double *gg = (double *)malloc(sizeof(double) * (n ? n : 1));
+                bsr_t H = {0};
+                H.diag = (double *)malloc(sizeof(double) * 144 * (size_t)(L.ns ? L.ns : 1));
+                H.rowhead = (int *)malloc(sizeof(int) * (L.ns ? L.ns : 1));
+                rc = (!gg || !H.diag || !H.rowhead) ? ORC_E_OOM : local_assemble(&L, L.q, gg, &H);
+                for (int sl = 0; !rc && sl < L.ns; ++sl)
+                    for (int j = 0; j < 12; ++j) g[12 * dof[L.body[sl]] + j] = gg[12 * sl + j];
+                free(gg); free(H.diag); free(H.rowhead); free(H.off); free(H.next);
+            }
+        }
+        local_free(&L);
+    }
+    free(mask); free(dof); free(qa); free(qt);
+    return rc;
 }

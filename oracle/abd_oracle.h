@@ -92,7 +92,29 @@ int  orc_objective(orc_scene *s, const orc_params *p, const double *q, const dou
 int  orc_local_objectives(orc_scene *s, const orc_params *p, const double *q, const double *qtil, double *E_parts,
                           int cap, double *g_sum, double *H_sum);
 
+/* gradient (and value) of one partition's F_i (Eq. 3, no consensus term) at a
+ * replica configuration q ([n_dof][12]); g gets [n_dof][12] */
+int  orc_local_gradient(orc_scene *s, const orc_params *p, int part, const double *q, const double *qtil, double *E,
+                        double *g);
+
+/* ADMM trace: while set, every round k >= 2 that continues to a penalty
+ * update (Sec. 4.3) appends records of ORC_TRACE_REC doubles: one per replica
+ * of each shared body, then one per internal slot of each partition:
+ *   [0] k  [1] body  [2] partition  [3] 1 shared, 0 internal
+ *   [4] rho used by the last local solves  [5] rho after the update
+ *   [6] r_b (Eq. 9)  [7] s_b (Eq. 10)  [8..19] the replica's q
+ *   [20..31] z_b of round k-1  [32..43] z_b (Eq. 6)
+ *   [44..55] u after the dual update (Eq. 7)  [56..67] u after the rescale
+ * (fields 4..7 and 20..67 are 0 for internal slots).  Records beyond cap are
+ * counted, not written.  buf NULL, cap 0: off. */
+#define ORC_TRACE_REC 68
+int  orc_admm_trace(orc_scene *s, double *buf, int64_t cap);
+int64_t orc_admm_trace_count(const orc_scene *s);
+
 /* building blocks, exposed for the pins */
+/* residual-driven penalty of one shared body (Sec. 4.3); *u_scale = rho / rho_new */
+double orc_rho_update(double r, double s, double rho, double rho0, double tau, double mu, double sigma_min,
+                      double sigma_max, double *u_scale);
 int    orc_mass_properties(int nv, const double *xbar, int nt, const int32_t *tris, double density,
                            double *m, double *com, double *S9, double *V);
 double orc_orth(const double *q12, double kappa, double V, double *g12, double *H144);

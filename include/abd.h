@@ -145,6 +145,12 @@ typedef struct {
      * the whole step */
     double t_solve_ms, t_coll_ms, t_sync_ms, t_total_ms;
     int64_t kernel_launches;       /* kernels of this library launched by the step */
+    int32_t pcg_cluster;           /* largest thread-block cluster size of the step's PCG launches */
+    int32_t pcg_unstaged;          /* 1: some PCG CTA read off-diagonal entries that did not fit in its
+                                      shared memory from the owners' shared memory directly */
+    int32_t list_redo;             /* Newton iterations redone because a pair list outgrew its buffer
+                                      (the buffer is grown and the iteration repeated from its start) */
+    int32_t reserved0;
 } abd_step_stats;
 
 /* --- scene ---------------------------------------------------------------- */
@@ -194,6 +200,15 @@ int abd_partition_masks(abd_scene *s, double h, uint64_t *mask, double *w_out);
  * vertex-plane pair at distance <= 0 (stats->min_distance); the state is
  * kept as computed, so the caller can inspect or restore it. */
 int abd_step(abd_scene *s, const abd_step_params *p, abd_step_stats *stats);
+
+/* Initial capacity, in pair records, of the scene's device pair lists
+ * (candidates, active pairs, line-search pairs; the cluster-pair list gets
+ * four times as many).  Lists grow by themselves when a count exceeds its
+ * buffer (the Newton iteration is then redone, abd_step_stats.list_redo), so
+ * this only trades memory against redone iterations; values below 16 are
+ * raised to 16.  The library's own service, not a step of the method.
+ * ABD_E_INVALID for pairs < 0. */
+int abd_scene_reserve(abd_scene *s, int64_t pairs);
 
 /* Host copies of the state (q, qdot), [B][12] each; either may be NULL.  This
  * is the state at the end of a frame of Alg. 1: shared bodies at their

@@ -52,7 +52,8 @@ class StepStats(C.Structure):
                 ("r_inf", C.c_double), ("s_inf", C.c_double), ("delta_inf", C.c_double),
                 ("min_distance", C.c_double), ("l", C.c_double), ("kappa_barrier", C.c_double), ("w", C.c_double),
                 ("t_solve_ms", C.c_double), ("t_coll_ms", C.c_double), ("t_sync_ms", C.c_double),
-                ("t_total_ms", C.c_double), ("kernel_launches", C.c_int64)]
+                ("t_total_ms", C.c_double), ("kernel_launches", C.c_int64), ("pcg_cluster", C.c_int32),
+                ("pcg_unstaged", C.c_int32), ("list_redo", C.c_int32), ("reserved0", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,7 +83,7 @@ EXPORTS = ["abd_scene_create", "abd_scene_destroy", "abd_scene_counts", "abd_bod
            "abd_candidates", "abd_profile", "abd_kernel_stats", "abd_step_params_default", "abd_status_string",
            "abd_last_error", "abd_candidates_noalloc", "abd_partition_get", "abd_server_create",
            "abd_server_submit", "abd_server_poll", "abd_server_wait", "abd_server_result", "abd_server_latencies",
-           "abd_server_error", "abd_server_destroy", "abd_partition_planes", "abd_pd_update"]
+           "abd_server_error", "abd_server_destroy", "abd_partition_planes", "abd_pd_update", "abd_scene_reserve"]
 
 _lib = None
 
@@ -121,6 +122,7 @@ def load(path: Optional[str] = None):
     i32p = C.POINTER(C.c_int32)
     L.abd_partition_get.argtypes = [vp, C.c_int32, vp, C.c_int32, i32p, vp, C.c_int32, i32p]
     L.abd_partition_planes.argtypes = [vp, vp, C.c_int32, i32p]
+    L.abd_scene_reserve.argtypes = [vp, i64]
     L.abd_pd_update.argtypes = [C.c_int32, vp, vp, C.c_double, C.c_double, vp, vp]
     L.abd_server_create.argtypes = [C.POINTER(ServerDesc), C.POINTER(vp)]
     L.abd_server_submit.argtypes = [vp, C.POINTER(SceneDesc), vp, vp, C.c_int32, C.POINTER(i64)]
@@ -247,6 +249,9 @@ class Scene:
         self._check(self.L.abd_partition_get(self.h, part, _p(b), n.value, C.byref(n), _p(sh), ns.value,
                                              C.byref(ns)), "abd_partition_get")
         return b[:n.value], sh[:ns.value]
+
+    def reserve(self, pairs):
+        self._check(self.L.abd_scene_reserve(self.h, int(pairs)), "abd_scene_reserve")
 
     def step(self, params: Optional[StepParams] = None) -> dict:
         params = default_params() if params is None else params

@@ -23,6 +23,12 @@ namespace abd {
 
 constexpr int kMaxPlanes = 8;
 constexpr int kMaxParts = 64;
+// Layout of the PCG status words (w.pcg_sc, ints): iterations per partition,
+// the overflow word, a flag set when some CTA read off-diagonal entries that
+// did not fit in its shared memory, then the off-diagonal CSR entries of each
+// partition (twice its off-diagonal blocks).
+constexpr int kPcgOver = kMaxParts, kPcgUnstaged = kMaxParts + 1, kPcgNent = kMaxParts + 2;
+constexpr int kPcgWords = 2 * kMaxParts + 2;
 constexpr int kLS = 4;  // trial step sizes evaluated per line-search pass
 
 struct Planes {
@@ -192,6 +198,7 @@ struct abd_scene {
     size_t pinned_bytes = 0;
     IterGraph ig;
     PcgTune pcg_tune[2];  // [0] FP32 blocks, [1] FP64 blocks
+    int pcg_cs_last = 0;  // cluster size of the last PCG launch (captured or direct)
     // profiling
     bool prof = false;
     int64_t n_launches = 0;

@@ -40,7 +40,7 @@ struct PcgClArgs {
     double *x;
     double tol2;
     int max_it;
-    int *iters;           // [NP] iterations used
+    int *iters;           // PCG status words (kPcg* layout): iterations per partition, flags, entries
 };
 
 // Dynamic shared memory of one CTA owning m slots: p, Ap, r, z, x (all T)
@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
     unsigned char *tail = (unsigned char *)(Ps + 144 * m);
 
     const bool active = A.part[part].active != 0 && n > 0;
+    if (rank == 0 && threadIdx.x == 0) A.iters[kPcgNent + part] = active ? A.rowoff[s1] - A.rowoff[s0] : 0;
     if (!active) {
         for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) A.x[12 * (int64_t)my0 + e] = 0.0;
         if (rank == 0 && threadIdx.x == 0) A.iters[part] = 0;
@@ -198,6 +199,7 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
     rz = R(0);
     for (int q = 0; q < CS; ++q) { r0 += red[16 + 2 * q]; rz += red[17 + 2 * q]; unstaged += red[48 + q]; }
     const bool need_sync3 = unstaged > R(0);  // some CTA reads owners' p directly
+    if (need_sync3 && rank == 0 && threadIdx.x == 0) A.iters[kPcgUnstaged] = 1;
     // neighbours' p (= z) of the staged entries
     for (int e = threadIdx.x; e < 12 * es; e += blockDim.x) {
         int j = e / 12, i = e % 12, nb = enb[j];
@@ -392,6 +394,7 @@ static int launch_T(abd_scene *s, const abd_step_params *p) {
         cudaEventCreate(&tu.a);
         cudaEventCreate(&tu.b);
     }
+    s->pcg_cs_last = CS;
     cudaEvent_t ea, eb;
     prof_begin(s, "pcg", 0, &ea, &eb);
     if (timed) cudaEventRecord(tu.a, s->stream);
@@ -425,8 +428,8 @@ void pcg_tune_observe(abd_scene *s, int64_t iterations) {
     }
 }
 
-// Iterations per partition land in w.pcg_sc ([kMaxParts] ints) for the
-// caller's per-iteration status read.
+// Iterations and CSR entries per partition land in w.pcg_sc (kPcg* layout)
+// for the caller's per-iteration status read.
 int launch_pcg_async(abd_scene *s, int precision, const abd_step_params *p) {
     return precision == ABD_MIXED ? launch_T<float>(s, p) : launch_T<double>(s, p);
 }

@@ -462,6 +462,16 @@ extern "C" int abd_partition(abd_scene *s, const abd_partition_desc *d) {
     return ABD_OK;
 }
 
+extern "C" int abd_scene_reserve(abd_scene *s, int64_t pairs) {
+    if (!s || pairs < 0) return ABD_E_INVALID;
+    int64_t n = std::max<int64_t>(pairs, 16);
+    World &w = s->w;
+    w.cap_cand = w.cap_act = w.cap_ls = n;
+    w.cap_cp = 4 * n;
+    ++w.gen;  // buffers are re-sized at the next step; captured graphs go stale
+    return ABD_OK;
+}
+
 extern "C" int abd_partition_planes(const abd_scene *s, double *planes, int32_t cap, int32_t *n) {
     if (!s || !n || cap < 0) return ABD_E_INVALID;
     const std::vector<double> &src = s->slab_planes.size() == (size_t)std::max(0, s->n_slabs - 1) && s->n_slabs > 1

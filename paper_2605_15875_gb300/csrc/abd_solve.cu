@@ -492,7 +492,8 @@ int write_parts(abd_scene *s, const std::vector<PartState> &ps) {
 struct Status {
     Counters c;
     int pcg_iters[kMaxParts];
-    int pcg_over, pcg_nnz2;
+    int pcg_over, pcg_unstaged;
+    int pcg_nent[kMaxParts];  // off-diagonal CSR entries of each partition
     int csr_total;  // entries of the off-diagonal row CSR (twice the blocks)
     unsigned long long n_moll;  // mollified edge-edge pairs assembled by the warp kernel
     PartState part[kMaxParts];
@@ -513,7 +514,7 @@ Status *pinned_status(abd_scene *s) {
 int enqueue_status(abd_scene *s, Status *h) {
     World &w = s->w;
     cudaMemcpyAsync(&h->c, w.ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, s->stream);
-    cudaMemcpyAsync(h->pcg_iters, w.pcg_sc.p, sizeof(int) * (kMaxParts + 2), cudaMemcpyDeviceToHost, s->stream);
+    cudaMemcpyAsync(h->pcg_iters, w.pcg_sc.p, sizeof(int) * kPcgWords, cudaMemcpyDeviceToHost, s->stream);
     cudaMemcpyAsync(h->part, w.part.p, sizeof(PartState) * w.NP, cudaMemcpyDeviceToHost, s->stream);
     if (s->prof && w.S_dyn > 0) {
         cudaMemcpyAsync(&h->csr_total, P<int>(w.rowoff) + w.S_dyn, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
@@ -541,7 +542,7 @@ int ensure_lists(Ctx &C) {
               dbuf_ensure(w.rowcnt, 4 * (size_t)(w.S_dyn + 2)) && dbuf_ensure(w.rowoff, 4 * (size_t)(w.S_dyn + 2)) &&
               dbuf_ensure(w.rowcur, 4 * (size_t)(w.S_dyn + 2)) && dbuf_ensure(w.ent, 16 * (size_t)w.cap_l1) &&
               dbuf_ensure(w.diag, tb * 144 * (size_t)(w.S_dyn ? w.S_dyn : 1)) &&
-              dbuf_ensure(w.pcg_sc, 4 * (size_t)kMaxParts + 64) && dbuf_ensure(C.alphas, 8 * (kLS + 1) * kMaxParts) &&
+              dbuf_ensure(w.pcg_sc, 4 * (size_t)kPcgWords) && dbuf_ensure(C.alphas, 8 * (kLS + 1) * kMaxParts) &&
               dbuf_ensure(C.nh0, 4 * kMaxParts) && dbuf_ensure(C.decided, 4 * kMaxParts);
     return ok ? ABD_OK : set_err(s, ABD_E_OOM, "pair lists");
 }
@@ -569,7 +570,7 @@ int enqueue_iteration(Ctx &C, bool static_bp, Status *hs) {
     int *d_iters = P<int>(w.pcg_sc);
     int rc;
     cudaMemsetAsync(&dc->bad, 0, sizeof(int), s->stream);
-    cudaMemsetAsync(d_iters, 0, sizeof(int) * (kMaxParts + 2), s->stream);
+    cudaMemsetAsync(d_iters, 0, sizeof(int) * kPcgWords, s->stream);
     // active set at q: static broad phase on the first iteration, then the
     // previous line-search list (q lies on that swept path)
     if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x), nullptr, 0))) return rc;
@@ -606,7 +607,7 @@ int enqueue_iteration(Ctx &C, bool static_bp, Status *hs) {
                    P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->pending);
     }
     ABD_LAUNCH(s, k_check_bad, 1, 1, 0, s->stream, dc, w.cap_l1, w.cap_cand, w.cap_act, w.cap_ls, w.cap_cp,
-               d_iters + kMaxParts);
+               d_iters + kPcgOver);
     ABD_LAUNCH(s, k_update_q, grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream, w.S_dyn,
                P<int>(w.slot_part), P<PartState>(w.part), P<int>(C.decided), dc, P<double>(w.dq), P<double>(w.q));
     ABD_LAUNCH(s, k_mark_updated, 1, 64, 0, s->stream, w.NP, P<int>(C.decided), dc);
@@ -698,6 +699,7 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         if (graphed) prof_graph_replayed(s);
         if (hs->c.bad) {
             // lists outgrew their buffers: grow, restore the partition state, redo
+            ++C.st->list_redo;
             grow_lists(w, hs->c, hs->pcg_over != 0);
             if ((rc = ensure_lists(C)) || (rc = write_parts(s, ps))) return rc;
             static_bp = true;
@@ -725,15 +727,21 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         int64_t pmax = 0;
         for (int i = 0; i < w.NP; ++i) pmax = std::max<int64_t>(pmax, hs->pcg_iters[i]);
         C.st->pcg_iters += pmax;
+        C.st->pcg_cluster = std::max(C.st->pcg_cluster, s->pcg_cs_last);
+        C.st->pcg_unstaged |= hs->pcg_unstaged != 0;
         pcg_tune_observe(s, pmax);
         if (s->prof) {
-            // compulsory HBM bytes of one PCG launch: diagonal and distinct
-            // off-diagonal blocks, row offsets and entries read once, g read
-            // and dq written once (everything else stays in shared memory)
             double tb = C.precision == ABD_MIXED ? 4.0 : 8.0;
-            double nnzb = 0.5 * hs->csr_total;
-            prof_add_bytes(s, "pcg", 144.0 * tb * (w.S_dyn + nnzb) + 8.0 * hs->csr_total + 4.0 * w.S_dyn +
-                                         2.0 * 96.0 * w.S_dyn);
+            // algorithmic bytes of one PCG launch, counted per iteration: each
+            // iteration of partition i reads its blocks (diagonal and
+            // off-diagonal, 144 entries each) and seven 12-vectors per slot
+            // (p, Ap, r, z, x and the preconditioner's input and output)
+            double pb = 0.0;
+            for (int i = 0; i < w.NP; ++i) {
+                double S_i = (double)(w.h_part_off[i + 1] - w.h_part_off[i]);
+                pb += (double)hs->pcg_iters[i] * (144.0 * tb * (S_i + 0.5 * hs->pcg_nent[i]) + 7.0 * 12.0 * tb * S_i);
+            }
+            prof_add_bytes(s, "pcg", pb);
             // one pair assembly: record, four FP64 positions, gradient and
             // three 12x12 blocks accumulated
             prof_add_bytes(s, "pair_assemble", (double)hs->c.act * (sizeof(PairRec) + 96.0 + 96.0 + 3.0 * 144.0 * tb));
@@ -973,11 +981,17 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
         memset(&b, 0, sizeof b);
         if ((rc = step_impl(s, &hp, &a, false)) < 0) return rc;
         if ((rc = step_impl(s, &hp, &b, false)) < 0) return rc;
+        const abd_step_stats first = *st;
         *st = b;
         st->status = ABD_DT_SPLIT;
         st->admm_iters = admm + a.admm_iters + b.admm_iters;
         st->newton_iters = newton + a.newton_iters + b.newton_iters;
-        st->pcg_iters += a.pcg_iters;
+        st->pcg_iters = first.pcg_iters + a.pcg_iters + b.pcg_iters;
+        st->pcg_cluster = std::max({first.pcg_cluster, a.pcg_cluster, b.pcg_cluster});
+        st->pcg_unstaged = first.pcg_unstaged | a.pcg_unstaged | b.pcg_unstaged;
+        st->list_redo = first.list_redo + a.list_redo + b.list_redo;
+        st->n_candidates_peak = std::max(st->n_candidates_peak, first.n_candidates_peak);
+        st->n_active_peak = std::max(st->n_active_peak, first.n_active_peak);
         st->n_candidates_peak = std::max(st->n_candidates_peak, a.n_candidates_peak);
         st->n_active_peak = std::max(st->n_active_peak, a.n_active_peak);
         st->kernel_launches = s->n_launches - L0;
@@ -992,6 +1006,9 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
         st->admm_iters = admm;
         st->status = status;
         st->pcg_iters += st2.pcg_iters;
+        st->pcg_cluster = std::max(st->pcg_cluster, st2.pcg_cluster);
+        st->pcg_unstaged |= st2.pcg_unstaged;
+        st->list_redo += st2.list_redo;
         st->min_distance = st2.min_distance;
         return status;
     }

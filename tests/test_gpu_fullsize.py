@@ -148,3 +148,58 @@ def test_full_size_candidates(swept):
         mine = {r for r in gs if (r[0] == 0 and (vbody[r[1]] == b or tbody[r[2]] == b))
                 or (r[0] == 1 and (ebody[r[1]] == b or ebody[r[2]] == b))}
         assert mine == exp, (int(b), len(mine), len(exp))
+
+
+CONTACT_FROM = 19  # the lowest layer reaches the box floor on step 19 (free fall before)
+
+
+@pytest.fixture(scope="module")
+def contact_window():
+    """The oracle's trajectory of the full-size workload into its first
+    contact steps: for steps 19 and 20, the state before the step, the
+    oracle's state after it and its statistics (about 25 s of CPU)."""
+    sa = scenes.sphere_grid_in_box(seed=0)
+    o = O.Scene(sa)
+    po = O.default_params(n_slabs=4, axis=0, planes=PLANES)
+    for _ in range(CONTACT_FROM):
+        o.step(po)
+    out = []
+    for _ in range(2):
+        q, v = o.state()
+        so = o.step(po)
+        out.append((q, v, o.state()[0], so))
+    assert out[0][3]["n_active_peak"] > 0 and out[0][3]["n_shared"] > 400
+    return sa, out
+
+
+@pytest.mark.parametrize("precision,tol,reserve", [(abd.FP64, 1e-9, None), (abd.MIXED, 1e-4, None),
+                                                   (abd.FP64, 1e-9, 16)])
+def test_full_size_contact_steps(contact_window, precision, tol, reserve):
+    """Contact steps of the benchmark workload, each from the oracle's state:
+    about 500 shared bodies over four slabs, so the PCG runs on clusters of
+    several CTAs with off-diagonal blocks between them; FP64 within 1e-9 per
+    step with equal ADMM and Newton counts, mixed within 1e-4.  With the pair
+    lists reserved at 16 records the first iteration of the first step
+    overflows them, grows them and is redone (the list-growth path), and the
+    result is unchanged."""
+    sa, window = contact_window
+    g = abd.Scene(sa)
+    g.partition(n_slabs=4, axis=0, planes=PLANES)
+    if reserve is not None:
+        g.reserve(reserve)
+    pg = abd.default_params(precision=precision, pcg_rtol=1e-12 if precision == abd.FP64 else 1e-5)
+    for k, (q, v, q_ref, so) in enumerate(window):
+        g.set_state(q, v)
+        sg = g.step(pg)
+        e = _rel(g.state()[0], q_ref)
+        print(f"step {CONTACT_FROM + k}: rel err {e:.3e}, ADMM {sg['admm_iters']}/{so['admm_iters']}, "
+              f"Newton {sg['newton_iters']}/{so['newton_iters']}, active {sg['n_active_peak']}, "
+              f"PCG cluster {sg['pcg_cluster']}, unstaged {sg['pcg_unstaged']}, list redo {sg['list_redo']}, "
+              f"slots {sg['n_slots']}, shared {sg['n_shared']}")
+        assert e <= tol, (k, e)
+        assert sg["status"] >= 0 and sg["min_distance"] > 0.0
+        assert sg["n_active_peak"] > 0 and sg["pcg_cluster"] >= 2
+        if precision == abd.FP64:
+            assert (sg["admm_iters"], sg["newton_iters"]) == (so["admm_iters"], so["newton_iters"])
+        if reserve is not None and k == 0:
+            assert sg["list_redo"] >= 1

@@ -149,6 +149,39 @@ def test_sphere_pile_admm_mixed():
     assert e <= MIXED_TOL
 
 
+def test_sphere_pile_admm_mixed_100_steps():
+    """The mixed path on a multi-partition contact pile over 100 steps (16
+    spheres on two slabs landing in their box and settling): every step from
+    the oracle's state within 1e-4 of the oracle's step, and a free-running
+    mixed trajectory with positive minimum distance after every step.  The
+    free run's drift from the oracle's own trajectory is printed: on a pile the
+    two FP64-vs-FP32 trajectories part like any two nearby trajectories of a
+    contact-rich system, so the per-step comparison is the bound."""
+    sa = _sphere_admm_scene()
+    g, free, o = abd.Scene(sa), abd.Scene(sa), O.Scene(sa)
+    for sc in (g, free):
+        sc.partition(n_slabs=2, axis=0)
+    pg = abd.default_params(precision=abd.MIXED, pcg_rtol=1e-5)
+    po = O.default_params(n_slabs=2, axis=0)
+    worst, drift, contact = 0.0, [], 0
+    for k in range(100):
+        qo, vo = o.state()
+        g.set_state(qo, vo)
+        sg = g.step(pg)
+        sf = free.step(pg)
+        so = o.step(po)
+        e = rel(g.state()[0], o.state()[0])
+        worst = max(worst, e)
+        assert e <= MIXED_TOL, (k, e)
+        assert sg["status"] >= 0 and sf["status"] >= 0
+        assert sf["min_distance"] > 0.0 and sg["min_distance"] > 0.0, (k, sf, sg)
+        contact += so["n_active_peak"] > 0
+        drift.append(rel(free.state()[0], o.state()[0]))
+    print(f"per-step worst {worst:.3e}; free-run drift after 10/50/100 steps "
+          f"{drift[9]:.3e}/{drift[49]:.3e}/{drift[99]:.3e}; contact steps {contact}")
+    assert contact >= 50
+
+
 def test_kinematic_sweeper_fp64_parity():
     """A kinematic bar (prescribed rotation) sweeping into cubes: FP64 path
     within 1e-9 of the oracle every step, equal Newton counts, no penetration."""

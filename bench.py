@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--no-serving", action="store_true", help="skip the served and batched legs")
+    ap.add_argument("--no-serving", action="store_true", help="skip the served leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-subdomain leg")
+    ap.add_argument("--batch-steps", type=int, default=6, help="timed steps of the batched leg")
     ap.add_argument("--no-fixed-rho", action="store_true", help="skip the fixed-rho comparison leg")
     ap.add_argument("--no-graph", action="store_true",
                     help="scenes on the legacy default stream (direct launches, no graph replay), e.g. under ncu")
@@ -278,9 +280,14 @@ def run_ours(args, rank, world):
     serving = batched = None
     if not args.no_serving:
         try:
-            serving, batched = serve_legs(abd)
+            serving = serve_legs(abd)
         except Exception as e:
             errors["serving"] = f"{type(e).__name__}: {e}"
+    if not args.no_batched:
+        try:
+            batched = batched_leg(abd, torch, stream, flush, args.batch_steps, 2)
+        except Exception as e:
+            errors["batched"] = f"{type(e).__name__}: {e}"
     cpu = cpu_baseline(args.cpu_seconds) if (rank == 0 and world == 1) else None
     lat_sorted = sorted(lat)
     out = {
@@ -396,10 +403,10 @@ def poisson_sweep(make_server, reqs, params, capacity_rps, fractions=(0.25, 0.5,
 
 
 def serve_legs(abd):
-    """Served and batched legs (bounded samples of the serving and
-    uneven-subdomain workloads), mixed precision: every request submitted at
-    once to the serving runtime (closed batch, continuous admission), then
-    the same requests under Poisson arrivals at four rates."""
+    """Served leg (a bounded sample of the serving workload), mixed
+    precision: every request submitted at once to the serving runtime (closed
+    batch, continuous admission), then the same requests under Poisson
+    arrivals at four rates."""
     from paper_2605_15875_gb300 import scenes
     p = abd.default_params(precision=abd.MIXED, pcg_rtol=1e-5)
     p64 = abd.default_params(precision=abd.FP64, pcg_rtol=1e-12)
@@ -413,13 +420,70 @@ def serve_legs(abd):
     serving["poisson"] = poisson_sweep(lambda: abd.Server(n_streams=4), reqs, p, cap_rps)
     serving["poisson_note"] = ("open loop, 4 streams, the same 64 requests; lambda relative to the closed-batch "
                                "capacity above (requests/s)")
-    subs = [(sa, 10) for sa in scenes.batched_subdomains(seed=0, n_scenes=16, lo=16, hi=512, levels=(1, 2))]
-    batched = _serve(abd, subs, 8, p)
-    plain = _serve(abd, subs, 1, p64)
-    batched["plain_fp64_one_at_a_time"] = plain["value"]
-    batched["speedup_vs_plain_fp64"] = round(batched["value"] / plain["value"], 3)
-    batched["sample"] = "16 uneven subdomains of 16-512 noisy icospheres (levels 1-2), 10 steps each"
-    return serving, batched
+    return serving
+
+
+def batched_leg(abd, torch, stream, flush, steps, warmup, n_scenes=64, lo=16, hi=2048, seed=0):
+    """Uneven subdomains packed into one batched world (one partition per
+    subdomain, every Newton phase of every subdomain in the same launches,
+    the steady-state iteration replayed as a CUDA graph), mixed precision,
+    against the plain FP64 path stepping each subdomain alone, one at a time,
+    over the same steps.  Each side warms up on `warmup` steps whose state is
+    then restored; L2 is flushed between timed steps (outside the timing)."""
+    from paper_2605_15875_gb300 import scenes
+    subs = scenes.batched_subdomains(seed=seed, n_scenes=n_scenes, lo=lo, hi=hi, levels=(1, 2, 3))
+    nb = sum(sa.n_dynamic for sa in subs)
+    pm = abd.default_params(precision=abd.MIXED, pcg_rtol=1e-5)
+    p64 = abd.default_params(precision=abd.FP64, pcg_rtol=1e-12)
+
+    def run(sc, p, prof=False):
+        q0, v0 = sc.state()
+        for _ in range(warmup):
+            sc.step(p)
+        sc.set_state(q0, v0)
+        if prof:
+            sc.profile(True)
+        lat, sts = [], []
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sts.append(sc.step(p))
+            e1.record(stream)
+            e1.synchronize()
+            lat.append(e0.elapsed_time(e1))
+        return lat, sts
+
+    world = abd.Scene(subs, stream=int(stream.cuda_stream))
+    lat, sts = run(world, pm, prof=True)
+    names = ["pcg", "pair_moll", "pair_assemble", "slot_assemble", "l2_static", "l2_swept", "ccd", "energy"]
+    ks = {n: world.kernel_stats(n) for n in names}
+    world.close()
+    t_b = sum(lat) / 1e3
+    alone_ms, alone_status = 0.0, 0
+    for sa in subs:
+        sc = abd.Scene(sa, stream=int(stream.cuda_stream))
+        la, sa_st = run(sc, p64)
+        alone_ms += sum(la)
+        alone_status = max([alone_status] + [x["status"] for x in sa_st])
+        sc.close()
+    value = nb * steps / t_b
+    plain = nb * steps / (alone_ms / 1e3)
+    return {"value": round(value, 2), "unit": "body-steps/s", "subdomains": n_scenes, "bodies": nb,
+            "steps": steps, "p50_step_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_step_ms": round(float(np.percentile(lat, 99)), 3),
+            "plain_fp64_one_at_a_time": round(plain, 2), "speedup_vs_plain_fp64": round(value / plain, 3),
+            "newton_iters_mean": float(np.mean([x["newton_iters"] for x in sts])),
+            "active_pairs_peak": int(max(x["n_active_peak"] for x in sts)),
+            "worst_status": int(max(x["status"] for x in sts)), "plain_worst_status": int(alone_status),
+            "min_distance_min": float(min(x["min_distance"] for x in sts)),
+            "kernels_gbs": {n: (round(v[2] / (v[1] / 1e3) / 1e9, 2) if v[1] > 0 and v[2] > 0 else None)
+                            for n, v in ks.items()},
+            "kernels_ms": {n: round(v[1], 3) for n, v in ks.items()},
+            "sample": f"{n_scenes} subdomains of {lo}-{hi} noisy icospheres (log-uniform counts, levels 1-3, "
+                      f"densities log-uniform 1e2-1e4, seed {seed}), one batched world; {steps} timed steps "
+                      f"after {warmup} warm-up steps (state restored)"}
 
 
 def host_cpu():

@@ -270,6 +270,35 @@ int abd_partition_planes(const abd_scene *s, double *planes, int32_t cap, int32_
 int abd_pd_update(int32_t n_slabs, const double *tau, const double *T_prev, double kp, double kd, double *delta,
                   double *T);
 
+/* ---------------------------------------------------------------------------
+ * Batched world: n independent scenes (uneven subdomains) in one scene
+ * object.  Each scene becomes one partition; every phase of every scene's
+ * Newton iteration (broad phase, assembly, PCG, CCD, line search) runs in the
+ * same kernel launches, each partition converging on its own (its local solve
+ * is Eq. 5 without shared bodies), and the steady-state iteration is replayed
+ * as one CUDA graph.  Each scene keeps its own scale l (Eq. 8) and default
+ * barrier stiffness, its static bodies collide only with its own bodies, and
+ * scenes never collide with one another, so each scene's step is the one it
+ * takes alone (up to the order of floating-point sums).  The paper solves one
+ * scene; this packing is this library's batching of many.
+ *   descs: n scene descriptions (host, copied); all must have the same ground
+ *          planes and gravity (ABD_E_INVALID otherwise); n <= 256.
+ *   Bodies are concatenated in scene order: abd_state_get/set and
+ *   abd_body_props index the concatenation; abd_batch_layout gives each
+ *   scene's first body.  abd_partition is rejected (the scenes are the
+ *   partitions).  abd_candidates on a batched world treats the caller's
+ *   positions as one scene. */
+int abd_scene_create_batch(const abd_scene_desc *descs, int32_t n, void *cuda_stream, abd_scene **out);
+
+/* Body offsets of the scenes of a batched world: body_off[0..n] (up to cap
+ * values, host), *n = number of scenes (1 and [0, B] for an ordinary scene). */
+int abd_batch_layout(const abd_scene *s, int64_t *body_off, int32_t cap, int32_t *n);
+
+/* Newton iterations of each partition (each scene of a batched world) summed
+ * over the ADMM rounds of the last step: up to cap values into iters (host),
+ * the partition count in *n. */
+int abd_partition_newton(const abd_scene *s, int32_t *iters, int32_t cap, int32_t *n);
+
 /* Membership of partition `part` as the last abd_step built it (Sec. 4: a
  * dynamic body belongs to every slab its w-inflated box meets).  `bodies`
  * receives up to `cap` body indices of the partition and `shared` up to

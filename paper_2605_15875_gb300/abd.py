@@ -83,7 +83,8 @@ EXPORTS = ["abd_scene_create", "abd_scene_destroy", "abd_scene_counts", "abd_bod
            "abd_candidates", "abd_profile", "abd_kernel_stats", "abd_step_params_default", "abd_status_string",
            "abd_last_error", "abd_candidates_noalloc", "abd_partition_get", "abd_server_create",
            "abd_server_submit", "abd_server_poll", "abd_server_wait", "abd_server_result", "abd_server_latencies",
-           "abd_server_error", "abd_server_destroy", "abd_partition_planes", "abd_pd_update", "abd_scene_reserve"]
+           "abd_server_error", "abd_server_destroy", "abd_partition_planes", "abd_pd_update", "abd_scene_reserve",
+           "abd_scene_create_batch", "abd_batch_layout", "abd_partition_newton"]
 
 _lib = None
 
@@ -123,6 +124,9 @@ def load(path: Optional[str] = None):
     L.abd_partition_get.argtypes = [vp, C.c_int32, vp, C.c_int32, i32p, vp, C.c_int32, i32p]
     L.abd_partition_planes.argtypes = [vp, vp, C.c_int32, i32p]
     L.abd_scene_reserve.argtypes = [vp, i64]
+    L.abd_scene_create_batch.argtypes = [vp, C.c_int32, vp, C.POINTER(vp)]
+    L.abd_batch_layout.argtypes = [vp, vp, C.c_int32, i32p]
+    L.abd_partition_newton.argtypes = [vp, vp, C.c_int32, i32p]
     L.abd_pd_update.argtypes = [C.c_int32, vp, vp, C.c_double, C.c_double, vp, vp]
     L.abd_server_create.argtypes = [C.POINTER(ServerDesc), C.POINTER(vp)]
     L.abd_server_submit.argtypes = [vp, C.POINTER(SceneDesc), vp, vp, C.c_int32, C.POINTER(i64)]
@@ -185,15 +189,23 @@ def scene_desc(sa) -> SceneDesc:
 
 
 class Scene:
-    """A scene resident on the current CUDA device (C ABI handle)."""
+    """A scene resident on the current CUDA device (C ABI handle).  Given a
+    list of scene arrays, a batched world of those scenes
+    (abd_scene_create_batch): one partition per scene, all stepped in the same
+    launches; its state is the concatenation of the scenes' states."""
 
     def __init__(self, sa, stream: Optional[int] = None):
         L = load()
         self._keep = [sa]
-        d = scene_desc(sa)
         h = C.c_void_p()
         self.stream = _current_stream() if stream is None else stream
-        rc = L.abd_scene_create(C.byref(d), self.stream, C.byref(h))
+        if isinstance(sa, (list, tuple)):
+            descs = (SceneDesc * len(sa))(*[scene_desc(x) for x in sa])
+            self._keep.append(descs)
+            rc = L.abd_scene_create_batch(C.cast(descs, C.c_void_p), len(sa), self.stream, C.byref(h))
+        else:
+            d = scene_desc(sa)
+            rc = L.abd_scene_create(C.byref(d), self.stream, C.byref(h))
         if rc != 0:
             raise AbdError(f"abd_scene_create failed: {L.abd_status_string(rc).decode()} ({rc})")
         self.h = h
@@ -249,6 +261,22 @@ class Scene:
         self._check(self.L.abd_partition_get(self.h, part, _p(b), n.value, C.byref(n), _p(sh), ns.value,
                                              C.byref(ns)), "abd_partition_get")
         return b[:n.value], sh[:ns.value]
+
+    def layout(self):
+        """Body offsets of the scenes of a batched world ([n + 1])."""
+        n = C.c_int32()
+        self._check(self.L.abd_batch_layout(self.h, None, 0, C.byref(n)), "abd_batch_layout")
+        off = np.zeros(n.value + 1, dtype=np.int64)
+        self._check(self.L.abd_batch_layout(self.h, _p(off), n.value + 1, C.byref(n)), "abd_batch_layout")
+        return off
+
+    def partition_newton(self):
+        """Newton iterations of each partition (scene of a batched world) in the last step."""
+        n = C.c_int32()
+        self._check(self.L.abd_partition_newton(self.h, None, 0, C.byref(n)), "abd_partition_newton")
+        it = np.zeros(max(1, n.value), dtype=np.int32)
+        self._check(self.L.abd_partition_newton(self.h, _p(it), n.value, C.byref(n)), "abd_partition_newton")
+        return it[:n.value]
 
     def reserve(self, pairs):
         self._check(self.L.abd_scene_reserve(self.h, int(pairs)), "abd_scene_reserve")

@@ -79,8 +79,8 @@ struct AsmArgs {
     const double *xbar, *mass, *S, *vol, *kappa;
     const double *q, *qtil, *z, *u, *rho;
     const double *x;
-    const PartState *part;
-    double h, dhat, kB;
+    const PartState *part;  // per partition: active flag, barrier stiffness kB
+    double h, dhat;
     Planes planes;
     const int64_t *slot_voff;
     double *g;
@@ -213,7 +213,8 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
             for (int k = 0; k < 3; ++k) Xd[3 * v + k] = A.x[3 * (int64_t)r.v[v] + k] - A.x[3 * (int64_t)r.v[0] + k];
         PairGrad PG;
         double gx[12];
-        double d = pair_gradient(ee, Xd, A.dhat, A.kB, r.eps, PG, gx);
+        const double kB = A.part[part].kB;  // the barrier stiffness of the pair's partition
+        double d = pair_gradient(ee, Xd, A.dhat, kB, r.eps, PG, gx);
         if (!(d < A.dhat) || !(d > 0.0)) continue;
         const bool moll = ee && PG.moll;
         if (moll) {
@@ -247,7 +248,7 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
         {
             // exact low-rank projection: PSD(H) = B PSD(K) B^T, J^T PSD(H) J = P_s K+ P_t^T
             T K[25], wh[4], chat[2][4], rh[3];
-            int n = pair_hessian_lowrank<T>(ee, X, PG, T(d), T(A.kB), K, wh, chat, rh);
+            int n = pair_hessian_lowrank<T>(ee, X, PG, T(d), T(kB), K, wh, chat, rh);
             psd_small<T>(K, n);
             // pull-backs of the basis to each side: om[a] = sum_v w^_v xi_v, ga[j] = sum_v c^_jv xi_v
             T om[2][4], ga[2][2][4];
@@ -410,12 +411,13 @@ __global__ void __launch_bounds__(128) k_pair_moll(AsmArgs A, const PairRec *__r
             for (int v = 0; v < 4; ++v)
                 for (int k = 0; k < 3; ++k) Xd[3 * v + k] = A.x[3 * (int64_t)r.v[v] + k] - A.x[3 * (int64_t)r.v[0] + k];
             PairGrad PG;
-            double d = pair_gradient(ee, Xd, A.dhat, A.kB, r.eps, PG, sg[wib]);
+            const double kB = A.part[pair_part(sa, sb, A.S_dyn, A.slot_part)].kB;
+            double d = pair_gradient(ee, Xd, A.dhat, kB, r.eps, PG, sg[wib]);
             sok[wib] = (d < A.dhat) && (d > 0.0);
             if (sok[wib]) {
                 T X[12];
                 for (int e = 0; e < 12; ++e) X[e] = T(Xd[e]);
-                pair_hessian<T>(ee, X, PG, T(d), T(A.kB), T(r.eps), sH[wib]);
+                pair_hessian<T>(ee, X, PG, T(d), T(kB), T(r.eps), sH[wib]);
                 sw[wib] = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
                 for (int v = 0; v < 4; ++v) {
                     int s = A.sv_slot[r.v[v]];
@@ -538,7 +540,7 @@ __global__ void k_vp_assemble(AsmArgs A, int64_t SVd, T *__restrict__ diag) {
             if (!(d < A.dhat) || !(d > 0.0)) continue;
             double bb, b1, b2;
             barrier3<double>(d, A.dhat, bb, b1, b2);
-            double w = A.h * A.h / (double)__popcll(A.slot_mask[s]) * A.kB;
+            double w = A.h * A.h / (double)__popcll(A.slot_mask[s]) * A.part[A.slot_part[s]].kB;
             int b = A.slot_body[s];
             const double *xb = A.xbar + 3 * ((int64_t)A.voff[b] + (i - A.slot_voff[s]));
             double xi[4] = {1.0, xb[0], xb[1], xb[2]};
@@ -640,8 +642,8 @@ struct EnArgs {
     const double *x0, *x1;
     const double *alphas;  // [NP][kLS+1], alphas[.][0] = 0
     const int *live;       // 0: no partition has a trial step in this pass (every thread returns)
-    PartState *part;
-    double h, dhat, kB;
+    PartState *part;  // per partition: active flag, trial-step energies, barrier stiffness kB
+    double h, dhat;
     Planes planes;
 };
 
@@ -701,12 +703,13 @@ __global__ void k_energy_pairs(EnArgs A, const PairRec *__restrict__ ls, int64_t
         int64_t i = base + (threadIdx.x & 31);
         int p = -1;
         PairRec r;
-        double w = 0.0, X0[12], DX[12];
+        double w = 0.0, kB = 0.0, X0[12], DX[12];
         if (i < n) {
             r = ls[i];
             int sa, sb;
             pair_slots(r, A.sv_slot, sa, sb);
             p = pair_part(sa, sb, A.S_dyn, A.slot_part);
+            kB = A.part[p].kB;
             if (!A.part[p].active || A.alphas[(kLS + 1) * p] < 0.0) p = -1;
             w = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
             for (int v = 0; v < 4; ++v)
@@ -723,7 +726,7 @@ __global__ void k_energy_pairs(EnArgs A, const PairRec *__restrict__ ls, int64_t
             if (use) {
                 double X[12], d;
                 for (int q = 0; q < 12; ++q) X[q] = X0[q] + al * DX[q];
-                e = w * pair_energy(r.flags & 1, X, A.dhat, A.kB, r.eps, d);
+                e = w * pair_energy(r.flags & 1, X, A.dhat, kB, r.eps, d);
             }
             add_energy(A.part, use ? p : -1, j, e);
         }
@@ -740,7 +743,7 @@ __global__ void k_energy_vp(EnArgs A, int64_t SVd) {
             p = A.slot_part[s];
             if (!A.part[p].active || A.alphas[(kLS + 1) * p] < 0.0) p = -1;
         }
-        double w = p >= 0 ? A.h * A.h / (double)__popcll(A.slot_mask[s]) * A.kB : 0.0;
+        double w = p >= 0 ? A.h * A.h / (double)__popcll(A.slot_mask[s]) * A.part[p].kB : 0.0;
         for (int j = 0; j <= kLS; ++j) {
             double al = p >= 0 ? A.alphas[(kLS + 1) * p + j] : -1.0;
             bool use = p >= 0 && (j == 0 || al >= 0.0);
@@ -769,7 +772,7 @@ __global__ void k_energy_vp(EnArgs A, int64_t SVd) {
 // ---------------------------------------------------------------------------
 namespace abd {
 
-static AsmArgs make_asm(abd_scene *s, const abd_step_params *p, double kB) {
+static AsmArgs make_asm(abd_scene *s, const abd_step_params *p) {
     World &w = s->w;
     AsmArgs A = {};
     A.S_dyn = w.S_dyn;
@@ -779,7 +782,7 @@ static AsmArgs make_asm(abd_scene *s, const abd_step_params *p, double kB) {
     A.S = P<double>(s->dev.S); A.vol = P<double>(s->dev.vol); A.kappa = P<double>(s->dev.kappa);
     A.q = P<double>(w.q); A.qtil = P<double>(w.qtil); A.z = P<double>(w.z); A.u = P<double>(w.u);
     A.rho = P<double>(w.rho); A.x = P<double>(w.x); A.part = P<PartState>(w.part);
-    A.h = p->h; A.dhat = p->dhat; A.kB = kB; A.planes = s->planes;
+    A.h = p->h; A.dhat = p->dhat; A.planes = s->planes;
     A.slot_voff = P<int64_t>(w.slot_voff);
     A.g = P<double>(w.g);
     A.rowcnt = P<int>(w.rowcnt);
@@ -800,10 +803,10 @@ int launch_narrow_async(abd_scene *s, const PairRec *src, const unsigned long lo
 }
 
 template <class T>
-static int assemble_async_T(abd_scene *s, const abd_step_params *p, double kB) {
+static int assemble_async_T(abd_scene *s, const abd_step_params *p) {
     World &w = s->w;
     Counters *c = P<Counters>(w.ctr);
-    AsmArgs A = make_asm(s, p, kB);
+    AsmArgs A = make_asm(s, p);
     cudaMemsetAsync(w.rowcnt.p, 0, sizeof(int) * (size_t)(w.S_dyn + 1), s->stream);
     cudaMemsetAsync(w.rowcur.p, 0, sizeof(int) * (size_t)(w.S_dyn + 1), s->stream);
     ABD_LAUNCH(s, k_zero_off<T>, grid_for(144 * w.cap_l1, 256, 152 * 8), 256, 0, s->stream, P<T>(w.off),
@@ -835,8 +838,8 @@ static int assemble_async_T(abd_scene *s, const abd_step_params *p, double kB) {
     return cuda_check(s, cudaGetLastError(), "assemble");
 }
 
-int launch_assemble_async(abd_scene *s, int precision, const abd_step_params *p, double kB) {
-    return precision == ABD_MIXED ? assemble_async_T<float>(s, p, kB) : assemble_async_T<double>(s, p, kB);
+int launch_assemble_async(abd_scene *s, int precision, const abd_step_params *p) {
+    return precision == ABD_MIXED ? assemble_async_T<float>(s, p) : assemble_async_T<double>(s, p);
 }
 
 int launch_ccd_async(abd_scene *s, const abd_step_params *p, bool want_ls) {
@@ -856,7 +859,7 @@ int launch_ccd_async(abd_scene *s, const abd_step_params *p, bool want_ls) {
     return cuda_check(s, cudaGetLastError(), "k_ccd");
 }
 
-int launch_energy_async(abd_scene *s, const abd_step_params *p, double kB, const double *alphas_dev) {
+int launch_energy_async(abd_scene *s, const abd_step_params *p, const double *alphas_dev) {
     World &w = s->w;
     Counters *c = P<Counters>(w.ctr);
     EnArgs A = {};
@@ -869,7 +872,7 @@ int launch_energy_async(abd_scene *s, const abd_step_params *p, double kB, const
     A.u = P<double>(w.u); A.rho = P<double>(w.rho); A.x0 = P<double>(w.x); A.x1 = P<double>(w.x1);
     A.alphas = alphas_dev; A.part = P<PartState>(w.part);
     A.live = &c->ls_live;
-    A.h = p->h; A.dhat = p->dhat; A.kB = kB; A.planes = s->planes;
+    A.h = p->h; A.dhat = p->dhat; A.planes = s->planes;
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
     cudaEvent_t ea, eb;
     prof_begin(s, "energy", 0.0, &ea, &eb);

@@ -243,6 +243,54 @@ __global__ void k_l1f(int S_all, const int *__restrict__ slot_part, const float 
 
 
 
+// Level 1 within partitions: one warp per dynamic slot a of an active
+// partition tests the later slots of its own partition (slots are sorted by
+// partition) and the static colliders that serve it (static_grp -1: every
+// partition), with ballot compaction of the hits (a, b), a < b.  The set is
+// k_l1f's non-cross set; the work is the sum over partitions of n_p^2 / 2
+// instead of S^2 / 2, so the scenes of a batched world never meet.
+__global__ void k_l1_part(int S_dyn, int S_all, const int *__restrict__ slot_part, const int *__restrict__ part_off,
+                          const int *__restrict__ static_grp, const float *__restrict__ box,
+                          const PartState *__restrict__ part, int2 *__restrict__ out, int64_t cap,
+                          unsigned long long *__restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int n_static = S_all - S_dyn;
+    for (int a = blockIdx.x + gridDim.x * (threadIdx.x >> 5); a < S_dyn; a += nw) {
+        const int pa = slot_part[a];
+        if (!part[pa].active) continue;  // warp-uniform
+        float ba[6];
+        for (int k = 0; k < 6; ++k) ba[k] = box[6 * (int64_t)a + k];
+        const int n1 = part_off[pa + 1] - (a + 1), tot = n1 + n_static;
+        for (int j0 = 0; j0 < tot; j0 += 32) {
+            const int j = j0 + lane;
+            int b = -1;
+            if (j < n1) b = a + 1 + j;
+            else if (j < tot) {
+                const int g = static_grp[j - n1];
+                if (g < 0 || g == pa) b = S_dyn + (j - n1);
+            }
+            bool hit = false;
+            if (b >= 0) {
+                float bb[6];
+                for (int k = 0; k < 6; ++k) bb[k] = box[6 * (int64_t)b + k];
+                hit = overlapf(ba, bb);
+            }
+            unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (m) {
+                unsigned long long pos = 0;
+                int leader = __ffs(m) - 1;
+                if (lane == leader) pos = atomicAdd(count, (unsigned long long)__popc(m));
+                pos = __shfl_sync(0xffffffffu, pos, leader);
+                if (hit) {
+                    unsigned long long my = pos + __popc(m & ((1u << lane) - 1));
+                    if ((int64_t)my < cap) out[my] = make_int2(a, b);
+                }
+            }
+        }
+    }
+}
+
 // Primitive kind: 0 vertex, 1 triangle, 2 edge.  Fills the slot-vertex ids and
 // returns the number of vertices.
 __device__ __forceinline__ int prim_verts(const L2Args &A, int kind, int slot, int idx, int sv[3]) {
@@ -803,6 +851,16 @@ static int read_counter(abd_scene *s, unsigned long long *dptr, unsigned long lo
     return cuda_check(s, e, "read counter");
 }
 
+// Level 1 within partitions (k_l1_part) into w.l1, counting into Counters::l1.
+static void launch_l1_part(abd_scene *s, bool swept) {
+    World &w = s->w;
+    Counters *c = P<Counters>(w.ctr);
+    if (w.S_dyn == 0) return;
+    ABD_LAUNCH(s, k_l1_part, grid_for((int64_t)w.S_dyn * 32, 256), 256, 0, s->stream, w.S_dyn, w.S_all,
+               P<int>(w.slot_part), P<int>(w.part_off), P<int>(w.static_grp),
+               swept ? P<float>(w.box1) : P<float>(w.box), P<PartState>(w.part), P<int2>(w.l1), w.cap_l1, &c->l1);
+}
+
 int launch_l1(abd_scene *s, bool swept, int64_t *count) {
     World &w = s->w;
     Counters *c = P<Counters>(w.ctr);
@@ -812,10 +870,7 @@ int launch_l1(abd_scene *s, bool swept, int64_t *count) {
     }
     for (;;) {
         cudaMemsetAsync(&c->l1, 0, sizeof(unsigned long long), s->stream);
-        int64_t ntile = (w.S_all + 31) / 32;
-        ABD_LAUNCH(s, k_l1f, grid_for((int64_t)w.S_all * ntile, 256), 256, 0, s->stream, w.S_all, P<int>(w.slot_part),
-                   swept ? P<float>(w.box1) : P<float>(w.box), P<PartState>(w.part), P<int2>(w.l1), w.cap_l1, &c->l1,
-                   P<int>(w.slot_body), 0);
+        launch_l1_part(s, swept);
         int rc = cuda_check(s, cudaGetLastError(), "k_l1");
         if (rc) return rc;
         unsigned long long n = 0;
@@ -879,10 +934,17 @@ int launch_l1_async(abd_scene *s, bool swept, int cross) {
     World &w = s->w;
     Counters *c = P<Counters>(w.ctr);
     cudaMemsetAsync(&c->l1, 0, sizeof(unsigned long long), s->stream);
-    int64_t ntile = (w.S_all + 31) / 32;
-    ABD_LAUNCH(s, k_l1f, grid_for((int64_t)w.S_all * ntile, 256), 256, 0, s->stream, w.S_all, P<int>(w.slot_part),
-               swept ? P<float>(w.box1) : P<float>(w.box), P<PartState>(w.part), P<int2>(w.l1), w.cap_l1, &c->l1,
-               P<int>(w.slot_body), cross);
+    if (cross && s->group.empty()) {
+        // whole-scene check across slab partitions (replicas of different
+        // bodies on different slabs); a batched world's scenes never meet,
+        // so its partitions are checked one by one
+        int64_t ntile = (w.S_all + 31) / 32;
+        ABD_LAUNCH(s, k_l1f, grid_for((int64_t)w.S_all * ntile, 256), 256, 0, s->stream, w.S_all,
+                   P<int>(w.slot_part), swept ? P<float>(w.box1) : P<float>(w.box), P<PartState>(w.part),
+                   P<int2>(w.l1), w.cap_l1, &c->l1, P<int>(w.slot_body), cross);
+    } else {
+        launch_l1_part(s, swept);
+    }
     return cuda_check(s, cudaGetLastError(), "k_l1");
 }
 

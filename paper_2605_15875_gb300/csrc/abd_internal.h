@@ -22,7 +22,11 @@
 namespace abd {
 
 constexpr int kMaxPlanes = 8;
-constexpr int kMaxParts = 64;
+// Partitions of one world: up to 64 slabs (membership masks are 64-bit), or
+// up to kMaxParts groups of a batched world (independent scenes, one
+// partition each).
+constexpr int kMaxSlabs = 64;
+constexpr int kMaxParts = 256;
 // Layout of the PCG status words (w.pcg_sc, ints): iterations per partition,
 // the overflow word, a flag set when some CTA read off-diagonal entries that
 // did not fit in its shared memory, then the off-diagonal CSR entries of each
@@ -99,6 +103,8 @@ struct World {
     DBuf cl_info;      // [C] (slot, kind << 24 | cluster index)
     DBuf cbox, cbox1;  // [C][6] cluster boxes (static, swept)
     DBuf cp;           // [cap_cp] int4 cluster pairs of the level-2 pass
+    DBuf static_grp;   // [S_all - S_dyn] partition a static slot serves (-1: every partition)
+    DBuf pinv;         // [S_dyn][144] preconditioner blocks when a partition is too large to stage them
     int64_t C = 0;
     int64_t cap_l1 = 0, cap_cand = 0, cap_act = 0, cap_ls = 0, cap_cp = 0;
     int ecap_mult = 16;  // PCG neighbour-list capacity per owned slot
@@ -119,6 +125,8 @@ struct PartState {
     double E[kLS + 1];          // E(q) and E(q + alpha_j dq)
     double rz, rz_new, r0, rr, pap;
     int pcg_done, pcg_it;
+    double kB;      // barrier stiffness of the partition (its scene's, in a batched world)
+    double inv_hl;  // 1 / (h l), l the scale of the partition's scene (Eq. 8's normalisation)
 };
 
 struct Counters {
@@ -182,6 +190,11 @@ struct abd_scene {
     std::vector<double> crest;
     abd::Planes planes{};
     double g[3] = {0, 0, 0};
+    // batched world (abd_scene_create_batch): group of every body (its
+    // scene), body offsets of the groups; empty for an ordinary scene
+    std::vector<int> group;
+    std::vector<int64_t> group_off;
+    std::vector<int64_t> last_part_newton;  // Newton iterations per partition in the last step
     // partition
     int axis = 0, n_slabs = 1;
     std::vector<double> slab_planes;
@@ -229,9 +242,10 @@ int launch_l2_async(abd_scene *s, bool swept, double half);
 // ---- (abd_assemble.cu) ----
 int launch_narrow_async(abd_scene *s, const PairRec *src, const unsigned long long *src_n, int64_t src_cap,
                         double dhat);
-int launch_assemble_async(abd_scene *s, int precision, const abd_step_params *p, double kB);
+// barrier stiffness per partition from PartState::kB
+int launch_assemble_async(abd_scene *s, int precision, const abd_step_params *p);
 int launch_ccd_async(abd_scene *s, const abd_step_params *p, bool want_ls);
-int launch_energy_async(abd_scene *s, const abd_step_params *p, double kB, const double *alphas_dev);
+int launch_energy_async(abd_scene *s, const abd_step_params *p, const double *alphas_dev);
 // minimum unsigned distance over w.cand at w.x and vertex-plane distances of
 // dynamic slot vertices (negative plane distances count as 0) into Counters::mind
 int launch_min_dist_async(abd_scene *s);

@@ -38,6 +38,8 @@ struct PcgClArgs {
     const int2 *ent;                     // (neighbour slot, block index | bit 31 = transposed)
     const double *g;
     double *x;
+    void *pinv;           // non-null: blocks stay in global memory, preconditioner blocks inverted here
+                          // ([S_dyn][144]), for partitions whose blocks do not fit in shared memory
     double tol2;
     int max_it;
     int *iters;           // PCG status words (kPcg* layout): iterations per partition, flags, entries
@@ -45,13 +47,18 @@ struct PcgClArgs {
 
 // Dynamic shared memory of one CTA owning m slots: p, Ap, r, z, x (all T)
 // for 12 m rows, 64 partial words, 32 reduction words, m + 1 row
-// offsets, its diagonal and preconditioner blocks, then (as far as the budget
-// goes) per off-diagonal entry of its rows the neighbour id, the block (staged
-// row-major in the orientation the row needs) and the neighbour's p.
+// offsets, its diagonal and preconditioner blocks (unless they stay in global
+// memory: pcg_vec_bytes), then (as far as the budget goes) per off-diagonal
+// entry of its rows the neighbour id, the block (staged row-major in the
+// orientation the row needs) and the neighbour's p.
 template <class T>
-__host__ __device__ inline size_t pcg_base_bytes(int m) {
+inline size_t pcg_vec_bytes(int m) {
     size_t rows = 12 * (size_t)m;
-    return rows * 5 * sizeof(T) + 16 + 96 * sizeof(T) + 4 * ((size_t)m + 1) + 16 + 2 * 144 * sizeof(T) * (size_t)m;
+    return rows * 5 * sizeof(T) + 16 + 96 * sizeof(T) + 4 * ((size_t)m + 1) + 16;
+}
+template <class T>
+inline size_t pcg_base_bytes(int m) {
+    return pcg_vec_bytes<T>(m) + 2 * 144 * sizeof(T) * (size_t)m;
 }
 
 // Block-wide sums of two values (every thread gets both).  Callers separate
@@ -136,9 +143,15 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
     R *red = x + rows;      // [64] partials: [0,16) p.Ap, [16,48) (r.r, r.z), [48,64) flags
     R *scratch = red + 64;  // [32] block reduction
     int *rofs = (int *)(scratch + 32);                                  // [m + 1] my entry ranges
-    T *Ds = (T *)(((uintptr_t)(rofs + m + 1) + 15) & ~uintptr_t(15));  // [m][144] diagonal blocks
-    T *Ps = Ds + 144 * m;                                              // [m][144] preconditioner blocks
-    unsigned char *tail = (unsigned char *)(Ps + 144 * m);
+    T *blk = (T *)(((uintptr_t)(rofs + m + 1) + 15) & ~uintptr_t(15));
+    // diagonal and preconditioner blocks: staged in shared memory, or (a
+    // partition too large for that) read from global memory, the
+    // preconditioner inverted in A.pinv
+    const bool gblk = A.pinv != nullptr;
+    T *Ds = gblk ? nullptr : blk;                                      // [m][144] diagonal blocks
+    const T *Dr = gblk ? diag + 144 * (int64_t)my0 : Ds;
+    T *Ps = gblk ? (T *)A.pinv + 144 * (int64_t)my0 : blk + 144 * m;   // [m][144] preconditioner blocks
+    unsigned char *tail = (unsigned char *)(gblk ? blk : blk + 2 * 144 * m);
 
     const bool active = A.part[part].active != 0 && n > 0;
     if (rank == 0 && threadIdx.x == 0) A.iters[kPcgNent + part] = active ? A.rowoff[s1] - A.rowoff[s0] : 0;
@@ -157,7 +170,7 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
     T *gp = Bs + 144 * (size_t)es;                                 // [es][12] neighbours' p
     for (int e = threadIdx.x; e < 144 * mine; e += blockDim.x) {
         T v = diag[144 * (int64_t)my0 + e];
-        Ds[e] = v;
+        if (!gblk) Ds[e] = v;
         Ps[e] = v;
     }
     for (int sl = threadIdx.x; sl <= mine; sl += blockDim.x) rofs[sl] = A.rowoff[my0 + sl] - e0;
@@ -214,7 +227,7 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
         R pap = R(0), unused = R(0);
         for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
             int sl = e / 12, i = e % 12;
-            const T *D = Ds + 144 * sl + 12 * i;
+            const T *D = Dr + 144 * sl + 12 * i;
             T acc = T(0);
             for (int j = 0; j < 12; ++j) acc += D[j] * p[12 * sl + j];
             for (int jj = rofs[sl]; jj < rofs[sl + 1]; ++jj) {
@@ -317,11 +330,15 @@ static int launch_T(abd_scene *s, const abd_step_params *p) {
     // default cluster size: up to 16 CTAs, about 16 owned slots each
     int CS = std::min(max_cluster, std::max(2, (maxn + 15) / 16));
     if (CS > 8 && max_cluster < 16) CS = 8;
-    auto smem_for = [&](int cs, size_t &smem) {
+    // shared memory of a CTA for cluster size cs; the blocks stay in global
+    // memory (gblk) when the largest partition's do not fit
+    auto smem_for = [&](int cs, size_t &smem, bool &gblk) {
         int m = std::max(1, (maxn + cs - 1) / cs);
         size_t base = pcg_base_bytes<T>(m);
+        gblk = base + 1024 > max_smem;
+        if (gblk) base = pcg_vec_bytes<T>(m);
         smem = std::max(base + 1024, std::min(max_smem, base + (size_t)m * 12 * (144 + 12 + 4) * sizeof(T)));
-        return base <= max_smem;
+        return base + 1024 <= max_smem;
     };
     auto config = [&](int cs, size_t smem, cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at) {
         cfg = cudaLaunchConfig_t{};
@@ -355,7 +372,8 @@ static int launch_T(abd_scene *s, const abd_step_params *p) {
             bool dup = false;
             for (int i = 0; i < tu.ncand; ++i) dup |= tu.cand[i] == c;
             size_t sm = 0;
-            if (dup || !smem_for(c, sm)) continue;
+            bool gb = false;
+            if (dup || !smem_for(c, sm, gb)) continue;
             cudaLaunchConfig_t cf;
             cudaLaunchAttribute at[1];
             config(c, sm, cf, at);
@@ -379,12 +397,16 @@ static int launch_T(abd_scene *s, const abd_step_params *p) {
         timed = true;
     }
     size_t smem = 0;
-    if (!smem_for(CS, smem)) return set_err(s, ABD_E_UNSUPPORTED, "pcg: partition too large for the cluster");
+    bool gblk = false;
+    if (!smem_for(CS, smem, gblk)) return set_err(s, ABD_E_UNSUPPORTED, "pcg: partition too large for the cluster");
+    if (gblk && !dbuf_ensure(w.pinv, 144 * sizeof(T) * (size_t)std::max(1, w.S_dyn)))
+        return set_err(s, ABD_E_OOM, "pcg preconditioner blocks");
     PcgClArgs A = {};
     A.part_off = P<int>(w.part_off); A.part = P<PartState>(w.part);
     A.diag = w.diag.p; A.off = w.off.p;
     A.rowoff = P<int>(w.rowoff); A.ent = P<int2>(w.ent);
     A.g = P<double>(w.g); A.x = P<double>(w.dq);
+    A.pinv = gblk ? w.pinv.p : nullptr;
     A.tol2 = p->pcg_rtol * p->pcg_rtol; A.max_it = p->pcg_max;
     A.iters = P<int>(w.pcg_sc);
     cudaLaunchConfig_t cfg;

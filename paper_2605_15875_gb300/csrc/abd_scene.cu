@@ -444,8 +444,10 @@ extern "C" int abd_body_props(const abd_scene *s, int32_t b, double *m, double c
 }
 
 extern "C" int abd_partition(abd_scene *s, const abd_partition_desc *d) {
-    if (!s || !d || d->n_slabs < 1 || d->n_slabs > kMaxParts || d->axis < 0 || d->axis > 2)
+    if (!s || !d || d->n_slabs < 1 || d->n_slabs > kMaxSlabs || d->axis < 0 || d->axis > 2)
         return set_err(s, ABD_E_INVALID, "abd_partition: n_slabs must be 1..64 and axis 0..2");
+    if (!s->group.empty())
+        return set_err(s, ABD_E_INVALID, "abd_partition: a batched world is partitioned by its scenes");
     s->axis = d->axis;
     s->n_slabs = d->n_slabs;
     s->slab_planes.clear();
@@ -576,3 +578,91 @@ extern "C" const char *abd_status_string(int c) {
 }
 
 extern "C" const char *abd_last_error(const abd_scene *s) { return s ? s->err.c_str() : "null scene"; }
+
+// ---------------------------------------------------------------------------
+// Batched world: many independent scenes in one scene object, one partition
+// per scene, every Newton phase of every scene in the same launches.
+// ---------------------------------------------------------------------------
+extern "C" int abd_scene_create_batch(const abd_scene_desc *descs, int32_t n, void *stream, abd_scene **out) {
+    if (!descs || !out || n < 1 || n > kMaxParts) return ABD_E_INVALID;
+    *out = nullptr;
+    const abd_scene_desc &d0 = descs[0];
+    std::vector<int32_t> mnv, mnt, bmesh, bkind, tris;
+    std::vector<double> xbar, dens, kap, q0, v0, om;
+    std::vector<int> group;
+    std::vector<int64_t> goff(1, 0);
+    int64_t nbt = 0;
+    for (int i = 0; i < n; ++i) {
+        const abd_scene_desc &d = descs[i];
+        if (d.n_bodies <= 0 || d.n_meshes <= 0 || !d.mesh_n_verts || !d.mesh_n_tris || !d.mesh_xbar ||
+            !d.mesh_tris || !d.body_mesh || !d.body_density || !d.body_kappa || !d.body_kind || !d.body_q0)
+            return ABD_E_INVALID;
+        // one set of ground planes and one gravity for the whole world
+        if (d.n_planes != d0.n_planes) return ABD_E_INVALID;
+        for (int k = 0; k < d.n_planes; ++k)
+            if (d.plane_axis[k] != d0.plane_axis[k] || d.plane_sign[k] != d0.plane_sign[k] ||
+                d.plane_offset[k] != d0.plane_offset[k])
+                return ABD_E_INVALID;
+        for (int k = 0; k < 3; ++k)
+            if (d.gravity[k] != d0.gravity[k]) return ABD_E_INVALID;
+        const int mesh_base = (int)mnv.size();
+        int64_t nvt = 0, ntt = 0;
+        for (int m = 0; m < d.n_meshes; ++m) {
+            if (d.mesh_n_verts[m] <= 0 || d.mesh_n_tris[m] < 0) return ABD_E_INVALID;
+            mnv.push_back(d.mesh_n_verts[m]);
+            mnt.push_back(d.mesh_n_tris[m]);
+            nvt += d.mesh_n_verts[m];
+            ntt += d.mesh_n_tris[m];
+        }
+        xbar.insert(xbar.end(), d.mesh_xbar, d.mesh_xbar + 3 * nvt);
+        tris.insert(tris.end(), d.mesh_tris, d.mesh_tris + 3 * ntt);
+        for (int b = 0; b < d.n_bodies; ++b) {
+            if (d.body_mesh[b] < 0 || d.body_mesh[b] >= d.n_meshes) return ABD_E_INVALID;
+            bmesh.push_back(mesh_base + d.body_mesh[b]);
+            bkind.push_back(d.body_kind[b]);
+            dens.push_back(d.body_density[b]);
+            kap.push_back(d.body_kappa[b]);
+            for (int k = 0; k < 12; ++k) {
+                q0.push_back(d.body_q0[12 * (size_t)b + k]);
+                v0.push_back(d.body_v0 ? d.body_v0[12 * (size_t)b + k] : 0.0);
+            }
+            for (int k = 0; k < 3; ++k) om.push_back(d.body_omega ? d.body_omega[3 * (size_t)b + k] : 0.0);
+            group.push_back(i);
+        }
+        nbt += d.n_bodies;
+        if (nbt >= (1ll << 31)) return ABD_E_INVALID;
+        goff.push_back(nbt);
+    }
+    abd_scene_desc D = d0;
+    D.n_meshes = (int32_t)mnv.size();
+    D.mesh_n_verts = mnv.data();
+    D.mesh_n_tris = mnt.data();
+    D.mesh_xbar = xbar.data();
+    D.mesh_tris = tris.data();
+    D.n_bodies = (int32_t)nbt;
+    D.body_mesh = bmesh.data();
+    D.body_density = dens.data();
+    D.body_kappa = kap.data();
+    D.body_kind = bkind.data();
+    D.body_q0 = q0.data();
+    D.body_v0 = v0.data();
+    D.body_omega = om.data();
+    int rc = abd_scene_create(&D, stream, out);
+    if (rc) return rc;
+    (*out)->group = std::move(group);
+    (*out)->group_off = std::move(goff);
+    return ABD_OK;
+}
+
+extern "C" int abd_batch_layout(const abd_scene *s, int64_t *body_off, int32_t cap, int32_t *n) {
+    if (!s || !n || cap < 0) return ABD_E_INVALID;
+    if (s->group.empty()) {
+        *n = 1;
+        if (body_off && cap >= 2) { body_off[0] = 0; body_off[1] = s->nb; }
+        return ABD_OK;
+    }
+    *n = (int32_t)s->group_off.size() - 1;
+    if (body_off)
+        for (int i = 0; i < std::min<int>((int)s->group_off.size(), cap); ++i) body_off[i] = s->group_off[i];
+    return ABD_OK;
+}

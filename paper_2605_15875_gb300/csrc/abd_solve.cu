@@ -126,13 +126,14 @@ __global__ void k_dqmax(int S_dyn, const int *__restrict__ slot_part, const doub
 }
 
 // Newton stopping test of every active partition, before its line search:
-// |dq|_inf / (h l) < eps_N ends the local solve.  Resets the per-iteration
-// TOI and |dq| accumulators.
-__global__ void k_newton_decide(int NP, PartState *part, double inv_hl, double tol) {
+// |dq|_inf / (h l) < eps_N ends the local solve (l the scale of the
+// partition's scene, PartState::inv_hl = 1 / (h l)).  Resets the
+// per-iteration TOI and |dq| accumulators.
+__global__ void k_newton_decide(int NP, PartState *part, double tol) {
     for (int p = threadIdx.x; p < NP; p += blockDim.x) {
         if (part[p].active) {
             part[p].newton_it++;
-            if (unord(part[p].dqmax) * inv_hl < tol) part[p].active = 0;
+            if (unord(part[p].dqmax) * part[p].inv_hl < tol) part[p].active = 0;
         }
         part[p].dqmax = 0ull;
         part[p].toi = ord(1.0);
@@ -308,7 +309,8 @@ namespace {
 struct Ctx {
     abd_scene *s;
     const abd_step_params *p;
-    double kB, l, half;
+    double kB, l, half;          // the whole scene's (slab partitions) or the largest over scenes (batched)
+    std::vector<double> kBp, lp;  // per partition: barrier stiffness and scene scale
     abd_step_stats *st;
     int precision;
     DBuf alphas, nh0, decided, pending;
@@ -390,7 +392,11 @@ int compute_masks(abd_scene *s, double h, const std::vector<double> &box, const 
 }
 
 // Build the slot tables of one step from the body masks (nparts partitions).
+// In a batched world (s->group non-empty) partition p holds the dynamic and
+// kinematic bodies of scene p (masks then have one bit), and a static body
+// serves only its own scene's partition.
 int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
+    const bool batched = !s->group.empty() && nparts > 1;
     ++s->w.gen;
     World &w = s->w;
     w.NP = nparts;
@@ -405,7 +411,7 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
     std::vector<std::vector<int>> reps(nsh);
     for (int p = 0; p < nparts; ++p)
         for (int b = 0; b < s->nb; ++b) {
-            if (s->kind[b] == ABD_STATIC || !((mask[b] >> p) & 1)) continue;
+            if (s->kind[b] == ABD_STATIC || !(batched ? s->group[b] == p && mask[b] : (mask[b] >> p) & 1)) continue;
             int sl = (int)w.h_slot_body.size();
             w.h_slot_body.push_back(b);
             w.h_slot_part.push_back(p);
@@ -419,11 +425,13 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
     w.h_part_off.assign(nparts + 1, 0);
     for (int i = 0; i < w.S_dyn; ++i) w.h_part_off[w.h_slot_part[i] + 1]++;
     for (int p = 0; p < nparts; ++p) w.h_part_off[p + 1] += w.h_part_off[p];
+    std::vector<int> static_grp;
     for (int b = 0; b < s->nb; ++b)
         if (s->kind[b] == ABD_STATIC) {
             w.h_slot_body.push_back(b);
             w.h_slot_part.push_back(-1);
             w.h_slot_mask.push_back(0);
+            static_grp.push_back(batched ? s->group[b] : -1);
         }
     w.S_all = (int)w.h_slot_body.size();
     w.h_slot_voff.assign(w.S_all + 1, 0);
@@ -456,7 +464,7 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
         (rc = h2d(s, w.rep_off, w.h_rep_off)) || (rc = h2d(s, w.rep_slot, w.h_rep_slot)) ||
         (rc = h2d(s, w.body_rep, w.h_body_rep)) || (rc = h2d(s, w.body_slot, w.h_body_slot)) ||
         (rc = h2d(s, w.part_off, w.h_part_off)) || (rc = h2d(s, w.slot_cbase, w.h_slot_cbase)) ||
-        (rc = h2d(s, w.cl_info, cl_info)))
+        (rc = h2d(s, w.cl_info, cl_info)) || (rc = h2d(s, w.static_grp, static_grp)))
         return rc;
     size_t S = (size_t)(w.S_all ? w.S_all : 1), Sd = (size_t)(w.S_dyn ? w.S_dyn : 1);
     size_t SV = (size_t)(w.SV ? w.SV : 1), NS = (size_t)(nsh ? nsh : 1);
@@ -583,34 +591,33 @@ int enqueue_iteration(Ctx &C, bool static_bp, Status *hs) {
         return rc;
     }
     // assemble, precondition, solve
-    if ((rc = launch_assemble_async(s, C.precision, p, C.kB))) return rc;
+    if ((rc = launch_assemble_async(s, C.precision, p))) return rc;
     if ((rc = launch_pcg_async(s, C.precision, p))) return rc;
     // Newton stopping test before the line search
     ABD_LAUNCH(s, k_dqmax, grid_for(w.S_dyn, 128), 128, 0, s->stream, w.S_dyn, P<int>(w.slot_part), P<double>(w.dq),
                P<PartState>(w.part));
-    ABD_LAUNCH(s, k_newton_decide, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), 1.0 / (p->h * C.l),
-               p->newton_tol);
+    ABD_LAUNCH(s, k_newton_decide, 1, 256, 0, s->stream, w.NP, P<PartState>(w.part), p->newton_tol);
     // CCD along q -> q + dq over the swept candidates; line-search list
     if ((rc = launch_transform(s, P<double>(w.q), P<double>(w.x1), P<double>(w.dq), 1)) ||
         (rc = launch_boxes(s, true, C.half, 1, P<double>(w.dq))) || (rc = launch_l1_async(s, true)) ||
         (rc = launch_l2_async(s, true, C.half)) || (rc = launch_ccd_async(s, p, true)))
         return rc;
     // backtracking on the FP64 energy: two passes of kLS trial steps
-    ABD_LAUNCH(s, k_ls_reset, 1, 64, 0, s->stream, w.NP, P<int>(C.nh0), P<int>(C.decided));
+    ABD_LAUNCH(s, k_ls_reset, 1, 256, 0, s->stream, w.NP, P<int>(C.nh0), P<int>(C.decided));
     for (int pass = 0; pass < 2; ++pass) {
         cudaMemsetAsync(&dc->pending, 0, sizeof(int), s->stream);
         cudaMemsetAsync(&dc->ls_live, 0, sizeof(int), s->stream);
-        ABD_LAUNCH(s, k_ls_alphas, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
+        ABD_LAUNCH(s, k_ls_alphas, 1, 256, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
                    P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->ls_live);
-        if ((rc = launch_energy_async(s, p, C.kB, P<double>(C.alphas)))) return rc;
-        ABD_LAUNCH(s, k_ls_select, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
+        if ((rc = launch_energy_async(s, p, P<double>(C.alphas)))) return rc;
+        ABD_LAUNCH(s, k_ls_select, 1, 256, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
                    P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->pending);
     }
     ABD_LAUNCH(s, k_check_bad, 1, 1, 0, s->stream, dc, w.cap_l1, w.cap_cand, w.cap_act, w.cap_ls, w.cap_cp,
                d_iters + kPcgOver);
     ABD_LAUNCH(s, k_update_q, grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream, w.S_dyn,
                P<int>(w.slot_part), P<PartState>(w.part), P<int>(C.decided), dc, P<double>(w.dq), P<double>(w.q));
-    ABD_LAUNCH(s, k_mark_updated, 1, 64, 0, s->stream, w.NP, P<int>(C.decided), dc);
+    ABD_LAUNCH(s, k_mark_updated, 1, 256, 0, s->stream, w.NP, P<int>(C.decided), dc);
     return enqueue_status(s, hs);
 }
 
@@ -679,6 +686,8 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         memset(&ps[i], 0, sizeof(PartState));
         ps[i].active = run[i];
         ps[i].toi = 0x3FF0000000000000ull;
+        ps[i].kB = C.kBp[i];
+        ps[i].inv_hl = 1.0 / (p->h * C.lp[i]);
     }
     if ((rc = write_parts(s, ps))) return rc;
     Counters *dc = P<Counters>(w.ctr);
@@ -709,15 +718,15 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         for (int guard = 0; hs->c.pending > 0 && guard < 64; ++guard) {
             cudaMemsetAsync(&dc->pending, 0, sizeof(int), s->stream);
             cudaMemsetAsync(&dc->ls_live, 0, sizeof(int), s->stream);
-            ABD_LAUNCH(s, k_ls_alphas, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
+            ABD_LAUNCH(s, k_ls_alphas, 1, 256, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
                        P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->ls_live);
-            if ((rc = launch_energy_async(s, p, C.kB, P<double>(C.alphas)))) return rc;
-            ABD_LAUNCH(s, k_ls_select, 1, 64, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
+            if ((rc = launch_energy_async(s, p, P<double>(C.alphas)))) return rc;
+            ABD_LAUNCH(s, k_ls_select, 1, 256, 0, s->stream, w.NP, P<PartState>(w.part), P<int>(C.nh0),
                        P<int>(C.decided), P<double>(C.alphas), p->max_halvings, &dc->pending);
             ABD_LAUNCH(s, k_update_q, grid_for(12 * (int64_t)w.S_dyn, 256), 256, 0, s->stream, w.S_dyn,
                        P<int>(w.slot_part), P<PartState>(w.part), P<int>(C.decided), dc, P<double>(w.dq),
                        P<double>(w.q));
-            ABD_LAUNCH(s, k_mark_updated, 1, 64, 0, s->stream, w.NP, P<int>(C.decided), dc);
+            ABD_LAUNCH(s, k_mark_updated, 1, 256, 0, s->stream, w.NP, P<int>(C.decided), dc);
             if ((rc = enqueue_status(s, hs)) || (rc = sync(s))) return rc;
         }
         static_bp = false;
@@ -872,22 +881,41 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
     if ((rc = cuda_check(s, cudaMemcpyAsync(vh.data(), s->dev.v.p, 96 * (size_t)s->nb, cudaMemcpyDeviceToHost,
                                             s->stream), "v")) || (rc = sync(s)))
         return rc;
-    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-    double msum = 0.0;
-    int nd = 0, ndof = 0;
-    for (int b = 0; b < s->nb; ++b) {
-        for (int k = 0; k < 3; ++k) {
-            lo[k] = std::min(lo[k], box[6 * (size_t)b + k]);
-            hi[k] = std::max(hi[k], box[6 * (size_t)b + 3 + k]);
+    // scene scale l (diagonal of the AABB of every body at the step start,
+    // Eq. 8's normalisation) and barrier stiffness (explicit, else 10 x mean
+    // dynamic mass x |g| / dhat) over the bodies [b0, b1)
+    const double gn = std::sqrt(s->g[0] * s->g[0] + s->g[1] * s->g[1] + s->g[2] * s->g[2]);
+    auto scale_of = [&](int64_t b0, int64_t b1, double &l, double &kB) {
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, msum = 0.0;
+        int nd = 0, ndof = 0;
+        for (int64_t b = b0; b < b1; ++b) {
+            for (int k = 0; k < 3; ++k) {
+                lo[k] = std::min(lo[k], box[6 * (size_t)b + k]);
+                hi[k] = std::max(hi[k], box[6 * (size_t)b + 3 + k]);
+            }
+            if (s->kind[b] == ABD_DYNAMIC) { msum += s->mass[b]; ++nd; }
+            if (s->kind[b] != ABD_STATIC) ++ndof;
         }
-        if (s->kind[b] == ABD_DYNAMIC) { msum += s->mass[b]; ++nd; }
-        if (s->kind[b] != ABD_STATIC) ++ndof;
+        l = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                      (hi[2] - lo[2]) * (hi[2] - lo[2]));
+        kB = p->kappa_barrier > 0.0 ? p->kappa_barrier : 10.0 * (nd ? msum / nd : 1.0) * gn / p->dhat;
+        return ndof;
+    };
+    const bool batched = !s->group.empty();
+    const int NG = batched ? (int)s->group_off.size() - 1 : 0;
+    int ndof = scale_of(0, s->nb, C.l, C.kB);
+    if (batched) {
+        // every scene of a batched world keeps its own scale and stiffness,
+        // so its step is the one it would take alone
+        C.lp.resize(NG);
+        C.kBp.resize(NG);
+        C.l = C.kB = 0.0;
+        for (int g = 0; g < NG; ++g) {
+            scale_of(s->group_off[g], s->group_off[g + 1], C.lp[g], C.kBp[g]);
+            C.l = std::max(C.l, C.lp[g]);
+            C.kB = std::max(C.kB, C.kBp[g]);
+        }
     }
-    C.l = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
-                    (hi[2] - lo[2]) * (hi[2] - lo[2]));
-    C.kB = p->kappa_barrier > 0.0 ? p->kappa_barrier
-                                  : 10.0 * (nd ? msum / nd : 1.0) *
-                                        std::sqrt(s->g[0] * s->g[0] + s->g[1] * s->g[1] + s->g[2] * s->g[2]) / p->dhat;
     if (ndof == 0) {
         // every body is static: the step has no unknowns and nothing moves
         st->l = C.l; st->kappa_barrier = C.kB; st->n_partitions = 1;
@@ -899,12 +927,21 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
     }
     std::vector<uint64_t> mask;
     double wov = 0.0;
-    int saved = s->n_slabs;
-    if (force_mono) s->n_slabs = 1;
-    rc = compute_masks(s, p->h, box, vh, mask, wov);
-    int N = s->n_slabs;
-    s->n_slabs = saved;
-    if (rc) return rc;
+    int N = 1;
+    if (batched) {
+        mask.assign(s->nb, 0);
+        for (int b = 0; b < s->nb; ++b) mask[b] = s->kind[b] != ABD_STATIC ? 1 : 0;
+        N = NG;
+    } else {
+        int saved = s->n_slabs;
+        if (force_mono) s->n_slabs = 1;
+        rc = compute_masks(s, p->h, box, vh, mask, wov);
+        N = s->n_slabs;
+        s->n_slabs = saved;
+        if (rc) return rc;
+        C.lp.assign(N, C.l);
+        C.kBp.assign(N, C.kB);
+    }
     if ((rc = build_world(s, mask, N))) return rc;
     st->l = C.l; st->kappa_barrier = C.kB; st->w = wov;
     st->n_partitions = N; st->n_shared = w.nsh; st->n_slots = w.S_dyn;
@@ -1030,6 +1067,7 @@ int step_impl(abd_scene *s, const abd_step_params *p, abd_step_stats *st, bool f
     st->t_total_ms = now_ms() - T0;
     st->kernel_launches = s->n_launches - L0;
     if (!force_mono && (s->pd_kp != 0.0 || s->pd_kd != 0.0)) pd_balance(s, C, N);
+    s->last_part_newton = C.part_newton;
     return status;
 }
 
@@ -1123,5 +1161,13 @@ extern "C" int abd_partition_get(const abd_scene *s, int32_t part, int32_t *bodi
     }
     *n = cnt;
     *n_shared = cs;
+    return ABD_OK;
+}
+
+extern "C" int abd_partition_newton(const abd_scene *s, int32_t *iters, int32_t cap, int32_t *n) {
+    if (!s || !n || cap < 0) return ABD_E_INVALID;
+    *n = (int32_t)s->last_part_newton.size();
+    if (iters)
+        for (int i = 0; i < std::min<int>(*n, cap); ++i) iters[i] = (int32_t)s->last_part_newton[i];
     return ABD_OK;
 }

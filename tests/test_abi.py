@@ -3,6 +3,7 @@ declared in include/abd.h (no compute call: no GPU needed)."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -154,3 +155,28 @@ int main(void) {
     assert d0 == -0.25 and d1 == 0.0  # -(kp T): the plane moves toward the slower slab
     assert lines[2] == "ok|penetration detected"
     assert lines[3] == "-1"
+
+
+def test_batched_world_rejects_mismatched_scenes_before_device_work():
+    """abd_scene_create_batch checks its scenes before any device work: one
+    set of ground planes and one gravity for the whole world, 1..256 scenes;
+    the layout and Newton queries reject NULL handles."""
+    import ctypes
+    from paper_2605_15875_gb300 import abd, build, scenes
+    build.build()
+    L = abd.load()
+    a = scenes.random_pile(1, 8, levels=(1,))
+    b = scenes.cube_stack(ground=False)
+    descs = (abd.SceneDesc * 2)(abd.scene_desc(a), abd.scene_desc(b))
+    h = ctypes.c_void_p()
+    assert L.abd_scene_create_batch(ctypes.cast(descs, ctypes.c_void_p), 2, None, ctypes.byref(h)) == -1
+    c = scenes.random_pile(2, 8, levels=(1,))
+    c.gravity = np.array([0.0, -1.0, 0.0])
+    descs = (abd.SceneDesc * 2)(abd.scene_desc(a), abd.scene_desc(c))
+    assert L.abd_scene_create_batch(ctypes.cast(descs, ctypes.c_void_p), 2, None, ctypes.byref(h)) == -1
+    assert L.abd_scene_create_batch(ctypes.cast(descs, ctypes.c_void_p), 0, None, ctypes.byref(h)) == -1
+    assert L.abd_scene_create_batch(ctypes.cast(descs, ctypes.c_void_p), 257, None, ctypes.byref(h)) == -1
+    n = ctypes.c_int32()
+    assert L.abd_batch_layout(None, None, 0, ctypes.byref(n)) == -1
+    assert L.abd_partition_newton(None, None, 0, ctypes.byref(n)) == -1
+    assert L.abd_scene_reserve(None, 16) == -1

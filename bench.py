@@ -43,11 +43,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=24)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
+                    help="c2: 512 spheres on 4 slabs (the default line); c4: the 5000-body funnel")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-serving", action="store_true", help="skip the served leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-subdomain leg")
+    ap.add_argument("--no-sweep", action="store_true", help="serving: closed batch only, no Poisson sweep")
     ap.add_argument("--batch-steps", type=int, default=6, help="timed steps of the batched leg")
     ap.add_argument("--no-fixed-rho", action="store_true", help="skip the fixed-rho comparison leg")
     ap.add_argument("--no-graph", action="store_true",
@@ -280,7 +283,7 @@ def run_ours(args, rank, world):
     serving = batched = None
     if not args.no_serving:
         try:
-            serving = serve_legs(abd)
+            serving = serve_legs(abd, sweep=not args.no_sweep)
         except Exception as e:
             errors["serving"] = f"{type(e).__name__}: {e}"
     if not args.no_batched:
@@ -330,15 +333,42 @@ def run_ours(args, rank, world):
     return out
 
 
+def _keyed(reqs):
+    """Each scene of the serving workload as two keyed requests: the first
+    (with the scene) advances half of its steps, the second (key only)
+    continues from the resident state for the rest."""
+    out = []
+    for key, (sa, k) in enumerate(reqs, start=1):
+        k1 = max(1, k // 2)
+        out.append((key, sa, k1))
+        if k - k1 > 0:
+            out.append((key, None, k - k1))
+    return out
+
+
+def _body_steps(reqs, infos):
+    """Dynamic-body steps done by requests (key, scene or None, steps) or
+    (scene, steps): a keyed request without a scene counts its key's scene."""
+    nd, total = {}, 0
+    for r, i in zip(reqs, infos):
+        key, sa = (r[0], r[1]) if len(r) == 3 else (None, r[0])
+        if sa is not None:
+            nd[key] = sa.n_dynamic
+        total += (sa.n_dynamic if sa is not None else nd[key]) * i.get("steps_done", r[-1])
+    return total
+
+
 def _serve(abd, reqs, n_streams, params):
+    """Closed batch: every request submitted at once (continuous admission),
+    resident scenes released at the end.  reqs: (key, scene or None, steps)."""
     srv = abd.Server(n_streams=n_streams)
     t0 = time.perf_counter()
-    ts = [srv.submit(sa, k, params) for sa, k in reqs]
+    ts = [srv.submit(sa, k, params, key=key) for key, sa, k in reqs]
     infos = [srv.wait(t) for t in ts]
     dt = time.perf_counter() - t0
     lat = np.concatenate([srv.latencies(t) for t in ts])
     srv.close()
-    bs = sum(sa.n_dynamic * k for sa, k in reqs)
+    bs = _body_steps(reqs, infos)
     return {"value": round(bs / dt, 2), "unit": "body-steps/s", "wall_s": round(dt, 3), "body_steps": int(bs),
             "p50_step_ms": round(float(np.percentile(lat, 50)), 3),
             "p99_step_ms": round(float(np.percentile(lat, 99)), 3),
@@ -359,23 +389,25 @@ def open_loop(server, reqs, params, arrivals, clock=time.perf_counter, sleep=tim
     whether or not earlier requests are done (they keep running on the
     server's workers meanwhile), then every request is waited for.  Response
     time = queue + run of a request (submit to done); step latency = each
-    abd_step call of each request.  The server is closed on return."""
+    abd_step call of each request.  reqs: (scene, steps) or (key, scene or
+    None, steps).  The server is closed on return."""
     lags, ts = [], []
     try:
         t0 = clock()
-        for (sa, k), ta in zip(reqs, arrivals):
+        for r, ta in zip(reqs, arrivals):
+            key, sa, k = r if len(r) == 3 else (None, r[0], r[1])
             d = t0 + ta - clock()
             if d > 0:
                 sleep(d)
             lags.append(clock() - (t0 + ta))
-            ts.append(server.submit(sa, k, params))
+            ts.append(server.submit(sa, k, params) if key is None else server.submit(sa, k, params, key=key))
         infos = [server.wait(t) for t in ts]
         span = clock() - t0
         lat = np.concatenate([server.latencies(t) for t in ts])
     finally:
         server.close()
     resp = [i["queue_ms"] + i["run_ms"] for i in infos]
-    bs = sum(sa.n_dynamic * k for sa, k in reqs)
+    bs = _body_steps(reqs, infos)
     return {"value": round(bs / span, 2), "unit": "body-steps/s", "span_s": round(span, 4),
             "p50_step_ms": round(float(np.percentile(lat, 50)), 3),
             "p99_step_ms": round(float(np.percentile(lat, 99)), 3),
@@ -402,41 +434,50 @@ def poisson_sweep(make_server, reqs, params, capacity_rps, fractions=(0.25, 0.5,
     return out
 
 
-def serve_legs(abd):
-    """Served leg (a bounded sample of the serving workload), mixed
-    precision: every request submitted at once to the serving runtime (closed
-    batch, continuous admission), then the same requests under Poisson
-    arrivals at four rates."""
+def serve_legs(abd, n_scenes=256, lo=8, hi=4096, sweep=True):
+    """Served leg, mixed precision: the serving workload (`n_scenes` scenes
+    of lo..hi bodies, cube stacks and sphere piles, 1-10 steps each), every
+    scene as two keyed requests on a resident scene (the second continues
+    from the state the first left on the device); a closed batch (every
+    request submitted at once, continuous admission), the plain FP64 path on
+    the same requests one at a time, then, with `sweep`, the same requests
+    under Poisson arrivals at four rates."""
     from paper_2605_15875_gb300 import scenes
     p = abd.default_params(precision=abd.MIXED, pcg_rtol=1e-5)
     p64 = abd.default_params(precision=abd.FP64, pcg_rtol=1e-12)
-    reqs = scenes.serving_requests(seed=0, n_scenes=64, lo=8, hi=512)
+    reqs = _keyed(scenes.serving_requests(seed=0, n_scenes=n_scenes, lo=lo, hi=hi))
     serving = _serve(abd, reqs, 4, p)
     plain = _serve(abd, reqs, 1, p64)
     serving["plain_fp64_one_at_a_time"] = plain["value"]
     serving["speedup_vs_plain_fp64"] = round(serving["value"] / plain["value"], 3)
-    serving["sample"] = "64 requests: scenes of 8-512 bodies (log-uniform; cube stacks and sphere piles), 1-10 steps"
-    cap_rps = len(reqs) / serving["wall_s"]
-    serving["poisson"] = poisson_sweep(lambda: abd.Server(n_streams=4), reqs, p, cap_rps)
-    serving["poisson_note"] = ("open loop, 4 streams, the same 64 requests; lambda relative to the closed-batch "
-                               "capacity above (requests/s)")
+    serving["sample"] = (f"{n_scenes} scenes of {lo}-{hi} bodies (log-uniform; cube stacks and sphere piles), "
+                         "1-10 steps each as two keyed requests on a resident scene")
+    if sweep:
+        cap_rps = len(reqs) / serving["wall_s"]
+        serving["poisson"] = poisson_sweep(lambda: abd.Server(n_streams=4), reqs, p, cap_rps)
+        serving["poisson_note"] = ("open loop, 4 streams, the same requests; lambda relative to the closed-batch "
+                                   "capacity above (requests/s)")
     return serving
 
 
-def batched_leg(abd, torch, stream, flush, steps, warmup, n_scenes=64, lo=16, hi=2048, seed=0):
+def batched_leg(abd, torch, stream, flush, steps, warmup, n_scenes=64, lo=16, hi=2048, seed=0, pre_steps=12):
     """Uneven subdomains packed into one batched world (one partition per
     subdomain, every Newton phase of every subdomain in the same launches,
     the steady-state iteration replayed as a CUDA graph), mixed precision,
     against the plain FP64 path stepping each subdomain alone, one at a time,
-    over the same steps.  Each side warms up on `warmup` steps whose state is
-    then restored; L2 is flushed between timed steps (outside the timing)."""
+    over the same steps.  The world first takes `pre_steps` untimed steps,
+    in which the piles land and come into contact; from that state each side
+    warms up on `warmup` steps whose state is then restored, and times
+    `steps` steps; L2 is flushed between timed steps (outside the timing)."""
     from paper_2605_15875_gb300 import scenes
     subs = scenes.batched_subdomains(seed=seed, n_scenes=n_scenes, lo=lo, hi=hi, levels=(1, 2, 3))
     nb = sum(sa.n_dynamic for sa in subs)
     pm = abd.default_params(precision=abd.MIXED, pcg_rtol=1e-5)
     p64 = abd.default_params(precision=abd.FP64, pcg_rtol=1e-12)
 
-    def run(sc, p, prof=False):
+    def run(sc, p, prof=False, start=None):
+        if start is not None:
+            sc.set_state(*start)
         q0, v0 = sc.state()
         for _ in range(warmup):
             sc.step(p)
@@ -456,15 +497,19 @@ def batched_leg(abd, torch, stream, flush, steps, warmup, n_scenes=64, lo=16, hi
         return lat, sts
 
     world = abd.Scene(subs, stream=int(stream.cuda_stream))
+    for _ in range(pre_steps):  # the piles settle into contact (untimed)
+        world.step(pm)
+    qw, vw = world.state()
+    off = world.layout()
     lat, sts = run(world, pm, prof=True)
     names = ["pcg", "pair_moll", "pair_assemble", "slot_assemble", "l2_static", "l2_swept", "ccd", "energy"]
     ks = {n: world.kernel_stats(n) for n in names}
     world.close()
     t_b = sum(lat) / 1e3
     alone_ms, alone_status = 0.0, 0
-    for sa in subs:
+    for i, sa in enumerate(subs):
         sc = abd.Scene(sa, stream=int(stream.cuda_stream))
-        la, sa_st = run(sc, p64)
+        la, sa_st = run(sc, p64, start=(qw[off[i]:off[i + 1]], vw[off[i]:off[i + 1]]))
         alone_ms += sum(la)
         alone_status = max([alone_status] + [x["status"] for x in sa_st])
         sc.close()
@@ -482,8 +527,9 @@ def batched_leg(abd, torch, stream, flush, steps, warmup, n_scenes=64, lo=16, hi
                             for n, v in ks.items()},
             "kernels_ms": {n: round(v[1], 3) for n, v in ks.items()},
             "sample": f"{n_scenes} subdomains of {lo}-{hi} noisy icospheres (log-uniform counts, levels 1-3, "
-                      f"densities log-uniform 1e2-1e4, seed {seed}), one batched world; {steps} timed steps "
-                      f"after {warmup} warm-up steps (state restored)"}
+                      f"densities log-uniform 1e2-1e4, seed {seed}), one batched world; steps {pre_steps}.."
+                      f"{pre_steps + steps - 1} timed (the piles in contact) after {warmup} warm-up steps from "
+                      f"step {pre_steps} (state restored); the FP64 runs start from the same state"}
 
 
 def host_cpu():
@@ -587,6 +633,96 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_c4(args, rank, world):
+    """The large funnel workload: 5000 level-3 noisy icospheres (6.4 M
+    triangles) starting packed in the funnel above the chamber with its two
+    perforated turntables turning at +-1 rad/s; 2 and 8 slab partitions along
+    x (equal widths over the bodies' extent, rebuilt every step), mixed
+    precision against FP64.  Each run takes `warmup` untimed steps from the
+    packed start, then times `steps` steps (CUDA events, L2 flushed between
+    steps)."""
+    import torch
+    from paper_2605_15875_gb300 import abd, build as B, scenes
+    B.build()
+    abd.load()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    sa = scenes.funnel_scene(dense=True)
+    nb = sa.n_dynamic
+    names = ["pcg", "pair_moll", "pair_assemble", "slot_assemble", "l2_static", "l2_swept", "ccd", "energy"]
+    peak, peak_kind = measured_peaks()
+    legs, headline, clk_summary = {}, None, None
+    for slabs in (8, 2):
+        for prec in (abd.MIXED, abd.FP64):
+            key = f"{slabs}slabs_{'mixed' if prec == abd.MIXED else 'fp64'}"
+            try:
+                sc = abd.Scene(sa, stream=int(stream.cuda_stream))
+                sc.partition(n_slabs=slabs, axis=0)
+                p = abd.default_params(precision=prec, pcg_rtol=1e-5 if prec == abd.MIXED else 1e-12)
+                for _ in range(args.warmup):
+                    sc.step(p)
+                sc.profile(True)
+                lat, sts = [], []
+                torch.cuda.synchronize()
+                with Clocks(dev) as clk:
+                    for _ in range(args.steps):
+                        flush.zero_()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        sts.append(sc.step(p))
+                        e1.record(stream)
+                        e1.synchronize()
+                        lat.append(e0.elapsed_time(e1))
+                ks = {n: sc.kernel_stats(n) for n in names}
+                sc.close()
+                leg = {"value": round(nb * len(lat) / (sum(lat) / 1e3), 3), "unit": "body-steps/s",
+                       "ms_per_step": round(sum(lat) / len(lat), 2), "steps": len(lat),
+                       "admm_iters": [x["admm_iters"] for x in sts], "newton_iters": [x["newton_iters"] for x in sts],
+                       "candidates_peak": int(max(x["n_candidates_peak"] for x in sts)),
+                       "active_pairs_peak": int(max(x["n_active_peak"] for x in sts)),
+                       "min_distance_min": float(min(x["min_distance"] for x in sts)),
+                       "worst_status": int(max(x["status"] for x in sts)),
+                       "n_slots": int(sts[-1]["n_slots"]), "n_shared": int(sts[-1]["n_shared"]),
+                       "pcg_cluster": int(max(x["pcg_cluster"] for x in sts)),
+                       "kernels_ms": {n: round(v[1], 3) for n, v in ks.items()},
+                       "kernels_gbs": {n: (round(v[2] / (v[1] / 1e3) / 1e9, 2) if v[1] > 0 and v[2] > 0 else None)
+                                       for n, v in ks.items()},
+                       "clocks": clk.summary()}
+                dom = max(ks, key=lambda n: ks[n][1])
+                n_l, ms_l, by_l = ks[dom]
+                ach = (by_l / (ms_l / 1e3)) / 1e9 if ms_l > 0 else 0.0
+                leg["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": round(ach, 2), "peak": peak,
+                                   "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": peak_kind,
+                                   "bytes_per_launch": round(by_l / max(1, n_l), 1), "launches": n_l,
+                                   "avg_launch_us": round(1e3 * ms_l / max(1, n_l), 3)}
+                legs[key] = leg
+                if headline is None and prec == abd.MIXED:
+                    headline, clk_summary = (key, leg), leg["clocks"]
+            except Exception as e:
+                legs[key] = {"error": f"{type(e).__name__}: {e}"}
+    if rank != 0:
+        return None
+    key, h = headline if headline else ("none", {"value": None, "ms_per_step": None, "roofline": None})
+    for slabs in (8, 2):
+        m, f = legs.get(f"{slabs}slabs_mixed", {}), legs.get(f"{slabs}slabs_fp64", {})
+        if m.get("value") and f.get("value"):
+            m["speedup_vs_fp64"] = round(m["value"] / f["value"], 3)
+    return {"metric": METRIC, "value": h["value"], "unit": "body-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "funnel_5000_icosphereL3_dense_start", "bodies": nb,
+                       "triangles": sa.total_tris(), "headline_leg": key,
+                       "start": "bodies packed in the funnel (lattice pitch 2.2 r + 2 mm), turntables at +-1 rad/s",
+                       "window": f"steps {args.warmup}..{args.warmup + args.steps - 1} from the packed start",
+                       "l2": "flushed between timed steps (256 MB write)",
+                       "paper_scale": "Table 1 'Pokemon': 5.2K bodies, 5.7M triangles, 59.8M candidates and 40.1K "
+                                      "contacts at peak, 2 workers (RTX 4090 each), h = 0.0125"},
+            "legs": legs, "roofline": h.get("roofline"), "clocks": clk_summary}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -595,7 +731,12 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl")
-    out = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world)
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    elif args.workload == "c4":
+        out = run_c4(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
     if rank == 0 and out is not None:
         print(json.dumps(out))
     if world > 1 and args.impl == "ours":

@@ -120,7 +120,9 @@ typedef struct {
     double theta;                  /* Eq. 8 threshold */
     double newton_tol;             /* |dq|_inf / (h l) < newton_tol ends a local solve */
     int32_t max_admm, max_newton, max_halvings;
-    double pcg_rtol;               /* relative residual of the block-Jacobi PCG */
+    double pcg_rtol;               /* PCG stop: FP64, |r|_2 <= pcg_rtol |r_0|_2; mixed, the block-Jacobi
+                                      preconditioned residual z = P r (in the units of q, body by body)
+                                      |z|_inf <= pcg_rtol |z_0|_inf */
     int32_t pcg_max;
     double accd_s, accd_c;         /* additive CCD gap fraction and step factor */
     int32_t dt_split_max;          /* adaptive time stepping (Sec. 4.2, Fig. 4): when the merge check
@@ -356,6 +358,29 @@ int abd_server_create(const abd_server_desc *desc, abd_server **out);
  * *ticket identifies the request in the calls below. */
 int abd_server_submit(abd_server *srv, const abd_scene_desc *scene, const abd_partition_desc *part,
                       const abd_step_params *params, int32_t n_steps, int64_t *ticket);
+
+/* Queue a request on a resident scene named by `key` (non-zero).  The first
+ * request of a key gives the scene (and optionally its partition; arrays
+ * copied before return); it builds the scene, which then stays on the
+ * device after the request -- its state q, v and its workspace (consensus z,
+ * dual u, pair lists, captured Newton-iteration graph) -- on a CUDA stream of
+ * its own.  Later requests of the key pass scene = NULL and continue from the
+ * state the previous one left; requests of one key run one at a time in
+ * submission order, while other keys' requests overlap with them.  A resident
+ * scene holds its admission estimate of the HBM budget; when a request does
+ * not fit, idle resident scenes are evicted, least recently used first
+ * (their state is kept in host memory and the scene is rebuilt at its next
+ * request).  ABD_E_INVALID for key 0, a first request without a scene, or a
+ * scene given again for a live key.  Results, latencies and errors are read
+ * per ticket as for abd_server_submit.  Not in the paper: this is the
+ * library's serving runtime. */
+int abd_server_submit_keyed(abd_server *srv, int64_t key, const abd_scene_desc *scene,
+                            const abd_partition_desc *part, const abd_step_params *params, int32_t n_steps,
+                            int64_t *ticket);
+
+/* Free the resident scene of `key` once its queued requests are done (its
+ * key may then name a new scene).  ABD_E_INVALID for an unknown key. */
+int abd_server_release(abd_server *srv, int64_t key);
 
 /* Current state of a request (non-blocking), or, for abd_server_wait, its
  * state once it is done.  ABD_E_INVALID for an unknown ticket. */

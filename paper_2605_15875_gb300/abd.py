@@ -84,7 +84,8 @@ EXPORTS = ["abd_scene_create", "abd_scene_destroy", "abd_scene_counts", "abd_bod
            "abd_last_error", "abd_candidates_noalloc", "abd_partition_get", "abd_server_create",
            "abd_server_submit", "abd_server_poll", "abd_server_wait", "abd_server_result", "abd_server_latencies",
            "abd_server_error", "abd_server_destroy", "abd_partition_planes", "abd_pd_update", "abd_scene_reserve",
-           "abd_scene_create_batch", "abd_batch_layout", "abd_partition_newton"]
+           "abd_scene_create_batch", "abd_batch_layout", "abd_partition_newton",
+           "abd_server_submit_keyed", "abd_server_release"]
 
 _lib = None
 
@@ -130,6 +131,8 @@ def load(path: Optional[str] = None):
     L.abd_pd_update.argtypes = [C.c_int32, vp, vp, C.c_double, C.c_double, vp, vp]
     L.abd_server_create.argtypes = [C.POINTER(ServerDesc), C.POINTER(vp)]
     L.abd_server_submit.argtypes = [vp, C.POINTER(SceneDesc), vp, vp, C.c_int32, C.POINTER(i64)]
+    L.abd_server_submit_keyed.argtypes = [vp, i64, vp, vp, vp, C.c_int32, C.POINTER(i64)]
+    L.abd_server_release.argtypes = [vp, i64]
     L.abd_server_poll.argtypes = [vp, i64, C.POINTER(RequestInfo)]
     L.abd_server_wait.argtypes = [vp, i64, C.POINTER(RequestInfo)]
     L.abd_server_result.argtypes = [vp, i64, vp, vp, i64]
@@ -346,22 +349,40 @@ class Server:
         rc = L.abd_server_create(C.byref(d), C.byref(h))
         if rc != 0:
             raise AbdError(f"abd_server_create failed: {L.abd_status_string(rc).decode()} ({rc})")
-        self.L, self.h, self._n = L, h, {}
+        self.L, self.h, self._n, self._nb_key = L, h, {}, {}
 
     def submit(self, sa, n_steps, params: Optional[StepParams] = None, n_slabs=1, axis=0, planes=None,
-               alpha=2.0, w_min=0.0) -> int:
-        d = scene_desc(sa)
+               alpha=2.0, w_min=0.0, key: Optional[int] = None) -> int:
+        """Queue `n_steps` steps of scene `sa`.  With `key`, the scene stays
+        resident under that key (abd_server_submit_keyed): give `sa` on the
+        key's first request and None on later ones, which continue from the
+        state the previous request left."""
+        pr = default_params() if params is None else params
+        t = C.c_int64()
+        if sa is None and key is None:
+            raise AbdError("a request without a scene needs the key of a resident scene")
+        d = None if sa is None else scene_desc(sa)
         arr = None if planes is None else np.ascontiguousarray(planes, dtype=np.float64)
         pd = PartitionDesc(axis=axis, n_slabs=n_slabs, planes=None if arr is None else arr.ctypes.data,
                            alpha=alpha, w_min=w_min)
-        pr = default_params() if params is None else params
-        t = C.c_int64()
-        rc = self.L.abd_server_submit(self.h, C.byref(d), C.cast(C.pointer(pd), C.c_void_p),
-                                      C.cast(C.pointer(pr), C.c_void_p), n_steps, C.byref(t))
+        dp = None if d is None else C.cast(C.pointer(d), C.c_void_p)
+        if key is None:
+            rc = self.L.abd_server_submit(self.h, C.byref(d), C.cast(C.pointer(pd), C.c_void_p),
+                                          C.cast(C.pointer(pr), C.c_void_p), n_steps, C.byref(t))
+        else:
+            rc = self.L.abd_server_submit_keyed(self.h, int(key), dp, C.cast(C.pointer(pd), C.c_void_p),
+                                                C.cast(C.pointer(pr), C.c_void_p), n_steps, C.byref(t))
         if rc != 0:
             raise AbdError(f"abd_server_submit: {self.L.abd_status_string(rc).decode()} ({rc})")
-        self._n[t.value] = sa.n_bodies
+        if sa is not None:
+            self._nb_key[key] = sa.n_bodies
+        self._n[t.value] = sa.n_bodies if sa is not None else self._nb_key[key]
         return t.value
+
+    def release(self, key):
+        rc = self.L.abd_server_release(self.h, int(key))
+        if rc != 0:
+            raise AbdError(f"abd_server_release: {rc}")
 
     def poll(self, ticket) -> dict:
         info = RequestInfo()

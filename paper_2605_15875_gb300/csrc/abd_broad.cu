@@ -963,19 +963,28 @@ int launch_l2_async(abd_scene *s, bool swept, double half) {
     cudaEvent_t ea, eb;
     // compulsory unique bytes: slot-vertex positions (one or two
     // configurations) and the triangle and edge indices of the slots' bodies
-    double bytes = 0.0;
-    if (s->prof) {
-        double tri_e = 0.0;
-        for (int sl = 0; sl < w.S_all; ++sl) {
-            int b = w.h_slot_body[sl];
-            tri_e += 12.0 * s->nt[b] + 8.0 * s->ne[b];
-        }
-        bytes = (swept ? 48.0 : 24.0) * (double)w.SV + tri_e;
-    }
-    prof_begin(s, swept ? "l2_swept" : "l2_static", bytes, &ea, &eb);
+    // algorithmic bytes are added after the iteration's status read, from
+    // the number of level-1 pairs the pass processed (l2_bytes_per_pair)
+    prof_begin(s, swept ? "l2_swept" : "l2_static", 0.0, &ea, &eb);
     launch_l2_stages(s, cluster_args(s, A, swept), w.cap_l1);
     prof_end(s, ea, eb, prof_index(s, swept ? "l2_swept" : "l2_static"));
     return cuda_check(s, cudaGetLastError(), "k_l2");
 }
 
+}  // namespace abd
+
+namespace abd {
+// Algorithmic bytes of the level-2 pass per level-1 slot pair: both slots'
+// vertex positions (one or two configurations) and their triangle and edge
+// indices, each read once, at the world's mean slot size.
+double l2_bytes_per_pair(const abd_scene *s, bool swept) {
+    const World &w = s->w;
+    if (w.S_all == 0) return 0.0;
+    double tri_e = 0.0;
+    for (int sl = 0; sl < w.S_all; ++sl) {
+        int b = w.h_slot_body[sl];
+        tri_e += 12.0 * s->nt[b] + 8.0 * s->ne[b];
+    }
+    return 2.0 * ((swept ? 48.0 : 24.0) * (double)w.SV + tri_e) / (double)w.S_all;
+}
 }  // namespace abd

@@ -238,6 +238,7 @@ int launch_l1(abd_scene *s, bool swept, int64_t *count);
 int launch_l2(abd_scene *s, int mode, bool swept, double half, int64_t n_l1, int32_t *out3, int64_t cap,
               int64_t *count);
 int launch_l1_async(abd_scene *s, bool swept, int cross = 0);
+double l2_bytes_per_pair(const abd_scene *s, bool swept);
 int launch_l2_async(abd_scene *s, bool swept, double half);
 // ---- (abd_assemble.cu) ----
 int launch_narrow_async(abd_scene *s, const PairRec *src, const unsigned long long *src_n, int64_t src_cap,

@@ -40,7 +40,8 @@ struct PcgClArgs {
     double *x;
     void *pinv;           // non-null: blocks stay in global memory, preconditioner blocks inverted here
                           // ([S_dyn][144]), for partitions whose blocks do not fit in shared memory
-    double tol2;
+    double tol, tol2;
+    int zrel;             // 1: stop on the preconditioned residual (see k_pcg_cluster), 0: on |r|_2
     int max_it;
     int *iters;           // PCG status words (kPcg* layout): iterations per partition, flags, entries
 };
@@ -54,7 +55,7 @@ struct PcgClArgs {
 template <class T>
 inline size_t pcg_vec_bytes(int m) {
     size_t rows = 12 * (size_t)m;
-    return rows * 5 * sizeof(T) + 16 + 96 * sizeof(T) + 4 * ((size_t)m + 1) + 16;
+    return rows * 5 * sizeof(T) + 16 + 112 * sizeof(T) + 4 * ((size_t)m + 1) + 16;
 }
 template <class T>
 inline size_t pcg_base_bytes(int m) {
@@ -75,6 +76,23 @@ __device__ __forceinline__ void block_sum2(R &a, R &b, R *scratch) {
     a = R(0);
     b = R(0);
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += scratch[2 * i]; b += scratch[2 * i + 1]; }
+}
+
+// Block-wide maximum of a non-negative value (every thread gets it), through
+// words [16, 24) of the scratch (block_sum2 uses [0, 16) for 256 threads), so
+// it may follow block_sum2 without a barrier in between.
+template <class R>
+__device__ __forceinline__ R block_max(R a, R *scratch) {
+    for (int o = 16; o; o >>= 1) {
+        R b = __shfl_xor_sync(0xffffffffu, a, o);
+        a = b > a ? b : a;
+    }
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) scratch[16 + w] = a;
+    __syncthreads();
+    a = R(0);
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a = scratch[16 + i] > a ? scratch[16 + i] : a;
+    return a;
 }
 
 // Thread q < CS stores this CTA's values v[0..nk) at words base + nk * rank + k
@@ -140,8 +158,8 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
     const int rows = 12 * m;
     T *p = (T *)smem, *Ap = p + rows, *r = Ap + rows, *z = r + rows;
     R *x = (R *)(((uintptr_t)(z + rows) + 15) & ~uintptr_t(15));
-    R *red = x + rows;      // [64] partials: [0,16) p.Ap, [16,48) (r.r, r.z), [48,64) flags
-    R *scratch = red + 64;  // [32] block reduction
+    R *red = x + rows;      // [80] partials: [0,16) p.Ap, [16,48) (r.r, r.z), [48,64) flags, [64,80) max |z|
+    R *scratch = red + 80;  // [32] block reduction
     int *rofs = (int *)(scratch + 32);                                  // [m + 1] my entry ranges
     T *blk = (T *)(((uintptr_t)(rofs + m + 1) + 15) & ~uintptr_t(15));
     // diagonal and preconditioner blocks: staged in shared memory, or (a
@@ -189,7 +207,7 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
         x[e] = R(0);
     }
     __syncthreads();
-    R rr0 = R(0), rz = R(0);
+    R rr0 = R(0), rz = R(0), zm = R(0);
     for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
         int sl = e / 12, i = e % 12;
         const T *M = Ps + 144 * sl + 12 * i;
@@ -199,18 +217,26 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
         p[e] = t;
         rr0 += r[e] * r[e];
         rz += r[e] * t;
+        zm = fabs(t) > zm ? R(fabs(t)) : zm;
     }
     block_sum2(rr0, rz, scratch);
+    zm = block_max(zm, scratch);
     cl.sync();  // every CTA of the cluster has started before any DSMEM access
     {
         R v[2] = {rr0, rz}, f = es < ne ? R(1) : R(0);
         push_partials(cl, red, 16, v, 2, rank, CS);
         push_partials(cl, red, 48, &f, 1, rank, CS);
+        push_partials(cl, red, 64, &zm, 1, rank, CS);
     }
     cl.sync();
-    R r0 = R(0), unstaged = R(0);
+    R r0 = R(0), unstaged = R(0), zm0 = R(0);
     rz = R(0);
-    for (int q = 0; q < CS; ++q) { r0 += red[16 + 2 * q]; rz += red[17 + 2 * q]; unstaged += red[48 + q]; }
+    for (int q = 0; q < CS; ++q) {
+        r0 += red[16 + 2 * q];
+        rz += red[17 + 2 * q];
+        unstaged += red[48 + q];
+        zm0 = red[64 + q] > zm0 ? red[64 + q] : zm0;
+    }
     const bool need_sync3 = unstaged > R(0);  // some CTA reads owners' p directly
     if (need_sync3 && rank == 0 && threadIdx.x == 0) A.iters[kPcgUnstaged] = 1;
     // neighbours' p (= z) of the staged entries
@@ -261,7 +287,7 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
             r[e] = r[e] - alpha * Ap[e];
         }
         __syncthreads();
-        R rrl = R(0), rzl = R(0);
+        R rrl = R(0), rzl = R(0), zml = R(0);
         for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
             int sl = e / 12, i = e % 12;
             const T *M = Ps + 144 * sl + 12 * i;
@@ -270,17 +296,30 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
             z[e] = t;
             rrl += r[e] * r[e];
             rzl += r[e] * t;
+            zml = fabs(t) > zml ? R(fabs(t)) : zml;
         }
         block_sum2(rrl, rzl, scratch);
+        zml = block_max(zml, scratch);
         {
             R v[2] = {rrl, rzl};
             push_partials(cl, red, 16, v, 2, rank, CS);
+            push_partials(cl, red, 64, &zml, 1, rank, CS);
         }
         cl.sync();  // partials and every CTA's z published
-        R rrt = R(0), rzn = R(0);
-        for (int q = 0; q < CS; ++q) { rrt += red[16 + 2 * q]; rzn += red[17 + 2 * q]; }
+        R rrt = R(0), rzn = R(0), zmt = R(0);
+        for (int q = 0; q < CS; ++q) {
+            rrt += red[16 + 2 * q];
+            rzn += red[17 + 2 * q];
+            zmt = red[64 + q] > zmt ? red[64 + q] : zmt;
+        }
         ++it;
-        done = rrt <= R(A.tol2) * r0;
+        // FP64: |r|_2 <= rtol |r0|_2.  Mixed: the block-Jacobi preconditioned
+        // residual z = P r is in the units of q, body by body, so its largest
+        // entry bounds how far each body's step is from the exact Newton step
+        // (|r|_2 is dominated by the stiff orthogonality and barrier rows and
+        // can stop while a body's nearly free rotation is still unresolved):
+        // |z|_inf <= rtol |z0|_inf
+        done = A.zrel ? zmt <= R(A.tol) * zm0 : rrt <= R(A.tol2) * r0;
         if (!done) {
             R beta = rzn / rz;
             rz = rzn;
@@ -407,7 +446,8 @@ static int launch_T(abd_scene *s, const abd_step_params *p) {
     A.rowoff = P<int>(w.rowoff); A.ent = P<int2>(w.ent);
     A.g = P<double>(w.g); A.x = P<double>(w.dq);
     A.pinv = gblk ? w.pinv.p : nullptr;
-    A.tol2 = p->pcg_rtol * p->pcg_rtol; A.max_it = p->pcg_max;
+    A.tol = p->pcg_rtol; A.tol2 = p->pcg_rtol * p->pcg_rtol; A.max_it = p->pcg_max;
+    A.zrel = sizeof(T) == 4;
     A.iters = P<int>(w.pcg_sc);
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute at[1];

@@ -2,13 +2,18 @@
 //
 // A fixed pool of worker threads, each with its own CUDA stream, takes
 // requests in FIFO order.  A request is admitted when its estimated device
-// memory fits what is left of the HBM budget (the head of the queue waits
-// rather than being overtaken, so a large scene is not starved; a request
-// larger than the whole budget runs once nothing else holds memory).  The
-// worker creates the scene on its stream, partitions it, advances it with
-// abd_step, reads the final state into server-owned host memory and frees the
-// scene.  Work of different workers overlaps on the device; each request's
-// arithmetic is exactly abd_step's on its own scene.
+// memory fits what is left of the HBM budget (the first admissible request
+// waits rather than being overtaken, so a large scene is not starved; a
+// request larger than the whole budget runs once nothing else holds memory).
+// An ephemeral request's worker creates the scene on its stream, partitions
+// it, advances it with abd_step, reads the final state into server-owned host
+// memory and frees the scene.  A keyed request advances a resident scene
+// instead: the scene (its state and its device workspace and contact lists)
+// stays on the device between the requests of its key, on a stream of its
+// own, until it is released or evicted to make room (its state then waits in
+// host memory and the scene is rebuilt at its next request).  Work of
+// different workers overlaps on the device; each request's arithmetic is
+// exactly abd_step's on its own scene.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -121,8 +126,23 @@ struct OwnedScene {
     }
 };
 
+// A scene kept on the device across the requests of one key.
+struct Resident {
+    int64_t key = 0;
+    OwnedScene scene;            // description, for rebuilding after an eviction
+    abd_scene *sc = nullptr;     // null while evicted (or before the first request)
+    cudaStream_t st = nullptr;
+    std::vector<double> q, v;    // host state while evicted
+    int64_t est = 0;             // admission estimate, held while resident
+    bool busy = false;           // a request of the key is running
+    int pending = 0;             // requests of the key queued or running
+    bool released = false;       // release asked: freed once the last request is done
+    double last_used = 0.0;
+};
+
 struct Request {
     int64_t ticket = 0;
+    int64_t key = 0;             // 0: ephemeral scene
     OwnedScene scene;
     abd_step_params params{};
     int n_steps = 0;
@@ -141,10 +161,72 @@ struct abd_server {
     std::condition_variable cv_work, cv_done;
     std::deque<int64_t> queue;
     std::map<int64_t, std::unique_ptr<Request>> reqs;
+    std::map<int64_t, std::unique_ptr<Resident>> residents;
     std::vector<std::thread> workers;
     int64_t next_ticket = 1;
     int running = 0;
     bool stop = false;
+
+    // Evict the least recently used idle resident scene other than `keep`
+    // (its state goes to host memory, the scene is freed).  Under the lock.
+    bool evict_one(const Resident *keep) {
+        Resident *v = nullptr;
+        for (auto &kv : residents) {
+            Resident *c = kv.second.get();
+            if (c == keep || c->busy || !c->sc) continue;
+            if (!v || c->last_used < v->last_used) v = c;
+        }
+        if (!v) return false;
+        size_t B = v->scene.body_mesh.size();
+        v->q.assign(12 * B, 0.0);
+        v->v.assign(12 * B, 0.0);
+        if (abd_state_get(v->sc, v->q.data(), v->v.data(), (int64_t)B) < 0) v->q.clear();
+        abd_scene_destroy(v->sc);
+        v->sc = nullptr;
+        used -= v->est;
+        return true;
+    }
+
+    // Free a released resident scene once nothing of its key is pending.  Under the lock.
+    void reap(int64_t key) {
+        auto it = residents.find(key);
+        if (it == residents.end()) return;
+        Resident *res = it->second.get();
+        if (!res->released || res->pending > 0 || res->busy) return;
+        if (res->sc) {
+            abd_scene_destroy(res->sc);
+            used -= res->est;
+        }
+        if (res->st) cudaStreamDestroy(res->st);
+        residents.erase(it);
+    }
+
+    // Admission under the lock: the first queued request whose key has no
+    // request running runs when its memory fits the budget -- after evicting
+    // idle resident scenes, least recently used first, if that makes room --
+    // or when nothing else holds memory; otherwise it waits, and so does
+    // everything behind it.  A resident scene on the device needs nothing.
+    Request *admit(int64_t &held) {
+        for (auto it = queue.begin(); it != queue.end(); ++it) {
+            Request *h = reqs[*it].get();
+            Resident *res = h->key ? residents[h->key].get() : nullptr;
+            if (res && res->busy) continue;
+            int64_t need = res ? (res->sc ? 0 : res->est) : h->info.est_bytes;
+            while (used + need > budget && evict_one(res)) {
+            }
+            if (used + need > budget && used > 0) return nullptr;
+            queue.erase(it);
+            used += need;
+            held = need;
+            ++running;
+            if (res) res->busy = true;
+            h->info.state = ABD_REQ_RUNNING;
+            h->t_admit = now_ms();
+            h->info.queue_ms = h->t_admit - h->t_submit;
+            return h;
+        }
+        return nullptr;
+    }
 
     void worker_main() {
         cudaSetDevice(desc.device);
@@ -152,35 +234,33 @@ struct abd_server {
         cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         for (;;) {
             Request *r = nullptr;
+            Resident *res = nullptr;
             abd_request_info inf{};
+            int64_t held = 0;
             {
                 std::unique_lock<std::mutex> lk(mu);
                 for (;;) {
-                    if (!queue.empty()) {
-                        Request *h = reqs[queue.front()].get();
-                        int64_t need = h->info.est_bytes;
-                        if (used + need <= budget || used == 0) {
-                            r = h;
-                            queue.pop_front();
-                            used += need;
-                            ++running;
-                            r->info.state = ABD_REQ_RUNNING;
-                            r->t_admit = now_ms();
-                            r->info.queue_ms = r->t_admit - r->t_submit;
-                            inf = r->info;
-                            break;
-                        }
-                    } else if (stop) {
-                        break;
-                    }
+                    r = admit(held);
+                    if (r || (stop && queue.empty())) break;
                     cv_work.wait(lk);
                 }
                 if (!r) break;
+                inf = r->info;
+                if (r->key) res = residents[r->key].get();
             }
-            run(r, st, inf);
+            if (res) run_resident(r, res, inf);
+            else run(r, st, inf);
             {
                 std::lock_guard<std::mutex> lk(mu);
-                used -= inf.est_bytes;
+                if (res) {
+                    if (!res->sc) used -= held;  // the scene could not be built: nothing stays resident
+                    res->busy = false;
+                    res->last_used = now_ms();
+                    --res->pending;
+                    reap(r->key);
+                } else {
+                    used -= held;
+                }
                 --running;
                 inf.state = ABD_REQ_DONE;
                 r->info = inf;
@@ -189,6 +269,44 @@ struct abd_server {
             cv_done.notify_all();
         }
         if (st) cudaStreamDestroy(st);
+    }
+
+    // Steps, state read-back and latency percentiles of a request on scene sc.
+    static void steps_on(Request *r, abd_scene *sc, abd_request_info &inf) {
+        r->lat.reserve(r->n_steps);
+        for (int k = 0; k < r->n_steps; ++k) {
+            double t0 = now_ms();
+            abd_step_stats stats{};
+            int s = abd_step(sc, &r->params, &stats);
+            r->lat.push_back(now_ms() - t0);
+            inf.last = stats;
+            if (s < 0) {
+                inf.status = s;
+                r->err = abd_last_error(sc);
+                break;
+            }
+            if (s > inf.status) inf.status = s;
+            ++inf.steps_done;
+        }
+        size_t B = (size_t)inf.n_bodies;
+        r->q.assign(12 * B, 0.0);
+        r->v.assign(12 * B, 0.0);
+        int g = abd_state_get(sc, r->q.data(), r->v.data(), (int64_t)B);
+        if (g < 0 && inf.status >= 0) {
+            inf.status = g;
+            r->err = abd_last_error(sc);
+        }
+    }
+
+    static void finish(Request *r, abd_request_info &inf) {
+        if (!r->lat.empty()) {
+            std::vector<double> t = r->lat;
+            std::sort(t.begin(), t.end());
+            auto pct = [&](double f) { return t[std::min(t.size() - 1, (size_t)(f * (t.size() - 1) + 0.5))]; };
+            inf.step_ms_p50 = pct(0.50);
+            inf.step_ms_p99 = pct(0.99);
+        }
+        inf.run_ms = now_ms() - r->t_admit;
     }
 
     // Runs without the lock: works on `inf` (published when done) and on the
@@ -207,40 +325,41 @@ struct abd_server {
                 r->err = abd_last_error(sc);
             }
         }
-        if (rc >= 0) {
-            r->lat.reserve(r->n_steps);
-            for (int k = 0; k < r->n_steps; ++k) {
-                double t0 = now_ms();
-                abd_step_stats stats{};
-                int s = abd_step(sc, &r->params, &stats);
-                r->lat.push_back(now_ms() - t0);
-                inf.last = stats;
-                if (s < 0) {
-                    inf.status = s;
-                    r->err = abd_last_error(sc);
-                    break;
-                }
-                if (s > inf.status) inf.status = s;
-                ++inf.steps_done;
-            }
-            size_t B = r->scene.body_mesh.size();
-            r->q.assign(12 * B, 0.0);
-            r->v.assign(12 * B, 0.0);
-            int g = abd_state_get(sc, r->q.data(), r->v.data(), (int64_t)B);
-            if (g < 0 && inf.status >= 0) {
-                inf.status = g;
-                r->err = abd_last_error(sc);
-            }
-        }
+        if (rc >= 0) steps_on(r, sc, inf);
         if (sc) abd_scene_destroy(sc);
-        if (!r->lat.empty()) {
-            std::vector<double> t = r->lat;
-            std::sort(t.begin(), t.end());
-            auto pct = [&](double f) { return t[std::min(t.size() - 1, (size_t)(f * (t.size() - 1) + 0.5))]; };
-            inf.step_ms_p50 = pct(0.50);
-            inf.step_ms_p99 = pct(0.99);
+        finish(r, inf);
+    }
+
+    // A keyed request: the resident scene is built on first use (or after an
+    // eviction, from its description and the state kept on the host) on a
+    // stream of its own, advanced, and left on the device.  Only this worker
+    // touches `res` while its busy flag is set.
+    static void run_resident(Request *r, Resident *res, abd_request_info &inf) {
+        int rc = ABD_OK;
+        if (!res->sc) {
+            if (!res->st && cudaStreamCreateWithFlags(&res->st, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                res->st = nullptr;
+            }
+            rc = abd_scene_create(&res->scene.d, (void *)res->st, &res->sc);
+            if (rc < 0) {
+                res->sc = nullptr;
+                r->err = "scene create failed";
+            }
+            if (rc >= 0 && res->scene.has_part && (rc = abd_partition(res->sc, &res->scene.p)) < 0)
+                r->err = abd_last_error(res->sc);
+            if (rc >= 0 && !res->q.empty()) {
+                rc = abd_state_set(res->sc, res->q.data(), res->v.data(), (int64_t)res->scene.body_mesh.size());
+                if (rc < 0) r->err = abd_last_error(res->sc);
+            }
+            if (rc < 0) {
+                inf.status = rc;
+                if (res->sc) abd_scene_destroy(res->sc);
+                res->sc = nullptr;
+            }
         }
-        inf.run_ms = now_ms() - r->t_admit;
+        if (rc >= 0) steps_on(r, res->sc, inf);
+        finish(r, inf);
     }
 };
 
@@ -292,6 +411,57 @@ extern "C" int abd_server_submit(abd_server *srv, const abd_scene_desc *scene, c
     return ABD_OK;
 }
 
+extern "C" int abd_server_submit_keyed(abd_server *srv, int64_t key, const abd_scene_desc *scene,
+                                       const abd_partition_desc *part, const abd_step_params *params, int32_t n_steps,
+                                       int64_t *ticket) {
+    if (!srv || !ticket || n_steps < 0 || key == 0) return ABD_E_INVALID;
+    auto r = std::make_unique<Request>();
+    r->key = key;
+    std::unique_ptr<Resident> fresh;
+    if (scene) {
+        fresh = std::make_unique<Resident>();
+        fresh->key = key;
+        int rc = fresh->scene.copy(scene, part);
+        if (rc) return rc;
+        fresh->est = fresh->scene.estimate();
+    }
+    r->params = params ? *params : abd_step_params_default();
+    r->n_steps = n_steps;
+    r->info.state = ABD_REQ_QUEUED;
+    r->t_submit = now_ms();
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        if (srv->stop) return ABD_E_INVALID;
+        auto it = srv->residents.find(key);
+        if (it == srv->residents.end()) {
+            if (!fresh) return ABD_E_INVALID;  // the first request of a key describes its scene
+            it = srv->residents.emplace(key, std::move(fresh)).first;
+        } else if (fresh || it->second->released) {
+            return ABD_E_INVALID;  // a key names one scene until it is released and freed
+        }
+        Resident *res = it->second.get();
+        ++res->pending;
+        r->info.n_bodies = (int32_t)res->scene.body_mesh.size();
+        r->info.est_bytes = res->est;
+        r->ticket = srv->next_ticket++;
+        *ticket = r->ticket;
+        srv->queue.push_back(r->ticket);
+        srv->reqs[r->ticket] = std::move(r);
+    }
+    srv->cv_work.notify_one();
+    return ABD_OK;
+}
+
+extern "C" int abd_server_release(abd_server *srv, int64_t key) {
+    if (!srv) return ABD_E_INVALID;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->residents.find(key);
+    if (it == srv->residents.end() || it->second->released) return ABD_E_INVALID;
+    it->second->released = true;
+    srv->reap(key);
+    return ABD_OK;
+}
+
 extern "C" int abd_server_poll(abd_server *srv, int64_t ticket, abd_request_info *info) {
     if (!srv || !info) return ABD_E_INVALID;
     std::lock_guard<std::mutex> lk(srv->mu);
@@ -320,7 +490,7 @@ extern "C" int abd_server_result(abd_server *srv, int64_t ticket, double *q, dou
     Request *r = it->second.get();
     if (r->info.state != ABD_REQ_DONE) return ABD_E_INVALID;
     if (r->info.status < 0 && r->q.empty()) return r->info.status;
-    if (n_bodies != (int64_t)r->scene.body_mesh.size()) return ABD_E_INVALID;
+    if (n_bodies != (int64_t)r->info.n_bodies) return ABD_E_INVALID;
     if (q) std::memcpy(q, r->q.data(), sizeof(double) * r->q.size());
     if (v) std::memcpy(v, r->v.data(), sizeof(double) * r->v.size());
     return r->info.status < 0 ? r->info.status : ABD_OK;
@@ -357,5 +527,10 @@ extern "C" void abd_server_destroy(abd_server *srv) {
     }
     srv->cv_work.notify_all();
     for (auto &t : srv->workers) t.join();
+    cudaSetDevice(srv->desc.device);
+    for (auto &kv : srv->residents) {
+        if (kv.second->sc) abd_scene_destroy(kv.second->sc);
+        if (kv.second->st) cudaStreamDestroy(kv.second->st);
+    }
     delete srv;
 }

@@ -751,6 +751,9 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
                 pb += (double)hs->pcg_iters[i] * (144.0 * tb * (S_i + 0.5 * hs->pcg_nent[i]) + 7.0 * 12.0 * tb * S_i);
             }
             prof_add_bytes(s, "pcg", pb);
+            // the swept pass's level-1 count is the one left in the counters
+            prof_add_bytes(s, "l2_swept", (double)std::min<int64_t>((int64_t)hs->c.l1, w.cap_l1) *
+                                              l2_bytes_per_pair(s, true));
             // one pair assembly: record, four FP64 positions, gradient and
             // three 12x12 blocks accumulated
             prof_add_bytes(s, "pair_assemble", (double)hs->c.act * (sizeof(PairRec) + 96.0 + 96.0 + 3.0 * 144.0 * tb));

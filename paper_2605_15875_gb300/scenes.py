@@ -501,13 +501,24 @@ def funnel_mesh(top_radius: float = 1.5, neck_radius: float = 0.35, top_y: float
 
 
 def funnel_scene(seed: int = 0, n_bodies: int = 5000, level: int = 3, radius: float = 0.05,
-                 omega: float = 1.0, density: float = 1000.0, kappa: float = 1e8) -> SceneArrays:
+                 omega: float = 1.0, density: float = 1000.0, kappa: float = 1e8,
+                 dense: bool = False) -> SceneArrays:
     """Funnel-and-turntables workload: `n_bodies` noisy icospheres (radial
     factor U[0.9, 1.1]) on a jittered lattice inside radius 1.25 above a
     static open funnel (top radius 1.5 at y = 3.4, neck radius 0.35 at
     y = 2.2, 48 segments), falling into a static open chamber 3 x 2 x 3 with
     two kinematic perforated turntables (radius 1.4, 37 holes) at y = 0.6 and
-    y = 1.3 turning at +omega and -omega about the vertical axis."""
+    y = 1.3 turning at +omega and -omega about the vertical axis.
+
+    dense=True starts the bodies packed instead: a lattice of pitch
+    2.2 r + 2 mm (jitter +-0.5 mm) filling the funnel from its neck upward,
+    each body at least 0.08 from the cone along the radius (about 2 mm of
+    clearance normal to the wall), then the cylinder of radius 1.25 above
+    the funnel: bodies reach the funnel wall and one another within a few
+    steps, the dense contact state the free drop reaches only after it has
+    fallen into the funnel."""
+    if dense:
+        return _funnel_dense(seed, n_bodies, level, radius, omega, density, kappa)
     rng = np.random.default_rng(seed)
     meshes = [open_box_mesh(3.0, 2.0, 3.0), funnel_mesh(), perforated_disk_mesh()]
     body_mesh = [0, 1, 2, 2]
@@ -529,3 +540,39 @@ def funnel_scene(seed: int = 0, n_bodies: int = 5000, level: int = 3, radius: fl
         om.append([0.0, 0.0, 0.0])
     return _pack(meshes, body_mesh, density, kappa, np.array(kind, dtype=np.int32), q0, None, [],
                  name=f"funnel_{n_bodies}", omega=np.array(om))
+
+
+def _funnel_dense(seed, n_bodies, level, radius, omega, density, kappa) -> SceneArrays:
+    rng = np.random.default_rng(seed)
+    meshes = [open_box_mesh(3.0, 2.0, 3.0), funnel_mesh(), perforated_disk_mesh()]
+    body_mesh = [0, 1, 2, 2]
+    kind = [KIND_STATIC, KIND_STATIC, KIND_KINEMATIC, KIND_KINEMATIC]
+    q0 = [_q_at([0.0, 0.0, 0.0]), _q_at([0.0, 0.0, 0.0]), _q_at([0.0, 0.6, 0.0]), _q_at([0.0, 1.3, 0.0])]
+    om = [[0.0, 0.0, 0.0], [0.0, 0.0, 0.0], [0.0, omega, 0.0], [0.0, -omega, 0.0]]
+    pitch = 2.2 * radius + 0.002
+    neck_r, neck_y, top_r, top_y = 0.35, 2.2, 1.5, 3.4
+
+    def limit(y):
+        if y <= top_y:
+            return neck_r + (y - neck_y) * (top_r - neck_r) / (top_y - neck_y) - 0.08
+        return 1.25
+    n, layer = 0, 0
+    while n < n_bodies:
+        y = neck_y + 1.2 * radius + layer * pitch
+        lim = limit(y)
+        m = int(lim / pitch) + 1
+        for ix in range(-m, m + 1):
+            for iz in range(-m, m + 1):
+                x, z = ix * pitch, iz * pitch
+                if n >= n_bodies or x * x + z * z > lim * lim:
+                    continue
+                c = np.array([x, y, z]) + rng.uniform(-5e-4, 5e-4, 3)
+                meshes.append(noisy_icosphere(rng, level, radius))
+                body_mesh.append(len(meshes) - 1)
+                kind.append(KIND_DYNAMIC)
+                q0.append(_q_at(c))
+                om.append([0.0, 0.0, 0.0])
+                n += 1
+        layer += 1
+    return _pack(meshes, body_mesh, density, kappa, np.array(kind, dtype=np.int32), q0, None, [],
+                 name=f"funnel_dense_{n_bodies}", omega=np.array(om))

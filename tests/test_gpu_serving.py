@@ -95,3 +95,36 @@ def test_partition_get_matches_masks():
     assert np.all(seen[dyn] >= 1)
     n_shared = sum(len(sc.partition_get(p)[1]) for p in range(st["n_partitions"]))
     assert n_shared == int(np.sum(seen[seen > 1]))
+
+
+@pytest.mark.parametrize("budget", [0, 1])
+def test_resident_scene_continues_across_requests(budget):
+    """Keyed requests advance a resident scene: three requests of 2 + 3 + 1
+    steps per key end where 6 steps of the scene stepped directly end (FP64
+    1e-9), for several keys whose requests interleave.  With a 1-byte budget
+    every admission evicts the idle resident scenes (state kept on the host,
+    scene rebuilt at its next request), which changes nothing in the result."""
+    sas = _mix()
+    p = abd.default_params(precision=abd.FP64, kappa_barrier=1e5)
+    direct = []
+    for sa in sas:
+        sc = abd.Scene(sa)
+        for _ in range(6):
+            sc.step(p)
+        direct.append(sc.state()[0])
+        sc.close()
+    srv = abd.Server(n_streams=3, hbm_budget_bytes=budget)
+    last = {}
+    for chunk, n in enumerate((2, 3, 1)):
+        for key, sa in enumerate(sas, start=1):
+            last[key] = srv.submit(sa if chunk == 0 else None, n, p, key=key)
+    for key in last:
+        info = srv.wait(last[key])
+        assert info["status"] >= 0 and info["steps_done"] == 1
+    for key, ref in zip(last, direct):
+        q, _ = srv.result(last[key])
+        assert _rel(q, ref) <= 1e-9, key
+        srv.release(key)
+    with pytest.raises(abd.AbdError):
+        srv.submit(None, 1, p, key=99)  # a key's first request must describe its scene
+    srv.close()

@@ -39,7 +39,13 @@ def test_batch_equals_each_subdomain_alone(precision, tol):
     alone = [abd.Scene(sa) for sa in subs]
     off = batch.layout()
     assert len(off) == len(subs) + 1 and off[-1] == sum(sa.n_bodies for sa in subs)
-    pg = abd.default_params(precision=precision, pcg_rtol=1e-12 if precision == abd.FP64 else 1e-5)
+    # Newton stops once its step is below eps_N h l (Eq. 8), about 5e-9 for
+    # these piles at the default eps_N = 1e-6; the batch's PCG clusters have
+    # the largest subdomain's size, so its dot products add in another order
+    # than a subdomain's alone, and the two solves may stop one sub-threshold
+    # step apart.  eps_N = 1e-8 puts that step far below the 1e-9 bound.
+    pg = abd.default_params(precision=precision, pcg_rtol=1e-12 if precision == abd.FP64 else 1e-5,
+                            newton_tol=1e-8 if precision == abd.FP64 else 1e-6)
     contact, worst = 0, 0.0
     for k in range(14):
         # every step from the same state: the alone scenes' states, concatenated
@@ -56,7 +62,7 @@ def test_batch_equals_each_subdomain_alone(precision, tol):
             worst = max(worst, e)
             assert e <= tol, (k, i, e)
             if precision == abd.FP64:
-                assert nb[i] == sa_["newton_iters"], (k, i, nb[i], sa_["newton_iters"])
+                assert abs(int(nb[i]) - sa_["newton_iters"]) <= 1, (k, i, nb[i], sa_["newton_iters"])
             contact += sa_["n_active_peak"] > 0
     print(f"worst per-step rel err {worst:.3e}; subdomain-steps in contact {contact}")
     assert contact >= 20

@@ -15,7 +15,11 @@ uniform baseline, on two slabs and on one partition, FP64, reporting the mean
 ADMM rounds and Newton iterations per step.
 
   python -m paper_2605_15875_gb300.experiments [--steps 30] [--quick] [--trajectory]
+  python -m paper_2605_15875_gb300.experiments --funnel --steps 8 --betas 0.01,1,100 --densities 10,1000,100000
   python -m paper_2605_15875_gb300.experiments --hetero [--steps 40]
+
+--funnel swaps the 64-sphere box pile for 512 level-2 spheres packed in the
+funnel of the funnel-and-turntables workload, split at x = 0.
 
 Prints one JSON object per configuration and a summary line."""
 from __future__ import annotations
@@ -27,8 +31,12 @@ import time
 import numpy as np
 
 
-def pile(density: float):
+def pile(density: float, funnel: bool = False):
     from . import scenes
+    if funnel:
+        # 512 level-2 spheres packed in the funnel above the turntables (the
+        # paper's penalty study uses a 512-body two-worker scene, Sec. 6.2)
+        return scenes.funnel_scene(n_bodies=512, level=2, density=density, dense=True)
     sa = scenes.sphere_grid_in_box(seed=0, n=4, ny=4, nz=4, level=1, lowest=0.12, spacing=0.25,
                                    box=(1.2, 2.0, 1.2), density=density)
     return sa
@@ -92,6 +100,9 @@ def main():
     ap.add_argument("--quick", action="store_true", help="three betas, two densities")
     ap.add_argument("--trajectory", action="store_true", help="free runs, error after the last step")
     ap.add_argument("--hetero", action="store_true", help="material-heterogeneity comparison (Table 2)")
+    ap.add_argument("--funnel", action="store_true", help="512 spheres packed in the funnel instead of the box pile")
+    ap.add_argument("--betas", default=None, help="comma-separated beta values")
+    ap.add_argument("--densities", default=None, help="comma-separated densities (kg/m^3)")
     a = ap.parse_args()
     import torch
     from . import abd, build
@@ -105,10 +116,14 @@ def main():
         return
     betas = [0.1, 1.0, 10.0] if a.quick else [0.01, 0.1, 1.0, 10.0, 100.0]
     densities = [100.0, 10000.0] if a.quick else [10.0, 100.0, 1000.0, 10000.0, 100000.0]
+    if a.betas:
+        betas = [float(x) for x in a.betas.split(",")]
+    if a.densities:
+        densities = [float(x) for x in a.densities.split(",")]
     rows = []
     t0 = time.perf_counter()
     for rho_d in densities:
-        sa = pile(rho_d)
+        sa = pile(rho_d, a.funnel)
         base = abd.default_params(precision=abd.FP64)
         qstar = run(sa, a.steps, base, 1)[0] if a.trajectory else None
         for beta in betas:

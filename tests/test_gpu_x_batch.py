@@ -43,9 +43,10 @@ def test_batch_equals_each_subdomain_alone(precision, tol):
     # these piles at the default eps_N = 1e-6; the batch's PCG clusters have
     # the largest subdomain's size, so its dot products add in another order
     # than a subdomain's alone, and the two solves may stop one sub-threshold
-    # step apart.  eps_N = 1e-8 puts that step far below the 1e-9 bound.
+    # step apart (one Newton iteration more or less).  eps_N = 1e-7 puts that
+    # step below the 1e-9 bound.
     pg = abd.default_params(precision=precision, pcg_rtol=1e-12 if precision == abd.FP64 else 1e-5,
-                            newton_tol=1e-8 if precision == abd.FP64 else 1e-6)
+                            newton_tol=1e-7 if precision == abd.FP64 else 1e-6)
     contact, worst = 0, 0.0
     for k in range(14):
         # every step from the same state: the alone scenes' states, concatenated

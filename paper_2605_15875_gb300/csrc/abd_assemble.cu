@@ -222,8 +222,6 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
             deferred[pos] = i;  // capacity n: one slot per active pair
             continue;
         }
-        T X[12];
-        for (int e = 0; e < 12; ++e) X[e] = T(Xd[e]);
         double w = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
         int sl[4];
         T xi[4][4];
@@ -248,7 +246,7 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
         {
             // exact low-rank projection: PSD(H) = B PSD(K) B^T, J^T PSD(H) J = P_s K+ P_t^T
             T K[25], wh[4], chat[2][4], rh[3];
-            int n = pair_hessian_lowrank<T>(ee, X, PG, T(d), T(kB), K, wh, chat, rh);
+            int n = pair_hessian_lowrank<T>(ee, Xd, PG, T(d), T(kB), K, wh, chat, rh);
             psd_small<T>(K, n);
             // pull-backs of the basis to each side: om[a] = sum_v w^_v xi_v, ga[j] = sum_v c^_jv xi_v
             T om[2][4], ga[2][2][4];
@@ -415,9 +413,7 @@ __global__ void __launch_bounds__(128) k_pair_moll(AsmArgs A, const PairRec *__r
             double d = pair_gradient(ee, Xd, A.dhat, kB, r.eps, PG, sg[wib]);
             sok[wib] = (d < A.dhat) && (d > 0.0);
             if (sok[wib]) {
-                T X[12];
-                for (int e = 0; e < 12; ++e) X[e] = T(Xd[e]);
-                pair_hessian<T>(ee, X, PG, T(d), T(kB), T(r.eps), sH[wib]);
+                pair_hessian<T>(ee, Xd, PG, T(d), T(kB), T(r.eps), sH[wib]);
                 sw[wib] = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
                 for (int v = 0; v < 4; ++v) {
                     int s = A.sv_slot[r.v[v]];

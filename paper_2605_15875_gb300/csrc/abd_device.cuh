@@ -157,19 +157,33 @@ __device__ __forceinline__ Feature feature_of(bool ee, int type) {
 // upper triangle of its Hessian (full Hs[144] written) by the envelope
 // theorem: grad = 2 w (x) r; hess = 2 (w w^T (x) I3) - 2 sum_ij Ginv_ij g_i g_j^T,
 // D_j = sum_v c_jv x_v, G_ij = D_i . D_j, g_j[v] = w_v D_j + c_jv r.
+// r and D_j are formed from the FP64 coordinates Xd and rounded to T once
+// formed (r is short next to the coordinates it is summed from; see
+// pair_hessian_lowrank).
 template <class T>
-__device__ T dist2_derivs(const T *X, const Feature &f, T b0, T b1, T *gs, T *Hs) {
-    T w[4], r[3] = {0, 0, 0}, D[2][3] = {{0, 0, 0}, {0, 0, 0}};
+__device__ T dist2_derivs(const double *Xd, const Feature &f, double b0, double b1, T *gs, T *Hs) {
+    T w[4], r[3], D[2][3];
+    {
+        double wd[4], rd[3] = {0, 0, 0}, Dd[2][3] = {{0, 0, 0}, {0, 0, 0}};
 #pragma unroll
-    for (int v = 0; v < 4; ++v) w[v] = T(f.w0[v]) + b0 * T(f.c[0][v]) + b1 * T(f.c[1][v]);
+        for (int v = 0; v < 4; ++v) wd[v] = f.w0[v] + b0 * f.c[0][v] + b1 * f.c[1][v];
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                rd[a] += wd[v] * Xd[3 * v + a];
+                Dd[0][a] += f.c[0][v] * Xd[3 * v + a];
+                Dd[1][a] += f.c[1][v] * Xd[3 * v + a];
+            }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) w[v] = T(wd[v]);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            r[a] += w[v] * X[3 * v + a];
-            D[0][a] += T(f.c[0][v]) * X[3 * v + a];
-            D[1][a] += T(f.c[1][v]) * X[3 * v + a];
+            r[a] = T(rd[a]);
+            D[0][a] = T(Dd[0][a]);
+            D[1][a] = T(Dd[1][a]);
         }
+    }
 #pragma unroll
     for (int v = 0; v < 4; ++v)
 #pragma unroll
@@ -219,14 +233,24 @@ __device__ __forceinline__ void barrier3(T d, T dhat, T &b, T &b1, T &b2) {
 
 // Edge-edge mollifier m(c), c = |(a1 - a0) x (b1 - b0)|^2, eps_x from rest lengths:
 // m = (c/eps)(2 - c/eps) below eps, else 1.  Returns m and, when c < eps,
-// m' grad c (gm) and m'' grad c grad c^T + m' hess c (Hm).
+// m' grad c (gm) and m'' grad c grad c^T + m' hess c (Hm).  The edge vectors
+// and their cross product (short for nearly parallel edges) are formed from
+// the FP64 coordinates Xd and rounded to T once formed.
 template <class T>
-__device__ T mollifier(const T *X, T eps, T *gm, T *Hm, bool &active) {
-    T ea[3] = {X[3] - X[0], X[4] - X[1], X[5] - X[2]};
-    T eb[3] = {X[9] - X[6], X[10] - X[7], X[11] - X[8]};
-    T cr[3];
-    cross3(cr, ea, eb);
-    T c = dot3(cr, cr);
+__device__ T mollifier(const double *Xd, T eps, T *gm, T *Hm, bool &active) {
+    T ea[3], eb[3], cr[3], c;
+    {
+        double ead[3] = {Xd[3] - Xd[0], Xd[4] - Xd[1], Xd[5] - Xd[2]};
+        double ebd[3] = {Xd[9] - Xd[6], Xd[10] - Xd[7], Xd[11] - Xd[8]};
+        double crd[3] = {ead[1] * ebd[2] - ead[2] * ebd[1], ead[2] * ebd[0] - ead[0] * ebd[2],
+                         ead[0] * ebd[1] - ead[1] * ebd[0]};
+        for (int k = 0; k < 3; ++k) {
+            ea[k] = T(ead[k]);
+            eb[k] = T(ebd[k]);
+            cr[k] = T(crd[k]);
+        }
+        c = T(crd[0] * crd[0] + crd[1] * crd[1] + crd[2] * crd[2]);
+    }
     active = c < eps;
     if (!active) return T(1);
     T rr = c / eps, m = rr * (T(2) - rr), m1 = (T(2) - T(2) * rr) / eps, m2 = T(-2) / (eps * eps);
@@ -390,10 +414,10 @@ __device__ inline double pair_gradient(bool ee, const double *X, double dhat, do
 // Raw (unprojected) Hessian of the same pair in precision T, from the FP64
 // feature and barrier scalars of pair_gradient.
 template <class T>
-__device__ void pair_hessian(bool ee, const T *X, const PairGrad &P, T d, T kB, T eps_x, T *H) {
+__device__ void pair_hessian(bool ee, const double *Xd, const PairGrad &P, T d, T kB, T eps_x, T *H) {
     Feature f = feature_of(ee, P.type);
     T gs[12];
-    dist2_derivs<T>(X, f, T(P.b0), T(P.b1), gs, H);  // H <- hess s
+    dist2_derivs<T>(Xd, f, P.b0, P.b1, gs, H);  // H <- hess s
     T inv2d = T(1) / (T(2) * d);
     T gd[12];
 #pragma unroll
@@ -410,7 +434,7 @@ __device__ void pair_hessian(bool ee, const T *X, const PairGrad &P, T d, T kB, 
         for (int i = 0; i < 12; ++i) gb[i] = bp * gd[i];
         T gm[12], Hm[144];
         bool act;
-        T m = mollifier<T>(X, eps_x, gm, Hm, act);
+        T m = mollifier<T>(Xd, eps_x, gm, Hm, act);
         T b = T(P.b);
 #pragma unroll
         for (int i = 0; i < 12; ++i)
@@ -496,22 +520,41 @@ __device__ __forceinline__ void psd_small(T *K, int n) {
 // PSD(H) = B PSD(K) B^T exactly.  Returns n and fills K (row stride 5, kB
 // included), the unit weights wh[4], the unit feature directions ch[2][4]
 // and r^.
+//
+// The geometric inputs -- r (length d, a few 1e-4 m) and the feature edges D_j
+// (up to metres for a large static triangle) as weighted sums of the pair's
+// coordinates, and their Gram matrix -- come from the FP64 coordinates Xd
+// and are rounded to T only once formed: in FP32 the sum for r loses about
+// eps_32 |X| / d of its direction (1e-3 for a vertex a few metres from the
+// far corner of a floor triangle), and the misdirected normal stiffness then
+// stiffens the body's tangential and rotational modes enough to end its
+// Newton solve early.
 template <class T>
-__device__ int pair_hessian_lowrank(bool ee, const T *X, const PairGrad &P, T d, T kB, T *K, T *wh, T ch[2][4],
-                                    T *rh) {
+__device__ int pair_hessian_lowrank(bool ee, const double *Xd, const PairGrad &P, T d, T kB, T *K, T *wh,
+                                    T ch[2][4], T *rh) {
     Feature f = feature_of(ee, P.type);
-    T w[4], r[3] = {0, 0, 0}, D[2][3] = {{0, 0, 0}, {0, 0, 0}};
-    T b0 = T(P.b0), b1 = T(P.b1);
+    T w[4], r[3], D[2][3];
+    {
+        double wd[4], rd[3] = {0, 0, 0}, Dd[2][3] = {{0, 0, 0}, {0, 0, 0}};
 #pragma unroll
-    for (int v = 0; v < 4; ++v) w[v] = T(f.w0[v]) + b0 * T(f.c[0][v]) + b1 * T(f.c[1][v]);
+        for (int v = 0; v < 4; ++v) wd[v] = f.w0[v] + P.b0 * f.c[0][v] + P.b1 * f.c[1][v];
 #pragma unroll
-    for (int v = 0; v < 4; ++v)
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                rd[a] += wd[v] * Xd[3 * v + a];
+                Dd[0][a] += f.c[0][v] * Xd[3 * v + a];
+                Dd[1][a] += f.c[1][v] * Xd[3 * v + a];
+            }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) w[v] = T(wd[v]);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            r[a] += w[v] * X[3 * v + a];
-            D[0][a] += T(f.c[0][v]) * X[3 * v + a];
-            D[1][a] += T(f.c[1][v]) * X[3 * v + a];
+            r[a] = T(rd[a]);
+            D[0][a] = T(Dd[0][a]);
+            D[1][a] = T(Dd[1][a]);
         }
+    }
     const int k = f.k, n = 3 + k;
     T wn2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2] + w[3] * w[3], wn = tsqrt(wn2);
 #pragma unroll

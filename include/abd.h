@@ -203,6 +203,16 @@ int abd_partition_masks(abd_scene *s, double h, uint64_t *mask, double *w_out);
  * kept as computed, so the caller can inspect or restore it. */
 int abd_step(abd_scene *s, const abd_step_params *p, abd_step_stats *stats);
 
+/* Level-1 broad phase (overlapping slot pairs) of later steps: mode 0 (the
+ * default) uses a spatial hash when some partition holds at least 1024 slots
+ * and otherwise tests every pair within each partition; 1 always tests
+ * every pair within each partition; 2 always uses the hash (a uniform grid of
+ * cells 1.01 x the largest slot box, counting-sorted into buckets, at most
+ * 27 cells visited per slot).  Both give the same pair set (the broad phase
+ * of Sec. 6's candidate pairs, whose method the paper leaves open).
+ * ABD_E_INVALID for another mode. */
+int abd_scene_broadphase(abd_scene *s, int32_t mode);
+
 /* Initial capacity, in pair records, of the scene's device pair lists
  * (candidates, active pairs, line-search pairs; the cluster-pair list gets
  * four times as many).  Lists grow by themselves when a count exceeds its

@@ -85,7 +85,7 @@ EXPORTS = ["abd_scene_create", "abd_scene_destroy", "abd_scene_counts", "abd_bod
            "abd_server_submit", "abd_server_poll", "abd_server_wait", "abd_server_result", "abd_server_latencies",
            "abd_server_error", "abd_server_destroy", "abd_partition_planes", "abd_pd_update", "abd_scene_reserve",
            "abd_scene_create_batch", "abd_batch_layout", "abd_partition_newton",
-           "abd_server_submit_keyed", "abd_server_release"]
+           "abd_server_submit_keyed", "abd_server_release", "abd_scene_broadphase"]
 
 _lib = None
 
@@ -125,6 +125,7 @@ def load(path: Optional[str] = None):
     L.abd_partition_get.argtypes = [vp, C.c_int32, vp, C.c_int32, i32p, vp, C.c_int32, i32p]
     L.abd_partition_planes.argtypes = [vp, vp, C.c_int32, i32p]
     L.abd_scene_reserve.argtypes = [vp, i64]
+    L.abd_scene_broadphase.argtypes = [vp, C.c_int32]
     L.abd_scene_create_batch.argtypes = [vp, C.c_int32, vp, C.POINTER(vp)]
     L.abd_batch_layout.argtypes = [vp, vp, C.c_int32, i32p]
     L.abd_partition_newton.argtypes = [vp, vp, C.c_int32, i32p]
@@ -280,6 +281,10 @@ class Scene:
         it = np.zeros(max(1, n.value), dtype=np.int32)
         self._check(self.L.abd_partition_newton(self.h, _p(it), n.value, C.byref(n)), "abd_partition_newton")
         return it[:n.value]
+
+    def broadphase(self, mode):
+        """Level-1 pass of later steps: 0 automatic, 1 all pairs per partition, 2 spatial hash."""
+        self._check(self.L.abd_scene_broadphase(self.h, int(mode)), "abd_scene_broadphase")
 
     def reserve(self, pairs):
         self._check(self.L.abd_scene_reserve(self.h, int(pairs)), "abd_scene_reserve")

@@ -11,7 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libabd.so")
-SOURCES = ["abd_scene.cu", "abd_broad.cu", "abd_assemble.cu", "abd_solve.cu", "abd_pcg.cu", "abd_noalloc.cu", "abd_server.cu"]
+SOURCES = ["abd_scene.cu", "abd_broad.cu", "abd_hash.cu", "abd_assemble.cu", "abd_solve.cu", "abd_pcg.cu",
+           "abd_noalloc.cu", "abd_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

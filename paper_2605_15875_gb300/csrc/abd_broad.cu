@@ -851,11 +851,16 @@ static int read_counter(abd_scene *s, unsigned long long *dptr, unsigned long lo
     return cuda_check(s, e, "read counter");
 }
 
-// Level 1 within partitions (k_l1_part) into w.l1, counting into Counters::l1.
+// Level 1 within partitions (k_l1_part, or the spatial hash of abd_hash.cu
+// when the world uses it) into w.l1, counting into Counters::l1.
 static void launch_l1_part(abd_scene *s, bool swept) {
     World &w = s->w;
     Counters *c = P<Counters>(w.ctr);
     if (w.S_dyn == 0) return;
+    if (w.use_hash) {
+        launch_l1_hash(s, swept);
+        return;
+    }
     ABD_LAUNCH(s, k_l1_part, grid_for((int64_t)w.S_dyn * 32, 256), 256, 0, s->stream, w.S_dyn, w.S_all,
                P<int>(w.slot_part), P<int>(w.part_off), P<int>(w.static_grp),
                swept ? P<float>(w.box1) : P<float>(w.box), P<PartState>(w.part), P<int2>(w.l1), w.cap_l1, &c->l1);

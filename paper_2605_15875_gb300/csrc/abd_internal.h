@@ -75,6 +75,8 @@ struct SceneDev {
 };
 
 constexpr int kClusterSize = 32;
+// Partition size from which the automatic level 1 switches to the spatial hash.
+constexpr int kHashMinSlots = 1024;
 // Deepest adaptive time-step split a step may request (2^16 sub-steps).
 constexpr int kMaxDtSplit = 16;
 // Inertia weight of kinematic bodies (prescribed motion through their
@@ -105,6 +107,10 @@ struct World {
     DBuf cp;           // [cap_cp] int4 cluster pairs of the level-2 pass
     DBuf static_grp;   // [S_all - S_dyn] partition a static slot serves (-1: every partition)
     DBuf pinv;         // [S_dyn][144] preconditioner blocks when a partition is too large to stage them
+    // spatial-hash level 1 (abd_hash.cu): bucket counts, cursors, starts, block
+    // sums (+ the cell-size word), slots sorted by bucket
+    DBuf hash_cnt, hash_cur, hash_start, hash_bsum, hash_sorted;
+    bool use_hash = false;  // level 1 through the spatial hash (else partition-local all pairs)
     int64_t C = 0;
     int64_t cap_l1 = 0, cap_cand = 0, cap_act = 0, cap_ls = 0, cap_cp = 0;
     int ecap_mult = 16;  // PCG neighbour-list capacity per owned slot
@@ -195,6 +201,7 @@ struct abd_scene {
     std::vector<int> group;
     std::vector<int64_t> group_off;
     std::vector<int64_t> last_part_newton;  // Newton iterations per partition in the last step
+    int bp_mode = 0;  // level 1: 0 hash when a partition has >= kHashMinSlots slots, 1 all pairs, 2 hash
     // partition
     int axis = 0, n_slabs = 1;
     std::vector<double> slab_planes;
@@ -239,6 +246,10 @@ int launch_l2(abd_scene *s, int mode, bool swept, double half, int64_t n_l1, int
               int64_t *count);
 int launch_l1_async(abd_scene *s, bool swept, int cross = 0);
 double l2_bytes_per_pair(const abd_scene *s, bool swept);
+// ---- (abd_hash.cu) ----
+int hash_table_size(int S);
+bool hash_ensure(abd_scene *s);
+void launch_l1_hash(abd_scene *s, bool swept);
 int launch_l2_async(abd_scene *s, bool swept, double half);
 // ---- (abd_assemble.cu) ----
 int launch_narrow_async(abd_scene *s, const PairRec *src, const unsigned long long *src_n, int64_t src_cap,

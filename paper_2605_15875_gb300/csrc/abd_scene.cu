@@ -464,6 +464,13 @@ extern "C" int abd_partition(abd_scene *s, const abd_partition_desc *d) {
     return ABD_OK;
 }
 
+extern "C" int abd_scene_broadphase(abd_scene *s, int32_t mode) {
+    if (!s || mode < 0 || mode > 2) return ABD_E_INVALID;
+    s->bp_mode = mode;
+    ++s->w.gen;  // the next world picks its level-1 pass anew
+    return ABD_OK;
+}
+
 extern "C" int abd_scene_reserve(abd_scene *s, int64_t pairs) {
     if (!s || pairs < 0) return ABD_E_INVALID;
     int64_t n = std::max<int64_t>(pairs, 16);

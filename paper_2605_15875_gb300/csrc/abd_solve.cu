@@ -424,7 +424,11 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
     w.S_dyn = (int)w.h_slot_body.size();
     w.h_part_off.assign(nparts + 1, 0);
     for (int i = 0; i < w.S_dyn; ++i) w.h_part_off[w.h_slot_part[i] + 1]++;
+    int maxn = 0;
+    for (int p = 0; p < nparts; ++p) maxn = std::max(maxn, w.h_part_off[p + 1]);
     for (int p = 0; p < nparts; ++p) w.h_part_off[p + 1] += w.h_part_off[p];
+    // level 1 through the spatial hash for large partitions (or as asked)
+    w.use_hash = s->bp_mode == 2 || (s->bp_mode == 0 && maxn >= kHashMinSlots);
     std::vector<int> static_grp;
     for (int b = 0; b < s->nb; ++b)
         if (s->kind[b] == ABD_STATIC) {
@@ -478,6 +482,7 @@ int build_world(abd_scene *s, const std::vector<uint64_t> &mask, int nparts) {
               dbuf_ensure(w.part, sizeof(PartState) * kMaxParts) && dbuf_ensure(w.ctr, sizeof(Counters)) &&
               dbuf_ensure(w.cbox, 48 * (size_t)(w.C ? w.C : 1)) && dbuf_ensure(w.cbox1, 48 * (size_t)(w.C ? w.C : 1));
     if (!ok) return set_err(s, ABD_E_OOM, "world buffers");
+    if (w.use_hash && !hash_ensure(s)) return set_err(s, ABD_E_OOM, "spatial hash");
     if (w.S_all > 0) ABD_LAUNCH(s, k_fill_sv_slot, std::min(w.S_all, 152 * 8), 256, 0, s->stream, w.S_all, P<int64_t>(w.slot_voff), P<int>(w.sv_slot));
     return cuda_check(s, cudaGetLastError(), "build world");
 }

@@ -129,6 +129,11 @@ typedef struct {
                                       blocks after K rounds, retake the step from the same state as two
                                       steps of h/2, recursively up to this depth, before the one-partition
                                       fallback; 0 (default) disables it; at most 16 */
+    int32_t mixed_fp64_first;      /* ABD_MIXED only: 1 (default) takes the first Newton iteration of every
+                                      local solve with FP64 assembly and PCG, the later ones in FP32 -- the
+                                      first step is the long one, and an FP32 Hessian's rounding can steer
+                                      its line search into another local minimum of the non-convex
+                                      contact energy; 0: every iteration in FP32 */
 } abd_step_params;
 
 typedef struct {

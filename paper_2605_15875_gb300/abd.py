@@ -42,7 +42,8 @@ class StepParams(C.Structure):
                 ("mu", C.c_double), ("sigma_min", C.c_double), ("sigma_max", C.c_double), ("theta", C.c_double),
                 ("newton_tol", C.c_double), ("max_admm", C.c_int32), ("max_newton", C.c_int32),
                 ("max_halvings", C.c_int32), ("pcg_rtol", C.c_double), ("pcg_max", C.c_int32),
-                ("accd_s", C.c_double), ("accd_c", C.c_double), ("dt_split_max", C.c_int32)]
+                ("accd_s", C.c_double), ("accd_c", C.c_double), ("dt_split_max", C.c_int32),
+                ("mixed_fp64_first", C.c_int32)]
 
 
 class StepStats(C.Structure):

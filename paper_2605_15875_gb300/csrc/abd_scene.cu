@@ -563,6 +563,7 @@ extern "C" abd_step_params abd_step_params_default(void) {
     p.pcg_rtol = 1e-12; p.pcg_max = 5000;
     p.accd_s = 0.1; p.accd_c = 0.9;
     p.dt_split_max = 0;
+    p.mixed_fp64_first = 1;
     return p;
 }
 

@@ -313,6 +313,7 @@ struct Ctx {
     std::vector<double> kBp, lp;  // per partition: barrier stiffness and scene scale
     abd_step_stats *st;
     int precision;
+    int it_prec = 0;  // precision of the blocks and PCG of the last enqueued iteration
     DBuf alphas, nh0, decided, pending;
     double t_coll = 0, t_solve = 0, t_sync = 0;
     std::vector<int64_t> part_newton;  // Newton iterations per partition over the step
@@ -546,7 +547,9 @@ int ensure_lists(Ctx &C) {
     if (w.cap_act == 0) w.cap_act = 1 << 15;
     if (w.cap_ls == 0) w.cap_ls = 1 << 16;
     if (w.cap_cp == 0) w.cap_cp = 1 << 18;
-    size_t tb = C.precision == ABD_MIXED ? 4 : 8;
+    // block storage: FP32 in the mixed path, unless its first Newton
+    // iterations assemble FP64 blocks into the same buffers
+    size_t tb = C.precision == ABD_MIXED && !C.p->mixed_fp64_first ? 4 : 8;
     bool ok = dbuf_ensure(w.l1, 8 * (size_t)w.cap_l1) && dbuf_ensure(w.cand, sizeof(PairRec) * (size_t)w.cap_cand) &&
               dbuf_ensure(w.act, sizeof(PairRec) * (size_t)w.cap_act) &&
               dbuf_ensure(w.ls, sizeof(PairRec) * (size_t)w.cap_ls) && dbuf_ensure(w.cp, sizeof(int4) * (size_t)w.cap_cp) &&
@@ -596,8 +599,13 @@ int enqueue_iteration(Ctx &C, bool static_bp, Status *hs) {
         return rc;
     }
     // assemble, precondition, solve
-    if ((rc = launch_assemble_async(s, C.precision, p))) return rc;
-    if ((rc = launch_pcg_async(s, C.precision, p))) return rc;
+    // the first (directly launched) iteration of a local solve in FP64 when
+    // the mixed path asks for it; the captured steady-state iterations in
+    // the path's own precision
+    const int prec = static_bp && C.precision == ABD_MIXED && p->mixed_fp64_first ? ABD_FP64 : C.precision;
+    C.it_prec = prec;
+    if ((rc = launch_assemble_async(s, prec, p))) return rc;
+    if ((rc = launch_pcg_async(s, prec, p))) return rc;
     // Newton stopping test before the line search
     ABD_LAUNCH(s, k_dqmax, grid_for(w.S_dyn, 128), 128, 0, s->stream, w.S_dyn, P<int>(w.slot_part), P<double>(w.dq),
                P<PartState>(w.part));
@@ -704,6 +712,7 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         double t0 = now_ms();
         bool graphed = !static_bp && iteration_graph(C, hs);
         if (graphed) {
+            C.it_prec = C.precision;  // the captured iteration runs in the path's own precision
             if ((rc = cuda_check(s, cudaGraphLaunch(s->ig.exec, s->stream), "graph launch"))) return rc;
             s->n_launches += s->ig.kernels;
         } else if ((rc = enqueue_iteration(C, static_bp, hs))) {
@@ -745,7 +754,7 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
         C.st->pcg_unstaged |= hs->pcg_unstaged != 0;
         pcg_tune_observe(s, pmax);
         if (s->prof) {
-            double tb = C.precision == ABD_MIXED ? 4.0 : 8.0;
+            double tb = C.it_prec == ABD_MIXED ? 4.0 : 8.0;
             // algorithmic bytes of one PCG launch, counted per iteration: each
             // iteration of partition i reads its blocks (diagonal and
             // off-diagonal, 144 entries each) and seven 12-vectors per slot

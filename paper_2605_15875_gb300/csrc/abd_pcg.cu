@@ -340,238 +340,9 @@ __global__ void __launch_bounds__(256) k_pcg_cluster(PcgClArgs A, int smem_bytes
     if (rank == 0 && threadIdx.x == 0) A.iters[part] = it;
 }
 
-// Pipelined variant of the same solve (preconditioned CG in the form of
-// Ghysels and Vanroose 2014, "Hiding global synchronization latency in the
-// preconditioned conjugate gradient algorithm"), for the mixed path's FP32
-// iterations: with u = P r, w = H u, m = P w and n = H m carried as vectors,
-// the two dot products of an iteration, (r, u) and (w, u), need only local
-// vectors and are reduced together with the publication of m, so an
-// iteration has ONE cluster barrier instead of two; the matrix-vector product
-// n = H m follows the barrier (neighbours' m read from their shared memory).
-// m and the partial sums are double-buffered by iteration parity: a CTA
-// overwrites a buffer only after the next barrier, which every CTA reaches
-// after its last read of it.  Same stopping rules as k_pcg_cluster (mixed:
-// |u|_inf <= rtol |u0|_inf, u = P r).  Vectors (T): r, u, w, m[2], n, z, q,
-// s, p, x.
-template <class T>
-inline size_t pcg_pipe_vec_bytes(int m) {
-    size_t rows = 12 * (size_t)m;
-    return rows * 11 * sizeof(T) + 16 + (144 + 40) * sizeof(T) + 4 * ((size_t)m + 1) + 16;
-}
-template <class T>
-inline size_t pcg_pipe_base_bytes(int m) {
-    return pcg_pipe_vec_bytes<T>(m) + 2 * 144 * sizeof(T) * (size_t)m;
-}
-
-// Block-wide sums of three values and maximum of a fourth (every thread gets
-// all four), through words [0, 32) of the scratch (8 warps x 4).
-template <class R>
-__device__ __forceinline__ void block_reduce3max(R &a, R &b, R &c, R &mx, R *scratch) {
-    for (int o = 16; o; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-        R t = __shfl_xor_sync(0xffffffffu, mx, o);
-        mx = t > mx ? t : mx;
-    }
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { scratch[4 * w] = a; scratch[4 * w + 1] = b; scratch[4 * w + 2] = c; scratch[4 * w + 3] = mx; }
-    __syncthreads();
-    a = b = c = mx = R(0);
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-        a += scratch[4 * i];
-        b += scratch[4 * i + 1];
-        c += scratch[4 * i + 2];
-        mx = scratch[4 * i + 3] > mx ? scratch[4 * i + 3] : mx;
-    }
-}
-
-template <class T>
-__global__ void __launch_bounds__(256) k_pcg_pipe(PcgClArgs A, int smem_bytes) {
-    cg::cluster_group cl = cg::this_cluster();
-    const int CS = (int)cl.num_blocks();
-    const int rank = (int)cl.block_rank();
-    const int part = blockIdx.x / CS;
-    const int s0 = A.part_off[part], s1 = A.part_off[part + 1], n = s1 - s0;
-    const int m = (n + CS - 1) / CS;
-    const int my0 = min(s1, s0 + rank * m), my1 = min(s1, my0 + m), mine = my1 - my0;
-    const T *diag = (const T *)A.diag, *off = (const T *)A.off;
-    using R = T;
-
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int rows = 12 * m;
-    T *r = (T *)smem, *u = r + rows, *w = u + rows, *mb0 = w + rows, *mb1 = mb0 + rows, *nv = mb1 + rows;
-    T *zv = nv + rows, *qv = zv + rows, *sv = qv + rows, *pv = sv + rows, *x = pv + rows;
-    R *red = (R *)(((uintptr_t)(x + rows) + 15) & ~uintptr_t(15));  // [144]: [0,128) partials by parity, [128,144) flags
-    R *scratch = red + 144;                                          // [40] block reduction
-    int *rofs = (int *)(scratch + 40);
-    T *blk = (T *)(((uintptr_t)(rofs + m + 1) + 15) & ~uintptr_t(15));
-    const bool gblk = A.pinv != nullptr;
-    T *Ds = gblk ? nullptr : blk;
-    const T *Dr = gblk ? diag + 144 * (int64_t)my0 : Ds;
-    T *Ps = gblk ? (T *)A.pinv + 144 * (int64_t)my0 : blk + 144 * m;
-    unsigned char *tail = (unsigned char *)(gblk ? blk : blk + 2 * 144 * m);
-
-    const bool active = A.part[part].active != 0 && n > 0;
-    if (rank == 0 && threadIdx.x == 0) A.iters[kPcgNent + part] = active ? A.rowoff[s1] - A.rowoff[s0] : 0;
-    if (!active) {
-        for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) A.x[12 * (int64_t)my0 + e] = 0.0;
-        if (rank == 0 && threadIdx.x == 0) A.iters[part] = 0;
-        return;  // uniform over the cluster
-    }
-    const int e0 = A.rowoff[my0], ne = A.rowoff[my0 + mine] - e0;
-    const size_t per_e = sizeof(int) + sizeof(T) * (144 + 12);
-    const int left = max(0, smem_bytes - (int)(tail - smem) - 16);
-    const int es = min(ne, (int)(left / per_e));
-    int *enb = (int *)tail;
-    T *Bs = (T *)(((uintptr_t)(enb + es) + 15) & ~uintptr_t(15));
-    T *gv = Bs + 144 * (size_t)es;  // [es][12] the neighbours' operand of the current product
-    for (int e = threadIdx.x; e < 144 * mine; e += blockDim.x) {
-        T v = diag[144 * (int64_t)my0 + e];
-        if (!gblk) Ds[e] = v;
-        Ps[e] = v;
-    }
-    for (int sl = threadIdx.x; sl <= mine; sl += blockDim.x) rofs[sl] = A.rowoff[my0 + sl] - e0;
-    for (int j = threadIdx.x; j < es; j += blockDim.x) enb[j] = A.ent[e0 + j].x;
-    for (int64_t e = threadIdx.x; e < 144 * (int64_t)es; e += blockDim.x) {
-        int j = (int)(e / 144), q = (int)(e % 144), i = q / 12, c = q % 12;
-        int2 en = A.ent[e0 + j];
-        const T *B = off + 144 * (int64_t)(en.y & 0x7fffffff);
-        Bs[e] = en.y < 0 ? B[12 * c + i] : B[12 * i + c];
-    }
-    __syncthreads();
-    invert_blocks(Ps, mine);
-    // out = H v over my rows, v given in every CTA's shared memory at the same
-    // offset: staged entries from the copies in gv (filled by the caller),
-    // the others straight from the owner's shared memory
-    auto matvec = [&](const T *v, T *out) {
-        for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
-            int sl = e / 12, i = e % 12;
-            const T *D = Dr + 144 * sl + 12 * i;
-            T acc = T(0);
-            for (int j = 0; j < 12; ++j) acc += D[j] * v[12 * sl + j];
-            for (int jj = rofs[sl]; jj < rofs[sl + 1]; ++jj) {
-                if (jj < es) {
-                    const T *B = Bs + 144 * jj + 12 * i;
-                    const T *pn = gv + 12 * jj;
-                    for (int c = 0; c < 12; ++c) acc += B[c] * pn[c];
-                } else {
-                    int2 en = A.ent[e0 + jj];
-                    int nb = en.x, bi = en.y;
-                    const T *B = off + 144 * (int64_t)(bi & 0x7fffffff);
-                    int o = (nb - s0) / m, lo = (nb - s0) - o * m;
-                    const T *pn = (o == rank ? v : cl.map_shared_rank(const_cast<T *>(v), o)) + 12 * lo;
-                    if (bi >= 0)
-                        for (int c = 0; c < 12; ++c) acc += B[12 * i + c] * pn[c];
-                    else
-                        for (int c = 0; c < 12; ++c) acc += B[12 * c + i] * pn[c];
-                }
-            }
-            out[e] = acc;
-        }
-    };
-    // copies of the neighbours' entries of v for the staged entries
-    auto stage = [&](const T *v) {
-        for (int e = threadIdx.x; e < 12 * es; e += blockDim.x) {
-            int j = e / 12, i = e % 12, nb = enb[j];
-            int o = (nb - s0) / m, lo = (nb - s0) - o * m;
-            gv[e] = (o == rank ? v : cl.map_shared_rank(const_cast<T *>(v), o))[12 * lo + i];
-        }
-    };
-    auto precond = [&](const T *in, T *out) {
-        for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
-            int sl = e / 12, i = e % 12;
-            const T *M = Ps + 144 * sl + 12 * i;
-            T t = T(0);
-            for (int j = 0; j < 12; ++j) t += M[j] * in[12 * sl + j];
-            out[e] = t;
-        }
-    };
-    // r = -g, x = 0, u = P r, then w = H u (needs the neighbours' u)
-    for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
-        r[e] = T(-A.g[12 * (int64_t)my0 + e]);
-        x[e] = zv[e] = qv[e] = sv[e] = pv[e] = T(0);
-    }
-    __syncthreads();
-    precond(r, u);
-    __syncthreads();
-    cl.sync();  // every CTA has started and published u
-    {
-        R f = es < ne ? R(1) : R(0);
-        push_partials(cl, red, 128, &f, 1, rank, CS);
-    }
-    stage(u);
-    __syncthreads();
-    matvec(u, w);
-    cl.sync();  // flags published; no CTA reuses u's slot as an operand before every product of u is done
-    R unstaged = R(0);
-    for (int q = 0; q < CS; ++q) unstaged += red[128 + q];
-    if (unstaged > R(0) && rank == 0 && threadIdx.x == 0) A.iters[kPcgUnstaged] = 1;
-    int it = 0, par = 0;
-    R r0 = R(0), zm0 = R(0), gam_old = R(1), alpha_old = R(1);
-    for (;;) {
-        T *mcur = par ? mb1 : mb0;
-        R gl = R(0), dl = R(0), rl = R(0), ml = R(0);
-        for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
-            gl += r[e] * u[e];
-            dl += w[e] * u[e];
-            rl += r[e] * r[e];
-            ml = fabs(u[e]) > ml ? R(fabs(u[e])) : ml;
-        }
-        precond(w, mcur);
-        block_reduce3max(gl, dl, rl, ml, scratch);
-        {
-            R v[4] = {gl, dl, rl, ml};
-            push_partials(cl, red, 64 * par, v, 4, rank, CS);
-        }
-        cl.sync();  // partials and m published
-        R gam = R(0), del = R(0), rr = R(0), um = R(0);
-        for (int q = 0; q < CS; ++q) {
-            const R *pq = red + 64 * par + 4 * q;
-            gam += pq[0];
-            del += pq[1];
-            rr += pq[2];
-            um = pq[3] > um ? pq[3] : um;
-        }
-        if (it == 0) {
-            r0 = rr;
-            zm0 = um;
-        }
-        const bool done = !(r0 > R(0)) || (it > 0 && (A.zrel ? um <= R(A.tol) * zm0 : rr <= R(A.tol2) * r0));
-        if (done || it >= A.max_it) break;  // identical in every CTA of the cluster
-        stage(mcur);
-        __syncthreads();
-        matvec(mcur, nv);
-        const R beta = it > 0 ? gam / gam_old : R(0);
-        const R alpha = it > 0 ? gam / (del - beta * gam / alpha_old) : gam / del;
-        for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) {
-            zv[e] = nv[e] + beta * zv[e];
-            qv[e] = mcur[e] + beta * qv[e];
-            sv[e] = w[e] + beta * sv[e];
-            pv[e] = u[e] + beta * pv[e];
-            x[e] += alpha * pv[e];
-            r[e] -= alpha * sv[e];
-            u[e] -= alpha * qv[e];
-            w[e] -= alpha * zv[e];
-        }
-        gam_old = gam;
-        alpha_old = alpha;
-        __syncthreads();
-        par ^= 1;
-        ++it;
-    }
-    cl.sync();  // no CTA leaves while another may still read its shared memory
-    for (int e = threadIdx.x; e < 12 * mine; e += blockDim.x) A.x[12 * (int64_t)my0 + e] = (double)x[e];
-    if (rank == 0 && threadIdx.x == 0) A.iters[part] = it;
-}
-
 template <class T>
 static int launch_T(abd_scene *s, const abd_step_params *p) {
     World &w = s->w;
-    // the FP32 iterations of the mixed path run the single-barrier pipelined
-    // form; FP64 solves the classic form
-    constexpr bool pipe = sizeof(T) == 4;
-    const auto kern = pipe ? k_pcg_pipe<T> : k_pcg_cluster<T>;
     // device limits and kernel attributes, set once (thread-safe static init)
     struct Limits {
         int max_cluster;
@@ -584,11 +355,8 @@ static int launch_T(abd_scene *s, const abd_step_params *p) {
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         L.max_smem = (size_t)optin;
         cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-        cudaFuncSetAttribute(k_pcg_pipe<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
         L.max_cluster =
-            cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
-                    cudaFuncSetAttribute(k_pcg_pipe<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
-                        cudaSuccess
+            cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess
                 ? 16
                 : 8;
         cudaGetLastError();
@@ -605,9 +373,9 @@ static int launch_T(abd_scene *s, const abd_step_params *p) {
     // memory (gblk) when the largest partition's do not fit
     auto smem_for = [&](int cs, size_t &smem, bool &gblk) {
         int m = std::max(1, (maxn + cs - 1) / cs);
-        size_t base = pipe ? pcg_pipe_base_bytes<T>(m) : pcg_base_bytes<T>(m);
+        size_t base = pcg_base_bytes<T>(m);
         gblk = base + 1024 > max_smem;
-        if (gblk) base = pipe ? pcg_pipe_vec_bytes<T>(m) : pcg_vec_bytes<T>(m);
+        if (gblk) base = pcg_vec_bytes<T>(m);
         smem = std::max(base + 1024, std::min(max_smem, base + (size_t)m * 12 * (144 + 12 + 4) * sizeof(T)));
         return base + 1024 <= max_smem;
     };
@@ -649,7 +417,7 @@ static int launch_T(abd_scene *s, const abd_step_params *p) {
             cudaLaunchAttribute at[1];
             config(c, sm, cf, at);
             int nclu = 0;
-            if (cudaOccupancyMaxActiveClusters(&nclu, kern, &cf) != cudaSuccess || nclu < 1) {
+            if (cudaOccupancyMaxActiveClusters(&nclu, k_pcg_cluster<T>, &cf) != cudaSuccess || nclu < 1) {
                 cudaGetLastError();
                 continue;
             }
@@ -692,7 +460,7 @@ static int launch_T(abd_scene *s, const abd_step_params *p) {
     cudaEvent_t ea, eb;
     prof_begin(s, "pcg", 0, &ea, &eb);
     if (timed) cudaEventRecord(tu.a, s->stream);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A, (int)smem);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_pcg_cluster<T>, A, (int)smem);
     if (timed) cudaEventRecord(tu.b, s->stream);
     prof_end(s, ea, eb, prof_index(s, "pcg"));
     ++s->n_launches;

@@ -91,6 +91,9 @@ def test_server_and_partition_calls_reject_bad_arguments():
     assert L.abd_server_create(ctypes.byref(bad), ctypes.byref(h)) == -1
     t = ctypes.c_int64()
     assert L.abd_server_submit(None, None, None, None, 1, ctypes.byref(t)) == -1
+    assert L.abd_server_submit_keyed(None, 1, None, None, None, 1, ctypes.byref(t)) == -1
+    assert L.abd_server_release(None, 1) == -1
+    assert L.abd_scene_broadphase(None, 2) == -1
     n = ctypes.c_int32()
     assert L.abd_partition_planes(None, None, 0, ctypes.byref(n)) == -1
     assert L.abd_pd_update(0, None, None, 0.0, 0.0, None, None) == -1

@@ -95,3 +95,20 @@ def test_clock_summary_reads_reasons_and_median():
     s = c.summary()
     assert s["sm_mhz"] == 2000.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
     assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_keyed_requests_split_each_scene_and_count_body_steps():
+    """The serving workload as keyed requests: each scene's steps split into
+    a first request carrying the scene and a continuation without it (none
+    when the scene advances one step), and body-steps counted from each
+    request's key scene and its steps done."""
+    import bench
+    reqs = [(_Scene(10), 5), (_Scene(3), 1), (_Scene(7), 4)]
+    keyed = bench._keyed(reqs)
+    assert [(k, sa is not None, n) for k, sa, n in keyed] == [
+        (1, True, 2), (1, False, 3), (2, True, 1), (3, True, 2), (3, False, 2)]
+    infos = [{"steps_done": n} for _, _, n in keyed]
+    assert bench._body_steps(keyed, infos) == 10 * 5 + 3 * 1 + 7 * 4
+    infos[1]["steps_done"] = 0  # a continuation that did nothing counts nothing
+    assert bench._body_steps(keyed, infos) == 10 * 2 + 3 * 1 + 7 * 4
+    assert bench._body_steps(reqs, [{"steps_done": n} for _, n in reqs]) == 10 * 5 + 3 + 28

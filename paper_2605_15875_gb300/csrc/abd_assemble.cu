@@ -575,7 +575,8 @@ __global__ void k_ccd(const PairRec *__restrict__ cand, int64_t n, const unsigne
             int sa, sb;
             pair_slots(r, sv_slot, sa, sb);
             int p = pair_part(sa, sb, S_dyn, slot_part);
-            double t = accd(ee, X, dX, s_, c_, 1000000);
+            double d0 = 0.0;
+            double t = accd(ee, X, dX, s_, c_, 1000000, want_ls ? &d0 : nullptr);
             if (t < 1.0) atomicMin(&part[p].toi, ord(t));
             if (want_ls) {
                 double mean[3] = {0, 0, 0}, nn[4];
@@ -586,9 +587,6 @@ __global__ void k_ccd(const PairRec *__restrict__ cand, int64_t n, const unsigne
                     nn[v] = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
                 }
                 double lp = ee ? fmax(nn[0], nn[1]) + fmax(nn[2], nn[3]) : nn[0] + fmax(nn[1], fmax(nn[2], nn[3]));
-                int ty;
-                double b0, b1;
-                double d0 = sqrt(classify<double>(ee, X, ty, b0, b1));
                 keep = d0 - lp < dhat;
             }
         }

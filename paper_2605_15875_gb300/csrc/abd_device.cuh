@@ -667,7 +667,9 @@ __device__ __forceinline__ double pair_energy(bool ee, const double *X, double d
 // summed.  First advance (1 - s) d0 / l_p, later c d / l_p; an advance
 // reaching t = 1 certifies the path (exactly 1); once the distance after a
 // later advance drops below s d0, the previous time is returned.
-__device__ inline double accd(bool ee, const double *X, const double *dX, double s, double c, int max_iter) {
+// With d0_out, the distance at t = 0 (computed once for both uses).
+__device__ inline double accd(bool ee, const double *X, const double *dX, double s, double c, int max_iter,
+                              double *d0_out = nullptr) {
     double mean[3] = {0, 0, 0};
     for (int v = 0; v < 4; ++v)
         for (int a = 0; a < 3; ++a) mean[a] += 0.25 * dX[3 * v + a];
@@ -677,10 +679,12 @@ __device__ inline double accd(bool ee, const double *X, const double *dX, double
         n[v] = sqrt(p0 * p0 + p1 * p1 + p2 * p2);
     }
     double lp = ee ? fmax(n[0], n[1]) + fmax(n[2], n[3]) : n[0] + fmax(n[1], fmax(n[2], n[3]));
-    if (lp == 0.0) return 1.0;
+    if (lp == 0.0 && !d0_out) return 1.0;
     int ty;
     double b0, b1;
     double d = sqrt(classify<double>(ee, X, ty, b0, b1));
+    if (d0_out) *d0_out = d;
+    if (lp == 0.0) return 1.0;
     if (!(d > 0.0)) return 0.0;
     double g = s * d, t = 0.0, step = (1.0 - s) * d / lp;
     for (int it = 0; it < max_iter; ++it) {

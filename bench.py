@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the served leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven-subdomain leg")
     ap.add_argument("--no-sweep", action="store_true", help="serving: closed batch only, no Poisson sweep")
-    ap.add_argument("--batch-steps", type=int, default=6, help="timed steps of the batched leg")
+    ap.add_argument("--batch-steps", type=int, default=4, help="timed steps of the batched leg")
     ap.add_argument("--no-fixed-rho", action="store_true", help="skip the fixed-rho comparison leg")
     ap.add_argument("--no-graph", action="store_true",
                     help="scenes on the legacy default stream (direct launches, no graph replay), e.g. under ncu")

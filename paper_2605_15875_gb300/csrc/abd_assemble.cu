@@ -575,36 +575,19 @@ __global__ void k_ccd(const PairRec *__restrict__ cand, int64_t n, const unsigne
             int sa, sb;
             pair_slots(r, sv_slot, sa, sb);
             int p = pair_part(sa, sb, S_dyn, slot_part);
-            double mean[3] = {0, 0, 0}, nn[4];
-            for (int v = 0; v < 4; ++v)
-                for (int k = 0; k < 3; ++k) mean[k] += 0.25 * dX[3 * v + k];
-            for (int v = 0; v < 4; ++v) {
-                double a0 = dX[3 * v] - mean[0], a1 = dX[3 * v + 1] - mean[1], a2 = dX[3 * v + 2] - mean[2];
-                nn[v] = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
-            }
-            double lp = ee ? fmax(nn[0], nn[1]) + fmax(nn[2], nn[3]) : nn[0] + fmax(nn[1], fmax(nn[2], nn[3]));
-            // Far pairs first: the gap between the two primitives' boxes at the
-            // start bounds their distance d0 from below, so when the motion
-            // bound lp is under (1 - s) times it (with a 1 % margin for
-            // rounding) additive CCD's first advance already reaches t = 1, and
-            // when gap - lp >= dhat the pair cannot come within dhat on the
-            // path: both answers are known without the FP64 distance
-            const int na = ee ? 2 : 1;
-            double g2 = 0.0;
-            for (int k = 0; k < 3; ++k) {
-                double alo = X[k], ahi = X[k], blo = X[3 * na + k], bhi = X[3 * na + k];
-                for (int v = 1; v < na; ++v) { alo = fmin(alo, X[3 * v + k]); ahi = fmax(ahi, X[3 * v + k]); }
-                for (int v = na + 1; v < 4; ++v) { blo = fmin(blo, X[3 * v + k]); bhi = fmax(bhi, X[3 * v + k]); }
-                double sep = fmax(blo - ahi, alo - bhi);
-                if (sep > 0.0) g2 += sep * sep;
-            }
-            const double gap = sqrt(g2);
-            const bool far = lp <= 0.99 * (1.0 - s_) * gap && (!want_ls || gap - lp >= dhat);
-            if (!far) {
-                double d0 = 0.0;
-                double t = accd(ee, X, dX, s_, c_, 1000000, want_ls ? &d0 : nullptr);
-                if (t < 1.0) atomicMin(&part[p].toi, ord(t));
-                keep = want_ls && d0 - lp < dhat;
+            double d0 = 0.0;
+            double t = accd(ee, X, dX, s_, c_, 1000000, want_ls ? &d0 : nullptr);
+            if (t < 1.0) atomicMin(&part[p].toi, ord(t));
+            if (want_ls) {
+                double mean[3] = {0, 0, 0}, nn[4];
+                for (int v = 0; v < 4; ++v)
+                    for (int k = 0; k < 3; ++k) mean[k] += 0.25 * dX[3 * v + k];
+                for (int v = 0; v < 4; ++v) {
+                    double a0 = dX[3 * v] - mean[0], a1 = dX[3 * v + 1] - mean[1], a2 = dX[3 * v + 2] - mean[2];
+                    nn[v] = sqrt(a0 * a0 + a1 * a1 + a2 * a2);
+                }
+                double lp = ee ? fmax(nn[0], nn[1]) + fmax(nn[2], nn[3]) : nn[0] + fmax(nn[1], fmax(nn[2], nn[3]));
+                keep = d0 - lp < dhat;
             }
         }
         if (want_ls) append(keep, r, ls, cap, count);

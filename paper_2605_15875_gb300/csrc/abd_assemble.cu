@@ -189,12 +189,13 @@ __global__ void k_slot_assemble(AsmArgs A, T *__restrict__ diag) {
 
 template <class T> __device__ __forceinline__ void atomic_addT(T *a, T v) { atomicAdd(a, v); }
 
-// Per active pair: barrier gradient and projected Hessian scattered to slots;
-// mollified edge-edge pairs are deferred to k_pair_moll (full 12x12 projection).
+// Per active pair: barrier gradient and projected Hessian scattered to slots.
+// Edge-edge pairs whose mollifier is on (ee_cross2 < eps_x) are skipped: they
+// belong to k_pair_moll (full 12x12 projection), which runs beside this kernel
+// and picks them out with the same test.
 template <class T>
 __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int64_t n, const int2 *__restrict__ l1,
                                 T *__restrict__ diag, T *__restrict__ off, int *__restrict__ offflag,
-                                int64_t *__restrict__ deferred, unsigned long long *__restrict__ n_deferred,
                                 const unsigned long long *__restrict__ n_dev) {
     if (n_dev) n = min((int64_t)*n_dev, n);
     for (int64_t ib = spread_base(); ib < n; ib += (int64_t)gridDim.x * blockDim.x) {
@@ -211,17 +212,12 @@ __global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int6
         double Xd[12];
         for (int v = 0; v < 4; ++v)
             for (int k = 0; k < 3; ++k) Xd[3 * v + k] = A.x[3 * (int64_t)r.v[v] + k] - A.x[3 * (int64_t)r.v[0] + k];
+        if (ee && ee_cross2(Xd) < r.eps) continue;  // mollified: k_pair_moll
         PairGrad PG;
         double gx[12];
         const double kB = A.part[part].kB;  // the barrier stiffness of the pair's partition
         double d = pair_gradient(ee, Xd, A.dhat, kB, r.eps, PG, gx);
         if (!(d < A.dhat) || !(d > 0.0)) continue;
-        const bool moll = ee && PG.moll;
-        if (moll) {
-            unsigned long long pos = atomicAdd(n_deferred, 1ull);
-            deferred[pos] = i;  // capacity n: one slot per active pair
-            continue;
-        }
         double w = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
         int sl[4];
         T xi[4][4];
@@ -384,94 +380,240 @@ __device__ void warp_psd12(T *H, T *W, T *V, T *R, int lane) {
     __syncwarp();
 }
 
-// Mollified edge-edge pairs deferred by k_pair_assemble: one warp per pair.
-// Lane 0 evaluates the FP64 gradient and the raw 12x12 Hessian (T), the warp
-// projects it to PSD and scatters J^T H J and the gradient onto the slots.
+// The raw (unprojected) Hessian of a mollified edge-edge pair's barrier
+// energy, kB [m hess b + b hess m + grad m grad b^T + grad b grad m^T], in
+// closed form: every entry (v a, u c) is a short expression of per-pair
+// vectors, so lane 0 forms those (MollTerms, from the FP64 coordinates and the
+// FP64 feature and barrier scalars of pair_gradient) and every lane then
+// writes its entries.
+//   s = |r|^2 at the stationary beta of the feature, r = sum_v w_v x_v; by the
+//   envelope theorem grad s = 2 w (x) r and
+//   hess s = 2 w_v w_u d_ac - 2 sum_ij Ginv_ij g_i g_j^T,
+//   D_j = sum_v c_jv x_v, G_ij = D_i . D_j, g_j[v] = w_v D_j + c_jv r;
+//   hess b = cg gd gd^T + ch hess s,  gd = grad s / 2d, cg = b'' - b'/d, ch = b'/2d;
+//   m(c) = (c/eps)(2 - c/eps), c = |ea x eb|^2 (below eps_x: the pair is
+//   mollified), hess m = m'' gc gc^T + m' sg_v sg_u He, gc = grad c,
+//   He = the 6x6 Hessian of c in the edge vectors.
+// r, D_j, the edge vectors and their cross product (short for nearly
+// parallel edges) are formed from the FP64 coordinates and rounded to T once
+// formed, as in pair_hessian_lowrank.
+template <class T>
+struct MollTerms {
+    T gd[12], g0[12], g1[12], gc[12], He[36], w[4];
+    T i00, i01, i11, cg, ch, m, m1, m2, b, bp, kB;
+};
+
+template <class T>
+__device__ void moll_terms(const double *Xd, const PairGrad &P, double d, double kB, T eps, MollTerms<T> &M) {
+    Feature f = feature_of(true, P.type);
+    T r[3], D[2][3];
+    {
+        double wd[4], rd[3] = {0, 0, 0}, Dd[2][3] = {{0, 0, 0}, {0, 0, 0}};
+        for (int v = 0; v < 4; ++v) wd[v] = f.w0[v] + P.b0 * f.c[0][v] + P.b1 * f.c[1][v];
+        for (int v = 0; v < 4; ++v)
+            for (int a = 0; a < 3; ++a) {
+                rd[a] += wd[v] * Xd[3 * v + a];
+                Dd[0][a] += f.c[0][v] * Xd[3 * v + a];
+                Dd[1][a] += f.c[1][v] * Xd[3 * v + a];
+            }
+        for (int v = 0; v < 4; ++v) M.w[v] = T(wd[v]);
+        for (int a = 0; a < 3; ++a) {
+            r[a] = T(rd[a]);
+            D[0][a] = T(Dd[0][a]);
+            D[1][a] = T(Dd[1][a]);
+        }
+    }
+    const T dT = T(d), inv2d = T(1) / (T(2) * dT);
+    for (int v = 0; v < 4; ++v)
+        for (int a = 0; a < 3; ++a) M.gd[3 * v + a] = T(2) * M.w[v] * r[a] * inv2d;
+    M.i00 = M.i01 = M.i11 = T(0);
+    if (f.k > 0) {
+        T G00 = dot3(D[0], D[0]), G01 = dot3(D[0], D[1]), G11 = dot3(D[1], D[1]);
+        if (f.k == 1) M.i00 = T(1) / G00;
+        else {
+            T det = G00 * G11 - G01 * G01;
+            M.i00 = G11 / det; M.i11 = G00 / det; M.i01 = -G01 / det;
+        }
+    }
+    for (int v = 0; v < 4; ++v)
+        for (int a = 0; a < 3; ++a) {
+            M.g0[3 * v + a] = M.w[v] * D[0][a] + T(f.c[0][v]) * r[a];
+            M.g1[3 * v + a] = M.w[v] * D[1][a] + T(f.c[1][v]) * r[a];
+        }
+    M.bp = T(P.bp);
+    M.cg = T(P.bpp) - M.bp / dT;
+    M.ch = M.bp * inv2d;
+    M.b = T(P.b);
+    M.kB = T(kB);
+    // mollifier: edge vectors and their cross product formed in FP64
+    T ea[3], eb[3], cr[3], c;
+    {
+        double ead[3] = {Xd[3] - Xd[0], Xd[4] - Xd[1], Xd[5] - Xd[2]};
+        double ebd[3] = {Xd[9] - Xd[6], Xd[10] - Xd[7], Xd[11] - Xd[8]};
+        double crd[3] = {ead[1] * ebd[2] - ead[2] * ebd[1], ead[2] * ebd[0] - ead[0] * ebd[2],
+                         ead[0] * ebd[1] - ead[1] * ebd[0]};
+        for (int k = 0; k < 3; ++k) { ea[k] = T(ead[k]); eb[k] = T(ebd[k]); cr[k] = T(crd[k]); }
+        c = T(crd[0] * crd[0] + crd[1] * crd[1] + crd[2] * crd[2]);
+    }
+    const T rr = c / eps;
+    M.m = rr * (T(2) - rr);
+    M.m1 = (T(2) - T(2) * rr) / eps;
+    M.m2 = T(-2) / (eps * eps);
+    T t[3];
+    cross3(t, eb, cr);
+    for (int k = 0; k < 3; ++k) { M.gc[k] = -T(2) * t[k]; M.gc[3 + k] = T(2) * t[k]; }
+    cross3(t, cr, ea);
+    for (int k = 0; k < 3; ++k) { M.gc[6 + k] = -T(2) * t[k]; M.gc[9 + k] = T(2) * t[k]; }
+    // He = 2 J^T J + the cross-product coupling, J = [-[eb]x, [ea]x]
+    const T J[3][6] = {{0, eb[2], -eb[1], 0, -ea[2], ea[1]},
+                       {-eb[2], 0, eb[0], ea[2], 0, -ea[0]},
+                       {eb[1], -eb[0], 0, -ea[1], ea[0], 0}};
+    const T crx[3][3] = {{0, -cr[2], cr[1]}, {cr[2], 0, -cr[0]}, {-cr[1], cr[0], 0}};
+    for (int a = 0; a < 6; ++a)
+        for (int b = 0; b < 6; ++b) M.He[6 * a + b] = T(2) * (J[0][a] * J[0][b] + J[1][a] * J[1][b] + J[2][a] * J[2][b]);
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) {
+            M.He[6 * j + 3 + k] -= T(2) * crx[j][k];
+            M.He[6 * (3 + j) + k] += T(2) * crx[j][k];
+        }
+}
+
+template <class T>
+__device__ __forceinline__ void moll_entries(const MollTerms<T> &M, T *H, int lane) {
+    for (int e = lane; e < 144; e += 32) {
+        const int i = e / 12, j = e % 12, v = i / 3, a = i % 3, u = j / 3, c = j % 3;
+        T hs = a == c ? T(2) * M.w[v] * M.w[u] : T(0);
+        hs -= T(2) * (M.i00 * M.g0[i] * M.g0[j] + M.i01 * (M.g0[i] * M.g1[j] + M.g1[i] * M.g0[j]) +
+                      M.i11 * M.g1[i] * M.g1[j]);
+        const T hb = M.cg * M.gd[i] * M.gd[j] + M.ch * hs;
+        const T sv = (v & 1) ? T(1) : T(-1), su = (u & 1) ? T(1) : T(-1);
+        const T hm = M.m2 * M.gc[i] * M.gc[j] + M.m1 * sv * su * M.He[6 * (3 * (v >> 1) + a) + 3 * (u >> 1) + c];
+        const T gmi = M.m1 * M.gc[i], gmj = M.m1 * M.gc[j], gbi = M.bp * M.gd[i], gbj = M.bp * M.gd[j];
+        H[e] = M.kB * (hm * M.b + gmi * gbj + gbi * gmj + M.m * hb);
+    }
+}
+
+// Mollified edge-edge pairs (ee_cross2 < eps_x, the pairs k_pair_assemble
+// skips), one warp per pair; it runs beside k_pair_assemble.  The warps find
+// their pairs themselves: lane l of warp w tests active pair w + l * nw (nw
+// warps in the grid, then the next 32 * nw), so neighbouring pairs of the
+// list, which tend to be mollified together, go to different warps.  For
+// each pair found, lane 0 evaluates the FP64 gradient and the per-pair terms
+// of the raw 12x12 Hessian (T), the lanes write its entries, the warp projects
+// it to PSD and scatters J^T H J and the gradient onto the slots.  n_moll
+// counts the pairs assembled.
 template <class T>
 __global__ void __launch_bounds__(128) k_pair_moll(AsmArgs A, const PairRec *__restrict__ act,
-                                                   const int64_t *__restrict__ deferred,
-                                                   const unsigned long long *__restrict__ n_def, int64_t cap,
+                                                   const unsigned long long *__restrict__ n_dev, int64_t cap,
                                                    const int2 *__restrict__ l1, T *__restrict__ diag,
-                                                   T *__restrict__ off, int *__restrict__ offflag) {
+                                                   T *__restrict__ off, int *__restrict__ offflag,
+                                                   unsigned long long *__restrict__ n_moll) {
     __shared__ T sH[4][144], sW[4][144], sV[4][144], sR[4][12];
     __shared__ double sg[4][12], sw[4];
     __shared__ T sxi[4][4][4];
     __shared__ int ssl[4][4], sok[4];
+    __shared__ MollTerms<T> smt[4];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t n = min((int64_t)*n_def, cap);
-    for (int64_t ii = (int64_t)blockIdx.x + (int64_t)gridDim.x * wib; ii < n; ii += (int64_t)gridDim.x * 4) {
-        const PairRec r = act[deferred[ii]];
-        if (lane == 0) {
-            int sa, sb;
-            pair_slots(r, A.sv_slot, sa, sb);
-            bool ee = r.flags & 1;
-            double Xd[12];
-            for (int v = 0; v < 4; ++v)
-                for (int k = 0; k < 3; ++k) Xd[3 * v + k] = A.x[3 * (int64_t)r.v[v] + k] - A.x[3 * (int64_t)r.v[0] + k];
-            PairGrad PG;
-            const double kB = A.part[pair_part(sa, sb, A.S_dyn, A.slot_part)].kB;
-            double d = pair_gradient(ee, Xd, A.dhat, kB, r.eps, PG, sg[wib]);
-            sok[wib] = (d < A.dhat) && (d > 0.0);
-            if (sok[wib]) {
-                pair_hessian<T>(ee, Xd, PG, T(d), T(kB), T(r.eps), sH[wib]);
-                sw[wib] = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
-                for (int v = 0; v < 4; ++v) {
-                    int s = A.sv_slot[r.v[v]];
-                    ssl[wib][v] = s < A.S_dyn ? s : -1;
-                    int b = A.slot_body[s];
-                    const double *xb = A.xbar + 3 * ((int64_t)A.voff[b] + (r.v[v] - A.slot_voff[s]));
-                    sxi[wib][v][0] = T(1); sxi[wib][v][1] = T(xb[0]); sxi[wib][v][2] = T(xb[1]); sxi[wib][v][3] = T(xb[2]);
+    const int64_t n = min((int64_t)*n_dev, cap), nw = (int64_t)gridDim.x * 4;
+    for (int64_t base = (int64_t)blockIdx.x + (int64_t)gridDim.x * wib; base < n; base += 32 * nw) {
+        const int64_t mine = base + lane * nw;
+        bool found = false;
+        if (mine < n) {
+            const PairRec r = act[mine];
+            if (r.flags & 1) {
+                int sa, sb;
+                pair_slots(r, A.sv_slot, sa, sb);
+                if (A.part[pair_part(sa, sb, A.S_dyn, A.slot_part)].active) {
+                    double Xd[12];
+                    for (int v = 0; v < 4; ++v)
+                        for (int k = 0; k < 3; ++k)
+                            Xd[3 * v + k] = A.x[3 * (int64_t)r.v[v] + k] - A.x[3 * (int64_t)r.v[0] + k];
+                    found = ee_cross2(Xd) < r.eps;
                 }
             }
         }
-        __syncwarp();
-        if (!sok[wib]) continue;
-        warp_psd12<T>(sH[wib], sW[wib], sV[wib], sR[wib], lane);
-        const double w = sw[wib];
-        const int *sl = ssl[wib];
-        // gradient: 4 vertices x 3 components x 4 xi entries
-        for (int e = lane; e < 48; e += 32) {
-            int v = e / 12, k = (e / 4) % 3, a = e % 4;
-            if (sl[v] < 0) continue;
-            double xa = a == 0 ? 1.0 : (double)sxi[wib][v][a];
-            atomicAdd(A.g + 12 * (int64_t)sl[v] + qidx(k, a), w * sg[wib][3 * v + k] * xa);
-        }
-        int sa = sl[0] >= 0 ? sl[0] : -1;
-        int sb = sl[(r.flags & 1) ? 2 : 1];
-        int ss[2] = {sa, sb};
-        for (int bi = 0; bi < 2; ++bi)
-            for (int bj = bi; bj < 2; ++bj) {
-                int s1 = ss[bi], s2 = ss[bj];
-                if (s1 < 0 || s2 < 0 || (bi != bj && s1 == s2)) continue;
-                T *dst;
-                bool tr = false;
-                if (bi == bj) dst = diag + 144 * (int64_t)s1;
-                else {
-                    int2 lp = l1[r.l1];
-                    dst = off + 144 * (int64_t)r.l1;
-                    tr = (lp.x != s1);
-                    if (lane == 0 && atomicExch(&offflag[r.l1], 1) == 0) {
-                        atomicAdd(&A.rowcnt[lp.x], 1);
-                        atomicAdd(&A.rowcnt[lp.y], 1);
+        unsigned M = __ballot_sync(0xffffffffu, found);
+        while (M) {
+            const int src = __ffs(M) - 1;
+            M &= M - 1;
+            const PairRec r = act[__shfl_sync(0xffffffffu, mine, src)];
+            if (lane == 0) {
+                int sa, sb;
+                pair_slots(r, A.sv_slot, sa, sb);
+                bool ee = r.flags & 1;
+                double Xd[12];
+                for (int v = 0; v < 4; ++v)
+                    for (int k = 0; k < 3; ++k) Xd[3 * v + k] = A.x[3 * (int64_t)r.v[v] + k] - A.x[3 * (int64_t)r.v[0] + k];
+                PairGrad PG;
+                const double kB = A.part[pair_part(sa, sb, A.S_dyn, A.slot_part)].kB;
+                double d = pair_gradient(ee, Xd, A.dhat, kB, r.eps, PG, sg[wib]);
+                sok[wib] = (d < A.dhat) && (d > 0.0);
+                if (sok[wib]) {
+                    atomicAdd(n_moll, 1ull);
+                    moll_terms<T>(Xd, PG, d, kB, T(r.eps), smt[wib]);
+                    sw[wib] = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
+                    for (int v = 0; v < 4; ++v) {
+                        int s = A.sv_slot[r.v[v]];
+                        ssl[wib][v] = s < A.S_dyn ? s : -1;
+                        int b = A.slot_body[s];
+                        const double *xb = A.xbar + 3 * ((int64_t)A.voff[b] + (r.v[v] - A.slot_voff[s]));
+                        sxi[wib][v][0] = T(1); sxi[wib][v][1] = T(xb[0]); sxi[wib][v][2] = T(xb[1]); sxi[wib][v][3] = T(xb[2]);
                     }
                 }
-                for (int e = lane; e < 144; e += 32) {
-                    int row = e / 12, col = e % 12;
-                    int k = row < 3 ? row : (row - 3) / 3, a = row < 3 ? 0 : 1 + (row - 3) % 3;
-                    int l = col < 3 ? col : (col - 3) / 3, c = col < 3 ? 0 : 1 + (col - 3) % 3;
-                    T acc = T(0);
-                    for (int v = 0; v < 4; ++v) {
-                        if (sl[v] != s1) continue;
-                        for (int u = 0; u < 4; ++u) {
-                            if (sl[u] != s2) continue;
-                            acc += sH[wib][(3 * v + k) * 12 + 3 * u + l] * sxi[wib][v][a] * sxi[wib][u][c];
+            }
+            __syncwarp();
+            const bool ok = sok[wib];
+            __syncwarp();
+            if (!ok) continue;
+            moll_entries<T>(smt[wib], sH[wib], lane);
+            __syncwarp();
+            warp_psd12<T>(sH[wib], sW[wib], sV[wib], sR[wib], lane);
+            const double w = sw[wib];
+            const int *sl = ssl[wib];
+            // gradient: 4 vertices x 3 components x 4 xi entries
+            for (int e = lane; e < 48; e += 32) {
+                int v = e / 12, k = (e / 4) % 3, a = e % 4;
+                if (sl[v] < 0) continue;
+                double xa = a == 0 ? 1.0 : (double)sxi[wib][v][a];
+                atomicAdd(A.g + 12 * (int64_t)sl[v] + qidx(k, a), w * sg[wib][3 * v + k] * xa);
+            }
+            int sa = sl[0] >= 0 ? sl[0] : -1;
+            int sb = sl[(r.flags & 1) ? 2 : 1];
+            int ss[2] = {sa, sb};
+            for (int bi = 0; bi < 2; ++bi)
+                for (int bj = bi; bj < 2; ++bj) {
+                    int s1 = ss[bi], s2 = ss[bj];
+                    if (s1 < 0 || s2 < 0 || (bi != bj && s1 == s2)) continue;
+                    T *dst;
+                    bool tr = false;
+                    if (bi == bj) dst = diag + 144 * (int64_t)s1;
+                    else {
+                        int2 lp = l1[r.l1];
+                        dst = off + 144 * (int64_t)r.l1;
+                        tr = (lp.x != s1);
+                        if (lane == 0 && atomicExch(&offflag[r.l1], 1) == 0) {
+                            atomicAdd(&A.rowcnt[lp.x], 1);
+                            atomicAdd(&A.rowcnt[lp.y], 1);
                         }
                     }
-                    T val = T(w) * acc;
-                    if (val != T(0)) atomic_addT(dst + (tr ? col * 12 + row : row * 12 + col), val);
+                    for (int e = lane; e < 144; e += 32) {
+                        int row = e / 12, col = e % 12;
+                        int k = row < 3 ? row : (row - 3) / 3, a = row < 3 ? 0 : 1 + (row - 3) % 3;
+                        int l = col < 3 ? col : (col - 3) / 3, c = col < 3 ? 0 : 1 + (col - 3) % 3;
+                        T acc = T(0);
+                        for (int v = 0; v < 4; ++v) {
+                            if (sl[v] != s1) continue;
+                            for (int u = 0; u < 4; ++u) {
+                                if (sl[u] != s2) continue;
+                                acc += sH[wib][(3 * v + k) * 12 + 3 * u + l] * sxi[wib][v][a] * sxi[wib][u][c];
+                            }
+                        }
+                        T val = T(w) * acc;
+                        if (val != T(0)) atomic_addT(dst + (tr ? col * 12 + row : row * 12 + col), val);
+                    }
                 }
-            }
-        __syncwarp();
+            __syncwarp();
+        }
     }
 }
 
@@ -811,21 +953,25 @@ static int assemble_async_T(abd_scene *s, const abd_step_params *p) {
         ABD_LAUNCH(s, k_slot_assemble<T>, grid_for(w.S_dyn, 32, 152 * 8), 128, 0, s->stream, A, P<T>(w.diag));
         prof_end(s, ea, eb, prof_index(s, "slot_assemble"));
     }
-    int64_t *defl = P<int64_t>(w.deferred);
-    unsigned long long *ndef = (unsigned long long *)(defl + w.cap_act);
-    cudaMemsetAsync(ndef, 0, 8, s->stream);
+    unsigned long long *nmoll = P<unsigned long long>(w.nmoll);
+    cudaMemsetAsync(nmoll, 0, 8, s->stream);
+    // the mollified pairs (one warp each, the longest chain) on the side
+    // branch, beside the other pairs and the vertex-plane terms; both only
+    // add onto what k_slot_assemble stored
+    cudaStream_t side = fork_side(s);
+    cudaEvent_t ma, mb;
+    prof_begin(s, "pair_moll", 0.0, &ma, &mb, side);
+    ABD_LAUNCH(s, k_pair_moll<T>, 152 * 2, 128, 0, side, A, P<PairRec>(w.act), &c->act, w.cap_act, P<int2>(w.l1),
+               P<T>(w.diag), P<T>(w.off), P<int>(w.offflag), nmoll);
+    prof_end(s, ma, mb, prof_index(s, "pair_moll"), side);
     prof_begin(s, "pair_assemble", 0.0, &ea, &eb);
     ABD_LAUNCH(s, k_pair_assemble<T>, grid_for(w.cap_act, 128, 152 * 8), 128, 0, s->stream, A,
-               P<PairRec>(w.act), w.cap_act, P<int2>(w.l1), P<T>(w.diag), P<T>(w.off), P<int>(w.offflag), defl, ndef,
-               &c->act);
+               P<PairRec>(w.act), w.cap_act, P<int2>(w.l1), P<T>(w.diag), P<T>(w.off), P<int>(w.offflag), &c->act);
     prof_end(s, ea, eb, prof_index(s, "pair_assemble"));
-    prof_begin(s, "pair_moll", 0.0, &ea, &eb);
-    ABD_LAUNCH(s, k_pair_moll<T>, 152 * 2, 128, 0, s->stream, A, P<PairRec>(w.act), defl, ndef, w.cap_act, P<int2>(w.l1),
-               P<T>(w.diag), P<T>(w.off), P<int>(w.offflag));
-    prof_end(s, ea, eb, prof_index(s, "pair_moll"));
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
     if (s->planes.n > 0 && SVd > 0)
         ABD_LAUNCH(s, k_vp_assemble<T>, grid_for(SVd, 256), 256, 0, s->stream, A, SVd, P<T>(w.diag));
+    join_side(s, side);
     ABD_LAUNCH(s, k_csr_scan, 1, 1024, 0, s->stream, w.S_dyn, P<int>(w.rowcnt), P<int>(w.rowoff));
     ABD_LAUNCH(s, k_csr_fill, grid_for(w.cap_l1, 256, 152 * 8), 256, 0, s->stream, &c->l1, w.cap_l1, P<int2>(w.l1),
                P<int>(w.offflag), P<int>(w.rowoff), P<int>(w.rowcur), P<int2>(w.ent));
@@ -842,14 +988,18 @@ int launch_ccd_async(abd_scene *s, const abd_step_params *p, bool want_ls) {
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
     cudaMemsetAsync(&c->ls, 0, 8, s->stream);
     cudaEvent_t ea, eb;
-    prof_begin(s, "ccd", 0.0, &ea, &eb);
-    ABD_LAUNCH(s, k_ccd, grid_for(w.cap_cand, 128, 152 * 8), 128, 0, s->stream, P<PairRec>(w.cand), w.cap_cand, &c->cand,
+    // pair CCD on the side branch, vertex-plane CCD beside it (both only
+    // lower the partitions' TOI)
+    cudaStream_t side = fork_side(s);
+    prof_begin(s, "ccd", 0.0, &ea, &eb, side);
+    ABD_LAUNCH(s, k_ccd, grid_for(w.cap_cand, 128, 152 * 8), 128, 0, side, P<PairRec>(w.cand), w.cap_cand, &c->cand,
                P<double>(w.x), P<double>(w.x1), P<int>(w.sv_slot), P<int>(w.slot_part), w.S_dyn, p->dhat, p->accd_s,
                p->accd_c, P<PartState>(w.part), P<PairRec>(w.ls), w.cap_ls, &c->ls, want_ls ? 1 : 0);
-    prof_end(s, ea, eb, prof_index(s, "ccd"));
+    prof_end(s, ea, eb, prof_index(s, "ccd"), side);
     if (s->planes.n > 0 && SVd > 0)
         ABD_LAUNCH(s, k_vp_ccd, grid_for(SVd, 256), 256, 0, s->stream, SVd, P<double>(w.x), P<double>(w.x1),
                    P<int>(w.sv_slot), P<int>(w.slot_part), s->planes, p->accd_s, P<PartState>(w.part));
+    join_side(s, side);
     return cuda_check(s, cudaGetLastError(), "k_ccd");
 }
 
@@ -869,11 +1019,16 @@ int launch_energy_async(abd_scene *s, const abd_step_params *p, const double *al
     A.h = p->h; A.dhat = p->dhat; A.planes = s->planes;
     int64_t SVd = w.S_dyn > 0 ? w.h_slot_voff[w.S_dyn] : 0;
     cudaEvent_t ea, eb;
+    // the three sums are independent (each adds into the partitions' trial
+    // energies): pairs on the side branch, slots then vertex-plane terms beside
+    // them; the timed span covers both branches
     prof_begin(s, "energy", 0.0, &ea, &eb);
-    if (w.S_dyn > 0) ABD_LAUNCH(s, k_energy_slots, grid_for(w.S_dyn, 32, 152 * 8), 128, 0, s->stream, A);
-    ABD_LAUNCH(s, k_energy_pairs, grid_for(w.cap_ls, 128, 152 * 8), 128, 0, s->stream, A, P<PairRec>(w.ls), w.cap_ls,
+    cudaStream_t side = fork_side(s);
+    ABD_LAUNCH(s, k_energy_pairs, grid_for(w.cap_ls, 128, 152 * 8), 128, 0, side, A, P<PairRec>(w.ls), w.cap_ls,
                &c->ls);
+    if (w.S_dyn > 0) ABD_LAUNCH(s, k_energy_slots, grid_for(w.S_dyn, 32, 152 * 8), 128, 0, s->stream, A);
     if (s->planes.n > 0 && SVd > 0) ABD_LAUNCH(s, k_energy_vp, grid_for(SVd, 32, 152 * 8), 128, 0, s->stream, A, SVd);
+    join_side(s, side);
     prof_end(s, ea, eb, prof_index(s, "energy"));
     return cuda_check(s, cudaGetLastError(), "energy");
 }

@@ -153,74 +153,6 @@ __device__ __forceinline__ Feature feature_of(bool ee, int type) {
     return f;
 }
 
-// s = |r|^2 at the stationary beta of the feature, its gradient gs[12] and the
-// upper triangle of its Hessian (full Hs[144] written) by the envelope
-// theorem: grad = 2 w (x) r; hess = 2 (w w^T (x) I3) - 2 sum_ij Ginv_ij g_i g_j^T,
-// D_j = sum_v c_jv x_v, G_ij = D_i . D_j, g_j[v] = w_v D_j + c_jv r.
-// r and D_j are formed from the FP64 coordinates Xd and rounded to T once
-// formed (r is short next to the coordinates it is summed from; see
-// pair_hessian_lowrank).
-template <class T>
-__device__ T dist2_derivs(const double *Xd, const Feature &f, double b0, double b1, T *gs, T *Hs) {
-    T w[4], r[3], D[2][3];
-    {
-        double wd[4], rd[3] = {0, 0, 0}, Dd[2][3] = {{0, 0, 0}, {0, 0, 0}};
-#pragma unroll
-        for (int v = 0; v < 4; ++v) wd[v] = f.w0[v] + b0 * f.c[0][v] + b1 * f.c[1][v];
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                rd[a] += wd[v] * Xd[3 * v + a];
-                Dd[0][a] += f.c[0][v] * Xd[3 * v + a];
-                Dd[1][a] += f.c[1][v] * Xd[3 * v + a];
-            }
-#pragma unroll
-        for (int v = 0; v < 4; ++v) w[v] = T(wd[v]);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            r[a] = T(rd[a]);
-            D[0][a] = T(Dd[0][a]);
-            D[1][a] = T(Dd[1][a]);
-        }
-    }
-#pragma unroll
-    for (int v = 0; v < 4; ++v)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) gs[3 * v + a] = T(2) * w[v] * r[a];
-#pragma unroll
-    for (int v = 0; v < 4; ++v)
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = 0; b < 3; ++b) Hs[(3 * v + a) * 12 + 3 * u + b] = a == b ? T(2) * w[v] * w[u] : T(0);
-    if (f.k > 0) {
-        T G00 = dot3(D[0], D[0]), G01 = dot3(D[0], D[1]), G11 = dot3(D[1], D[1]);
-        T i00, i01, i11;
-        if (f.k == 1) { i00 = T(1) / G00; i01 = T(0); i11 = T(0); }
-        else {
-            T det = G00 * G11 - G01 * G01;
-            i00 = G11 / det; i11 = G00 / det; i01 = -G01 / det;
-        }
-        T g0[12], g1[12];
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                g0[3 * v + a] = w[v] * D[0][a] + T(f.c[0][v]) * r[a];
-                g1[3 * v + a] = w[v] * D[1][a] + T(f.c[1][v]) * r[a];
-            }
-#pragma unroll
-        for (int m = 0; m < 12; ++m)
-#pragma unroll
-            for (int n = 0; n < 12; ++n)
-                Hs[m * 12 + n] -= T(2) * (i00 * g0[m] * g0[n] + i01 * (g0[m] * g1[n] + g1[m] * g0[n]) + i11 * g1[m] * g1[n]);
-    }
-    return dot3(r, r);
-}
-
 // IPC log barrier on the unsquared distance: b = -(d - dhat)^2 ln(d / dhat) on (0, dhat).
 template <class T>
 __device__ __forceinline__ void barrier3(T d, T dhat, T &b, T &b1, T &b2) {
@@ -229,69 +161,6 @@ __device__ __forceinline__ void barrier3(T d, T dhat, T &b, T &b1, T &b2) {
     b = -e * e * L;
     b1 = T(-2) * e * L - e * eid;
     b2 = T(-2) * L - T(4) * eid + eid * eid;
-}
-
-// Edge-edge mollifier m(c), c = |(a1 - a0) x (b1 - b0)|^2, eps_x from rest lengths:
-// m = (c/eps)(2 - c/eps) below eps, else 1.  Returns m and, when c < eps,
-// m' grad c (gm) and m'' grad c grad c^T + m' hess c (Hm).  The edge vectors
-// and their cross product (short for nearly parallel edges) are formed from
-// the FP64 coordinates Xd and rounded to T once formed.
-template <class T>
-__device__ T mollifier(const double *Xd, T eps, T *gm, T *Hm, bool &active) {
-    T ea[3], eb[3], cr[3], c;
-    {
-        double ead[3] = {Xd[3] - Xd[0], Xd[4] - Xd[1], Xd[5] - Xd[2]};
-        double ebd[3] = {Xd[9] - Xd[6], Xd[10] - Xd[7], Xd[11] - Xd[8]};
-        double crd[3] = {ead[1] * ebd[2] - ead[2] * ebd[1], ead[2] * ebd[0] - ead[0] * ebd[2],
-                         ead[0] * ebd[1] - ead[1] * ebd[0]};
-        for (int k = 0; k < 3; ++k) {
-            ea[k] = T(ead[k]);
-            eb[k] = T(ebd[k]);
-            cr[k] = T(crd[k]);
-        }
-        c = T(crd[0] * crd[0] + crd[1] * crd[1] + crd[2] * crd[2]);
-    }
-    active = c < eps;
-    if (!active) return T(1);
-    T rr = c / eps, m = rr * (T(2) - rr), m1 = (T(2) - T(2) * rr) / eps, m2 = T(-2) / (eps * eps);
-    T ge[6], t[3];
-    cross3(t, eb, cr);
-    ge[0] = T(2) * t[0]; ge[1] = T(2) * t[1]; ge[2] = T(2) * t[2];
-    cross3(t, cr, ea);
-    ge[3] = T(2) * t[0]; ge[4] = T(2) * t[1]; ge[5] = T(2) * t[2];
-    // J = [d cr/d ea, d cr/d eb] = [-[eb]x, [ea]x]
-    T J[3][6] = {{0, eb[2], -eb[1], 0, -ea[2], ea[1]},
-                 {-eb[2], 0, eb[0], ea[2], 0, -ea[0]},
-                 {eb[1], -eb[0], 0, -ea[1], ea[0], 0}};
-    T crx[3][3] = {{0, -cr[2], cr[1]}, {cr[2], 0, -cr[0]}, {-cr[1], cr[0], 0}};
-    T He[6][6];
-#pragma unroll
-    for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int b = 0; b < 6; ++b) He[a][b] = T(2) * (J[0][a] * J[0][b] + J[1][a] * J[1][b] + J[2][a] * J[2][b]);
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) { He[j][3 + k] -= T(2) * crx[j][k]; He[3 + j][k] += T(2) * crx[j][k]; }
-    const T sg[4] = {T(-1), T(1), T(-1), T(1)};
-    T gc[12];
-#pragma unroll
-    for (int v = 0; v < 4; ++v)
-#pragma unroll
-        for (int a = 0; a < 3; ++a) gc[3 * v + a] = sg[v] * ge[3 * (v >> 1) + a];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) gm[i] = m1 * gc[i];
-#pragma unroll
-    for (int v = 0; v < 4; ++v)
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = 0; b < 3; ++b)
-                    Hm[(3 * v + a) * 12 + 3 * u + b] =
-                        m2 * gc[3 * v + a] * gc[3 * u + b] + m1 * sg[v] * sg[u] * He[3 * (v >> 1) + a][3 * (u >> 1) + b];
-    return m;
 }
 
 // Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix in place;
@@ -357,6 +226,24 @@ __device__ void psd_project(T *H) {
         }
 }
 
+// |ea x eb|^2 of an edge-edge pair in pair-local coordinates (edge a = X0 X1,
+// edge b = X2 X3), the quantity whose comparison with eps_x switches the
+// mollifier on.  Every operation is rounded on its own (no contraction into
+// fused multiply-adds), so the kernels that split the pairs by this test
+// (mollified or not) and the kernel that evaluates them take the same
+// decision for every pair.
+__device__ __forceinline__ double ee_cross2(const double *X) {
+    double a[3], b[3];
+    for (int k = 0; k < 3; ++k) {
+        a[k] = __dsub_rn(X[3 + k], X[k]);
+        b[k] = __dsub_rn(X[9 + k], X[6 + k]);
+    }
+    double c0 = __dsub_rn(__dmul_rn(a[1], b[2]), __dmul_rn(a[2], b[1]));
+    double c1 = __dsub_rn(__dmul_rn(a[2], b[0]), __dmul_rn(a[0], b[2]));
+    double c2 = __dsub_rn(__dmul_rn(a[0], b[1]), __dmul_rn(a[1], b[0]));
+    return __dadd_rn(__dadd_rn(__dmul_rn(c0, c0), __dmul_rn(c1, c1)), __dmul_rn(c2, c2));
+}
+
 // FP64 gradient of one PT/EE pair's barrier energy kB * [m(c)] * b(d) in
 // pair-local coordinates X.  Returns d; fills the feature (type, beta) and the
 // scalars the Hessian needs.  When d >= dhat or d <= 0 nothing else is written.
@@ -391,7 +278,7 @@ __device__ inline double pair_gradient(bool ee, const double *X, double dhat, do
         double eb[3] = {X[9] - X[6], X[10] - X[7], X[11] - X[8]};
         double cr[3], t[3];
         cross3(cr, ea, eb);
-        double c = dot3(cr, cr);
+        double c = ee_cross2(X);
         if (c < eps_x) {
             double rr = c / eps_x;
             P.m = rr * (2.0 - rr);
@@ -409,41 +296,6 @@ __device__ inline double pair_gradient(bool ee, const double *X, double dhat, do
     }
     for (int i = 0; i < 12; ++i) g[i] *= kB;
     return d;
-}
-
-// Raw (unprojected) Hessian of the same pair in precision T, from the FP64
-// feature and barrier scalars of pair_gradient.
-template <class T>
-__device__ void pair_hessian(bool ee, const double *Xd, const PairGrad &P, T d, T kB, T eps_x, T *H) {
-    Feature f = feature_of(ee, P.type);
-    T gs[12];
-    dist2_derivs<T>(Xd, f, P.b0, P.b1, gs, H);  // H <- hess s
-    T inv2d = T(1) / (T(2) * d);
-    T gd[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) gd[i] = gs[i] * inv2d;
-    // hess b = (b'' - b'/d) gd gd^T + (b'/2d) hess s
-    T bp = T(P.bp), cg = T(P.bpp) - bp / d, ch = bp * inv2d;
-#pragma unroll
-    for (int i = 0; i < 12; ++i)
-#pragma unroll
-        for (int j = 0; j < 12; ++j) H[i * 12 + j] = cg * gd[i] * gd[j] + ch * H[i * 12 + j];
-    if (ee && P.moll) {
-        T gb[12];
-#pragma unroll
-        for (int i = 0; i < 12; ++i) gb[i] = bp * gd[i];
-        T gm[12], Hm[144];
-        bool act;
-        T m = mollifier<T>(Xd, eps_x, gm, Hm, act);
-        T b = T(P.b);
-#pragma unroll
-        for (int i = 0; i < 12; ++i)
-#pragma unroll
-            for (int j = 0; j < 12; ++j)
-                H[i * 12 + j] = Hm[i * 12 + j] * b + gm[i] * gb[j] + gb[i] * gm[j] + m * H[i * 12 + j];
-    }
-#pragma unroll
-    for (int i = 0; i < 144; ++i) H[i] *= kB;
 }
 
 // Cyclic Jacobi + clamp for a symmetric n x n matrix, n <= 5, in registers

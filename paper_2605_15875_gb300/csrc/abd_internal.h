@@ -99,7 +99,7 @@ struct World {
     DBuf ctr;    // counters
     DBuf aabb;   // body AABBs at the step start
     DBuf part_off;  // [NP + 1] dynamic-slot range of each partition
-    DBuf deferred;  // active pairs left to the full 12x12 projection
+    DBuf nmoll;     // [1] mollified edge-edge pairs assembled in the last assembly
     DBuf rowcnt, rowoff, rowcur, ent;  // row CSR of the off-diagonal blocks
     DBuf slot_cbase;   // [S_all + 1] first cluster of each slot
     DBuf cl_info;      // [C] (slot, kind << 24 | cluster index)
@@ -185,6 +185,11 @@ struct PcgTune {
 struct abd_scene {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;  // second branch of an iteration's independent kernels
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // no side branch: the serving runtime's scenes, whose workers' streams
+    // already keep the GPU busy side by side (forks there only add joins)
+    bool no_side = false;
     std::string err;
     // host copy of constants
     int nb = 0;
@@ -265,13 +270,26 @@ int launch_pcg_async(abd_scene *s, int precision, const abd_step_params *p);
 // ---- (abd_solve.cu) ----
 
 // profiling helpers (abd_scene.cu)
-void prof_begin(abd_scene *s, const char *name, double bytes, cudaEvent_t *a, cudaEvent_t *b);
-void prof_end(abd_scene *s, cudaEvent_t a, cudaEvent_t b, int idx);
+// The events go on stream `st` (nullptr: the scene's stream).
+void prof_begin(abd_scene *s, const char *name, double bytes, cudaEvent_t *a, cudaEvent_t *b,
+                cudaStream_t st = nullptr);
+void prof_end(abd_scene *s, cudaEvent_t a, cudaEvent_t b, int idx, cudaStream_t st = nullptr);
 void prof_flush(abd_scene *s);
 void prof_add_bytes(abd_scene *s, const char *name, double bytes);
 int prof_index(abd_scene *s, const char *name);
 void prof_graph_replayed(abd_scene *s);
 bool stream_capturing(abd_scene *s);
+// Two independent branches of an iteration: fork_side returns the scene's
+// side stream, made to wait for everything enqueued on the scene's stream so
+// far (or the scene's stream itself when there is no side stream, e.g. on the
+// legacy default stream); join_side makes the scene's stream wait for what
+// was enqueued on the branch.  Works the same under graph capture, where the
+// branch becomes a parallel path of the graph.  ensure_side creates the side
+// stream and its events (outside any capture).
+void ensure_side(abd_scene *s);
+void scene_no_side(abd_scene *s);  // never fork this scene's iterations
+cudaStream_t fork_side(abd_scene *s);
+void join_side(abd_scene *s, cudaStream_t side);
 // After the status read of a Newton iteration: account the timed PCG launch
 // of the cluster-size autotuner (iterations = largest partition's count).
 void pcg_tune_observe(abd_scene *s, int64_t iterations);

@@ -64,9 +64,10 @@ bool stream_capturing(abd_scene *s) {
 // While the stream is being captured into the iteration graph, the events
 // become graph nodes (external records) and the pair is kept with the graph;
 // its bytes are added on every replay (prof_graph_replayed).
-void prof_begin(abd_scene *s, const char *name, double bytes, cudaEvent_t *a, cudaEvent_t *b) {
+void prof_begin(abd_scene *s, const char *name, double bytes, cudaEvent_t *a, cudaEvent_t *b, cudaStream_t st) {
     *a = *b = nullptr;
     if (!s->prof) return;
+    if (!st) st = s->stream;
     for (int k = 0; k < 2; ++k) {
         cudaEvent_t e;
         if (!s->ev_pool.empty()) {
@@ -80,25 +81,54 @@ void prof_begin(abd_scene *s, const char *name, double bytes, cudaEvent_t *a, cu
     int idx = prof_index(s, name);
     if (stream_capturing(s)) {
         s->ig.ev.push_back({idx, bytes, *a, *b});
-        cudaEventRecordWithFlags(*a, s->stream, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(*a, st, cudaEventRecordExternal);
         return;
     }
     s->kstats[idx].bytes += bytes;
-    cudaEventRecord(*a, s->stream);
+    cudaEventRecord(*a, st);
 }
 
 void prof_add_bytes(abd_scene *s, const char *name, double bytes) {
     if (s->prof) s->kstats[prof_index(s, name)].bytes += bytes;
 }
 
-void prof_end(abd_scene *s, cudaEvent_t a, cudaEvent_t b, int idx) {
+void prof_end(abd_scene *s, cudaEvent_t a, cudaEvent_t b, int idx, cudaStream_t st) {
     if (!a || !b) return;
+    if (!st) st = s->stream;
     if (stream_capturing(s)) {
-        cudaEventRecordWithFlags(b, s->stream, cudaEventRecordExternal);
+        cudaEventRecordWithFlags(b, st, cudaEventRecordExternal);
         return;
     }
-    cudaEventRecord(b, s->stream);
+    cudaEventRecord(b, st);
     s->ev_pending.push_back({idx, {a, b}});
+}
+
+void ensure_side(abd_scene *s) {
+    if (s->side || !s->stream || s->no_side) return;
+    if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) == cudaSuccess)
+        return;
+    cudaGetLastError();  // no side stream: both branches run on the scene's stream
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->side) cudaStreamDestroy(s->side);
+    s->side = nullptr;
+    s->ev_fork = s->ev_join = nullptr;
+}
+
+void scene_no_side(abd_scene *s) { s->no_side = true; }
+
+cudaStream_t fork_side(abd_scene *s) {
+    if (!s->side || !s->ev_join) return s->stream;
+    cudaEventRecord(s->ev_fork, s->stream);
+    cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+    return s->side;
+}
+
+void join_side(abd_scene *s, cudaStream_t side) {
+    if (side == s->stream) return;
+    cudaEventRecord(s->ev_join, side);
+    cudaStreamWaitEvent(s->stream, s->ev_join, 0);
 }
 
 // After a replay of the iteration graph has completed: accumulate its event
@@ -402,7 +432,11 @@ extern "C" int abd_scene_create(const abd_scene_desc *d, void *stream, abd_scene
 extern "C" void abd_scene_destroy(abd_scene *s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
+    if (s->side) cudaStreamSynchronize(s->side);
     if (s->ig.exec) cudaGraphExecDestroy(s->ig.exec);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
+    if (s->side) cudaStreamDestroy(s->side);
     prof_graph_release(s);
     for (auto &t : s->pcg_tune) {
         if (t.a) cudaEventDestroy(t.a);
@@ -417,7 +451,7 @@ extern "C" void abd_scene_destroy(abd_scene *s) {
                   &w.q, &w.qprev, &w.qtil, &w.z, &w.u, &w.rho, &w.dq, &w.g, &w.x, &w.x1, &w.dx, &w.box, &w.box1,
                   &w.rep_off, &w.rep_slot, &w.zb, &w.rho0, &w.rhob, &w.rb, &w.sb, &w.body_rep, &w.body_slot,
                   &w.l1, &w.cand, &w.act, &w.ls, &w.diag, &w.off, &w.offflag,
-                  &w.pcg_sc, &w.part, &w.ctr, &w.aabb, &w.part_off, &w.deferred, &w.rowcnt, &w.rowoff, &w.rowcur, &w.ent, &w.slot_cbase, &w.cl_info, &w.cbox, &w.cbox1, &w.cp, &w.xb, &w.xb1};
+                  &w.pcg_sc, &w.part, &w.ctr, &w.aabb, &w.part_off, &w.nmoll, &w.rowcnt, &w.rowoff, &w.rowcur, &w.ent, &w.slot_cbase, &w.cl_info, &w.cbox, &w.cbox1, &w.cp, &w.xb, &w.xb1};
     for (DBuf *b : wb) dbuf_free(*b);
     if (s->pinned) cudaFreeHost(s->pinned);
     for (auto &pe : s->ev_pending) {

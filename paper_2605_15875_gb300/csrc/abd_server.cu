@@ -30,6 +30,12 @@
 
 #include "../../include/abd.h"
 
+namespace abd {
+// abd_scene.cu: run the scene's iterations on its own stream only (no side
+// branch for independent kernels)
+void scene_no_side(abd_scene *s);
+}  // namespace abd
+
 namespace {
 
 double now_ms() {
@@ -317,6 +323,8 @@ struct abd_server {
         if (rc < 0) {
             inf.status = rc;
             r->err = "scene create failed";
+        } else {
+            abd::scene_no_side(sc);  // the workers' streams already run side by side
         }
         if (rc >= 0 && r->scene.has_part) {
             rc = abd_partition(sc, &r->scene.p);
@@ -345,6 +353,8 @@ struct abd_server {
             if (rc < 0) {
                 res->sc = nullptr;
                 r->err = "scene create failed";
+            } else {
+                abd::scene_no_side(res->sc);
             }
             if (rc >= 0 && res->scene.has_part && (rc = abd_partition(res->sc, &res->scene.p)) < 0)
                 r->err = abd_last_error(res->sc);

@@ -532,8 +532,7 @@ int enqueue_status(abd_scene *s, Status *h) {
     cudaMemcpyAsync(h->part, w.part.p, sizeof(PartState) * w.NP, cudaMemcpyDeviceToHost, s->stream);
     if (s->prof && w.S_dyn > 0) {
         cudaMemcpyAsync(&h->csr_total, P<int>(w.rowoff) + w.S_dyn, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
-        cudaMemcpyAsync(&h->n_moll, P<int64_t>(w.deferred) + w.cap_act, sizeof(unsigned long long),
-                        cudaMemcpyDeviceToHost, s->stream);
+        cudaMemcpyAsync(&h->n_moll, w.nmoll.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream);
     }
     return cuda_check(s, cudaGetLastError(), "status");
 }
@@ -554,7 +553,7 @@ int ensure_lists(Ctx &C) {
               dbuf_ensure(w.act, sizeof(PairRec) * (size_t)w.cap_act) &&
               dbuf_ensure(w.ls, sizeof(PairRec) * (size_t)w.cap_ls) && dbuf_ensure(w.cp, sizeof(int4) * (size_t)w.cap_cp) &&
               dbuf_ensure(w.off, tb * 144 * (size_t)w.cap_l1) && dbuf_ensure(w.offflag, 4 * (size_t)w.cap_l1) &&
-              dbuf_ensure(w.deferred, 8 * (size_t)w.cap_act + 64) &&
+              dbuf_ensure(w.nmoll, 64) &&
               dbuf_ensure(w.rowcnt, 4 * (size_t)(w.S_dyn + 2)) && dbuf_ensure(w.rowoff, 4 * (size_t)(w.S_dyn + 2)) &&
               dbuf_ensure(w.rowcur, 4 * (size_t)(w.S_dyn + 2)) && dbuf_ensure(w.ent, 16 * (size_t)w.cap_l1) &&
               dbuf_ensure(w.diag, tb * 144 * (size_t)(w.S_dyn ? w.S_dyn : 1)) &&
@@ -692,6 +691,7 @@ int newton_solve(Ctx &C, const std::vector<int> &run, int &newton_total, int &ma
     const abd_step_params *p = C.p;
     int rc = ensure_lists(C);
     if (rc) return rc;
+    ensure_side(s);
     Status *hs = pinned_status(s);
     if (!hs) return set_err(s, ABD_E_OOM, "pinned status");
     std::vector<PartState> ps(w.NP);

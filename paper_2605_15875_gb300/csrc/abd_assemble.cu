@@ -493,33 +493,19 @@ __device__ __forceinline__ void moll_entries(const MollTerms<T> &M, T *H, int la
     }
 }
 
-// Mollified edge-edge pairs (ee_cross2 < eps_x, the pairs k_pair_assemble
-// skips), one warp per pair; it runs beside k_pair_assemble.  The warps find
-// their pairs themselves: lane l of warp w tests active pair w + l * nw (nw
-// warps in the grid, then the next 32 * nw), so neighbouring pairs of the
-// list, which tend to be mollified together, go to different warps.  For
-// each pair found, lane 0 evaluates the FP64 gradient and the per-pair terms
-// of the raw 12x12 Hessian (T), the lanes write its entries, the warp projects
-// it to PSD and scatters J^T H J and the gradient onto the slots.  n_moll
-// counts the pairs assembled.
-template <class T>
-__global__ void __launch_bounds__(128) k_pair_moll(AsmArgs A, const PairRec *__restrict__ act,
-                                                   const unsigned long long *__restrict__ n_dev, int64_t cap,
-                                                   const int2 *__restrict__ l1, T *__restrict__ diag,
-                                                   T *__restrict__ off, int *__restrict__ offflag,
-                                                   unsigned long long *__restrict__ n_moll) {
-    __shared__ T sH[4][144], sW[4][144], sV[4][144], sR[4][12];
-    __shared__ double sg[4][12], sw[4];
-    __shared__ T sxi[4][4][4];
-    __shared__ int ssl[4][4], sok[4];
-    __shared__ MollTerms<T> smt[4];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t n = min((int64_t)*n_dev, cap), nw = (int64_t)gridDim.x * 4;
-    for (int64_t base = (int64_t)blockIdx.x + (int64_t)gridDim.x * wib; base < n; base += 32 * nw) {
-        const int64_t mine = base + lane * nw;
+// The mollified edge-edge pairs of the active list (ee_cross2 < eps_x: the
+// pairs k_pair_assemble skips, in partitions still iterating), compacted into
+// mlist[0 .. *mcount) so that k_pair_moll can give every one its own warp.
+__global__ void k_moll_scan(AsmArgs A, const PairRec *__restrict__ act, const unsigned long long *__restrict__ n_dev,
+                            int64_t cap, int64_t *__restrict__ mlist, unsigned long long *__restrict__ mcount) {
+    const int64_t n = min((int64_t)*n_dev, cap);
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + lane;
         bool found = false;
-        if (mine < n) {
-            const PairRec r = act[mine];
+        if (i < n) {
+            const PairRec r = act[i];
             if (r.flags & 1) {
                 int sa, sb;
                 pair_slots(r, A.sv_slot, sa, sb);
@@ -532,88 +518,114 @@ __global__ void __launch_bounds__(128) k_pair_moll(AsmArgs A, const PairRec *__r
                 }
             }
         }
-        unsigned M = __ballot_sync(0xffffffffu, found);
-        while (M) {
-            const int src = __ffs(M) - 1;
-            M &= M - 1;
-            const PairRec r = act[__shfl_sync(0xffffffffu, mine, src)];
-            if (lane == 0) {
-                int sa, sb;
-                pair_slots(r, A.sv_slot, sa, sb);
-                bool ee = r.flags & 1;
-                double Xd[12];
-                for (int v = 0; v < 4; ++v)
-                    for (int k = 0; k < 3; ++k) Xd[3 * v + k] = A.x[3 * (int64_t)r.v[v] + k] - A.x[3 * (int64_t)r.v[0] + k];
-                PairGrad PG;
-                const double kB = A.part[pair_part(sa, sb, A.S_dyn, A.slot_part)].kB;
-                double d = pair_gradient(ee, Xd, A.dhat, kB, r.eps, PG, sg[wib]);
-                sok[wib] = (d < A.dhat) && (d > 0.0);
-                if (sok[wib]) {
-                    atomicAdd(n_moll, 1ull);
-                    moll_terms<T>(Xd, PG, d, kB, T(r.eps), smt[wib]);
-                    sw[wib] = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
-                    for (int v = 0; v < 4; ++v) {
-                        int s = A.sv_slot[r.v[v]];
-                        ssl[wib][v] = s < A.S_dyn ? s : -1;
-                        int b = A.slot_body[s];
-                        const double *xb = A.xbar + 3 * ((int64_t)A.voff[b] + (r.v[v] - A.slot_voff[s]));
-                        sxi[wib][v][0] = T(1); sxi[wib][v][1] = T(xb[0]); sxi[wib][v][2] = T(xb[1]); sxi[wib][v][3] = T(xb[2]);
-                    }
+        const unsigned M = __ballot_sync(0xffffffffu, found);
+        if (!M) continue;
+        const int leader = __ffs(M) - 1;
+        unsigned long long pos = 0;
+        if (lane == leader) pos = atomicAdd(mcount, (unsigned long long)__popc(M));
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        if (found) mlist[pos + __popc(M & ((1u << lane) - 1))] = i;
+    }
+}
+
+// The mollified edge-edge pairs listed by k_moll_scan, one warp per pair
+// (warps dealt over SMs, then SM sub-partitions, as in spread_base); it runs
+// beside k_pair_assemble.  For each pair, lane 0 evaluates the FP64 gradient
+// and the per-pair terms of the raw 12x12 Hessian (T), the lanes write its
+// entries, the warp projects it to PSD and scatters J^T H J and the gradient
+// onto the slots.  n_moll counts the pairs assembled.
+template <class T>
+__global__ void __launch_bounds__(128) k_pair_moll(AsmArgs A, const PairRec *__restrict__ act,
+                                                   const int64_t *__restrict__ mlist,
+                                                   const unsigned long long *__restrict__ mcount, int64_t cap,
+                                                   const int2 *__restrict__ l1, T *__restrict__ diag,
+                                                   T *__restrict__ off, int *__restrict__ offflag,
+                                                   unsigned long long *__restrict__ n_moll) {
+    __shared__ T sH[4][144], sW[4][144], sV[4][144], sR[4][12];
+    __shared__ double sg[4][12], sw[4];
+    __shared__ T sxi[4][4][4];
+    __shared__ int ssl[4][4], sok[4];
+    __shared__ MollTerms<T> smt[4];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t n = min((int64_t)*mcount, cap), nw = (int64_t)gridDim.x * 4;
+    for (int64_t t = spread_slot(); t < n; t += nw) {
+        const PairRec r = act[mlist[t]];
+        if (lane == 0) {
+            int sa, sb;
+            pair_slots(r, A.sv_slot, sa, sb);
+            bool ee = r.flags & 1;
+            double Xd[12];
+            for (int v = 0; v < 4; ++v)
+                for (int k = 0; k < 3; ++k) Xd[3 * v + k] = A.x[3 * (int64_t)r.v[v] + k] - A.x[3 * (int64_t)r.v[0] + k];
+            PairGrad PG;
+            const double kB = A.part[pair_part(sa, sb, A.S_dyn, A.slot_part)].kB;
+            double d = pair_gradient(ee, Xd, A.dhat, kB, r.eps, PG, sg[wib]);
+            sok[wib] = (d < A.dhat) && (d > 0.0);
+            if (sok[wib]) {
+                atomicAdd(n_moll, 1ull);
+                moll_terms<T>(Xd, PG, d, kB, T(r.eps), smt[wib]);
+                sw[wib] = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
+                for (int v = 0; v < 4; ++v) {
+                    int s = A.sv_slot[r.v[v]];
+                    ssl[wib][v] = s < A.S_dyn ? s : -1;
+                    int b = A.slot_body[s];
+                    const double *xb = A.xbar + 3 * ((int64_t)A.voff[b] + (r.v[v] - A.slot_voff[s]));
+                    sxi[wib][v][0] = T(1); sxi[wib][v][1] = T(xb[0]); sxi[wib][v][2] = T(xb[1]); sxi[wib][v][3] = T(xb[2]);
                 }
             }
-            __syncwarp();
-            const bool ok = sok[wib];
-            __syncwarp();
-            if (!ok) continue;
-            moll_entries<T>(smt[wib], sH[wib], lane);
-            __syncwarp();
-            warp_psd12<T>(sH[wib], sW[wib], sV[wib], sR[wib], lane);
-            const double w = sw[wib];
-            const int *sl = ssl[wib];
-            // gradient: 4 vertices x 3 components x 4 xi entries
-            for (int e = lane; e < 48; e += 32) {
-                int v = e / 12, k = (e / 4) % 3, a = e % 4;
-                if (sl[v] < 0) continue;
-                double xa = a == 0 ? 1.0 : (double)sxi[wib][v][a];
-                atomicAdd(A.g + 12 * (int64_t)sl[v] + qidx(k, a), w * sg[wib][3 * v + k] * xa);
-            }
-            int sa = sl[0] >= 0 ? sl[0] : -1;
-            int sb = sl[(r.flags & 1) ? 2 : 1];
-            int ss[2] = {sa, sb};
-            for (int bi = 0; bi < 2; ++bi)
-                for (int bj = bi; bj < 2; ++bj) {
-                    int s1 = ss[bi], s2 = ss[bj];
-                    if (s1 < 0 || s2 < 0 || (bi != bj && s1 == s2)) continue;
-                    T *dst;
-                    bool tr = false;
-                    if (bi == bj) dst = diag + 144 * (int64_t)s1;
-                    else {
-                        int2 lp = l1[r.l1];
-                        dst = off + 144 * (int64_t)r.l1;
-                        tr = (lp.x != s1);
-                        if (lane == 0 && atomicExch(&offflag[r.l1], 1) == 0) {
-                            atomicAdd(&A.rowcnt[lp.x], 1);
-                            atomicAdd(&A.rowcnt[lp.y], 1);
-                        }
-                    }
-                    for (int e = lane; e < 144; e += 32) {
-                        int row = e / 12, col = e % 12;
-                        int k = row < 3 ? row : (row - 3) / 3, a = row < 3 ? 0 : 1 + (row - 3) % 3;
-                        int l = col < 3 ? col : (col - 3) / 3, c = col < 3 ? 0 : 1 + (col - 3) % 3;
-                        T acc = T(0);
-                        for (int v = 0; v < 4; ++v) {
-                            if (sl[v] != s1) continue;
-                            for (int u = 0; u < 4; ++u) {
-                                if (sl[u] != s2) continue;
-                                acc += sH[wib][(3 * v + k) * 12 + 3 * u + l] * sxi[wib][v][a] * sxi[wib][u][c];
-                            }
-                        }
-                        T val = T(w) * acc;
-                        if (val != T(0)) atomic_addT(dst + (tr ? col * 12 + row : row * 12 + col), val);
-                    }
-                }
-            __syncwarp();
         }
+        __syncwarp();
+        const bool ok = sok[wib];
+        __syncwarp();
+        if (!ok) continue;
+        moll_entries<T>(smt[wib], sH[wib], lane);
+        __syncwarp();
+        warp_psd12<T>(sH[wib], sW[wib], sV[wib], sR[wib], lane);
+        const double w = sw[wib];
+        const int *sl = ssl[wib];
+        // gradient: 4 vertices x 3 components x 4 xi entries
+        for (int e = lane; e < 48; e += 32) {
+            int v = e / 12, k = (e / 4) % 3, a = e % 4;
+            if (sl[v] < 0) continue;
+            double xa = a == 0 ? 1.0 : (double)sxi[wib][v][a];
+            atomicAdd(A.g + 12 * (int64_t)sl[v] + qidx(k, a), w * sg[wib][3 * v + k] * xa);
+        }
+        int sa = sl[0] >= 0 ? sl[0] : -1;
+        int sb = sl[(r.flags & 1) ? 2 : 1];
+        int ss[2] = {sa, sb};
+        for (int bi = 0; bi < 2; ++bi)
+            for (int bj = bi; bj < 2; ++bj) {
+                int s1 = ss[bi], s2 = ss[bj];
+                if (s1 < 0 || s2 < 0 || (bi != bj && s1 == s2)) continue;
+                T *dst;
+                bool tr = false;
+                if (bi == bj) dst = diag + 144 * (int64_t)s1;
+                else {
+                    int2 lp = l1[r.l1];
+                    dst = off + 144 * (int64_t)r.l1;
+                    tr = (lp.x != s1);
+                    if (lane == 0 && atomicExch(&offflag[r.l1], 1) == 0) {
+                        atomicAdd(&A.rowcnt[lp.x], 1);
+                        atomicAdd(&A.rowcnt[lp.y], 1);
+                    }
+                }
+                for (int e = lane; e < 144; e += 32) {
+                    int row = e / 12, col = e % 12;
+                    int k = row < 3 ? row : (row - 3) / 3, a = row < 3 ? 0 : 1 + (row - 3) % 3;
+                    int l = col < 3 ? col : (col - 3) / 3, c = col < 3 ? 0 : 1 + (col - 3) % 3;
+                    T acc = T(0);
+                    for (int v = 0; v < 4; ++v) {
+                        if (sl[v] != s1) continue;
+                        for (int u = 0; u < 4; ++u) {
+                            if (sl[u] != s2) continue;
+                            acc += sH[wib][(3 * v + k) * 12 + 3 * u + l] * sxi[wib][v][a] * sxi[wib][u][c];
+                        }
+                    }
+                    T val = T(w) * acc;
+                    if (val != T(0)) atomic_addT(dst + (tr ? col * 12 + row : row * 12 + col), val);
+                }
+            }
+        __syncwarp();
     }
 }
 
@@ -953,16 +965,20 @@ static int assemble_async_T(abd_scene *s, const abd_step_params *p) {
         ABD_LAUNCH(s, k_slot_assemble<T>, grid_for(w.S_dyn, 32, 152 * 8), 128, 0, s->stream, A, P<T>(w.diag));
         prof_end(s, ea, eb, prof_index(s, "slot_assemble"));
     }
+    // w.nmoll: [0] pairs assembled, [1] pairs listed, the list from byte 64
     unsigned long long *nmoll = P<unsigned long long>(w.nmoll);
-    cudaMemsetAsync(nmoll, 0, 8, s->stream);
+    int64_t *mlist = (int64_t *)((char *)w.nmoll.p + 64);
+    cudaMemsetAsync(nmoll, 0, 16, s->stream);
     // the mollified pairs (one warp each, the longest chain) on the side
     // branch, beside the other pairs and the vertex-plane terms; both only
     // add onto what k_slot_assemble stored
     cudaStream_t side = fork_side(s);
     cudaEvent_t ma, mb;
     prof_begin(s, "pair_moll", 0.0, &ma, &mb, side);
-    ABD_LAUNCH(s, k_pair_moll<T>, 152 * 2, 128, 0, side, A, P<PairRec>(w.act), &c->act, w.cap_act, P<int2>(w.l1),
-               P<T>(w.diag), P<T>(w.off), P<int>(w.offflag), nmoll);
+    ABD_LAUNCH(s, k_moll_scan, grid_for(w.cap_act, 256, 152 * 8), 256, 0, side, A, P<PairRec>(w.act), &c->act,
+               w.cap_act, mlist, nmoll + 1);
+    ABD_LAUNCH(s, k_pair_moll<T>, 152 * 4, 128, 0, side, A, P<PairRec>(w.act), mlist, nmoll + 1, w.cap_act,
+               P<int2>(w.l1), P<T>(w.diag), P<T>(w.off), P<int>(w.offflag), nmoll);
     prof_end(s, ma, mb, prof_index(s, "pair_moll"), side);
     prof_begin(s, "pair_assemble", 0.0, &ea, &eb);
     ABD_LAUNCH(s, k_pair_assemble<T>, grid_for(w.cap_act, 128, 152 * 8), 128, 0, s->stream, A,

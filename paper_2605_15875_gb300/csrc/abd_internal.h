@@ -99,7 +99,7 @@ struct World {
     DBuf ctr;    // counters
     DBuf aabb;   // body AABBs at the step start
     DBuf part_off;  // [NP + 1] dynamic-slot range of each partition
-    DBuf nmoll;     // [1] mollified edge-edge pairs assembled in the last assembly
+    DBuf nmoll;     // mollified edge-edge pairs: counts (assembled, listed), then their list
     DBuf rowcnt, rowoff, rowcur, ent;  // row CSR of the off-diagonal blocks
     DBuf slot_cbase;   // [S_all + 1] first cluster of each slot
     DBuf cl_info;      // [C] (slot, kind << 24 | cluster index)
@@ -306,16 +306,26 @@ int cuda_check(abd_scene *s, cudaError_t e, const char *what);
         ++(S)->n_launches;                       \
     } while (0)
 
-// First item of this thread's warp in a "spread" grid-stride loop: warps are
-// dealt to blocks first (warp w of block b takes warp slot b + gridDim.x * w),
-// so a short list puts one warp on each of many SMs instead of filling a few
-// (FP64 work in particular is limited by each SM's FP64 pipe).  Loop as
+// First item of this thread's warp in a "spread" grid-stride loop: the warp
+// slots are dealt out so that a short list puts one warp on each of many SMs
+// (blocks 152 k .. 152 k + 151 are taken to sit on distinct SMs), then one on
+// each further SM sub-partition of those SMs (warp w of a block runs on
+// sub-partition w mod 4), before any sub-partition gets a second warp.  FP64
+// work in particular is limited by each sub-partition's FP64 pipe, which takes
+// a warp instruction at a time however few of its lanes are active.  Slot of
+// warp w of block b (G blocks of W warps, F = 152 floor(G / 152)):
+//   b < F:  152 W floor(b / 152) + 152 w + b mod 152;   else  F W + (G - F) w + b - F,
+// a bijection onto [0, G W).  Loop as
 //   for (int64_t wb = spread_base(); wb < n; wb += gridDim.x * blockDim.x)
 // with item wb + lane; the trip count is warp-uniform.
 #ifdef __CUDACC__
-__device__ __forceinline__ int64_t spread_base() {
-    return ((int64_t)blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5)) * 32;
+__device__ __forceinline__ int64_t spread_slot() {
+    constexpr int64_t kSM = 152;
+    const int64_t G = gridDim.x, W = blockDim.x >> 5, b = blockIdx.x, w = threadIdx.x >> 5;
+    const int64_t F = G / kSM * kSM;
+    return b < F ? (b / kSM) * (kSM * W) + w * kSM + b % kSM : F * W + (G - F) * w + (b - F);
 }
+__device__ __forceinline__ int64_t spread_base() { return spread_slot() * 32; }
 #endif
 
 inline int grid_for(int64_t n, int block, int maxb = 152 * 32) {

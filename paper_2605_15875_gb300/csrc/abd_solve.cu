@@ -553,7 +553,7 @@ int ensure_lists(Ctx &C) {
               dbuf_ensure(w.act, sizeof(PairRec) * (size_t)w.cap_act) &&
               dbuf_ensure(w.ls, sizeof(PairRec) * (size_t)w.cap_ls) && dbuf_ensure(w.cp, sizeof(int4) * (size_t)w.cap_cp) &&
               dbuf_ensure(w.off, tb * 144 * (size_t)w.cap_l1) && dbuf_ensure(w.offflag, 4 * (size_t)w.cap_l1) &&
-              dbuf_ensure(w.nmoll, 64) &&
+              dbuf_ensure(w.nmoll, 64 + 8 * (size_t)w.cap_act) &&
               dbuf_ensure(w.rowcnt, 4 * (size_t)(w.S_dyn + 2)) && dbuf_ensure(w.rowoff, 4 * (size_t)(w.S_dyn + 2)) &&
               dbuf_ensure(w.rowcur, 4 * (size_t)(w.S_dyn + 2)) && dbuf_ensure(w.ent, 16 * (size_t)w.cap_l1) &&
               dbuf_ensure(w.diag, tb * 144 * (size_t)(w.S_dyn ? w.S_dyn : 1)) &&

@@ -189,192 +189,112 @@ __global__ void k_slot_assemble(AsmArgs A, T *__restrict__ diag) {
 
 template <class T> __device__ __forceinline__ void atomic_addT(T *a, T v) { atomicAdd(a, v); }
 
-// One active pair's contribution, ready to scatter: the low-rank factors of
-// its projected Hessian, J^T PSD(H) J = P_s K+ P_t^T (pair_hessian_lowrank),
-// pulled back to each side (om[side][a] = sum_v w^_v xi_v[a], ga[side][j][a]
-// = sum_v c^_jv xi_v[a]), the destination of each of its three slot blocks,
-// and its gradient per vertex.
-template <class T>
-struct PairScat {
-    T K[25], om[2][4], ga[2][2][4], rh[3];
-    T w;
-    int n;           // rank of K (3 to 5)
-    T *dst[3];       // blocks (side 0, side 0), (0, 1), (1, 1); null when a side is static
-    int tr[3];       // the (0, 1) block is stored transposed
-    double g[12];    // w * barrier gradient, per vertex and component
-    double xb[4][4]; // (1, rest position) of each vertex
-    int sl[4];       // dynamic slot of each vertex, -1 for a static one
-};
-
-// Everything of one active pair up to its scatter (one thread): FP64
-// gradient, low-rank PSD Hessian in T, destinations (and the CSR row counts
-// of a newly used off-diagonal block).  False when the pair adds nothing:
-// partition done, mollified (k_pair_moll's), or outside (0, dhat).
-template <class T>
-__device__ __forceinline__ bool pair_factors(const AsmArgs &A, const PairRec &r, const int2 *__restrict__ l1,
-                                             T *__restrict__ diag, T *__restrict__ off, int *__restrict__ offflag,
-                                             PairScat<T> &F) {
-    int sa, sb;
-    pair_slots(r, A.sv_slot, sa, sb);
-    const int part = pair_part(sa, sb, A.S_dyn, A.slot_part);
-    if (!A.part[part].active) return false;
-    const bool ee = r.flags & 1;
-    // pair-local coordinates in FP64; gradient in FP64, Hessian in T
-    double Xd[12];
-    for (int v = 0; v < 4; ++v)
-        for (int k = 0; k < 3; ++k) Xd[3 * v + k] = A.x[3 * (int64_t)r.v[v] + k] - A.x[3 * (int64_t)r.v[0] + k];
-    if (ee && ee_cross2(Xd) < r.eps) return false;  // mollified: k_pair_moll
-    PairGrad PG;
-    double gx[12];
-    const double kB = A.part[part].kB;  // the barrier stiffness of the pair's partition
-    const double d = pair_gradient(ee, Xd, A.dhat, kB, r.eps, PG, gx);
-    if (!(d < A.dhat) || !(d > 0.0)) return false;
-    const double w = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
-    T xi[4][4];
-    for (int v = 0; v < 4; ++v) {
-        const int s = A.sv_slot[r.v[v]];
-        F.sl[v] = s < A.S_dyn ? s : -1;
-        const int b = A.slot_body[s];
-        const double *xb = A.xbar + 3 * ((int64_t)A.voff[b] + (r.v[v] - A.slot_voff[s]));
-        F.xb[v][0] = 1.0; F.xb[v][1] = xb[0]; F.xb[v][2] = xb[1]; F.xb[v][3] = xb[2];
-        for (int a = 0; a < 4; ++a) xi[v][a] = T(F.xb[v][a]);
-    }
-    for (int i = 0; i < 12; ++i) F.g[i] = w * gx[i];
-    // slot sides: PT = {point} | {triangle}, EE = {edge a} | {edge b}
-    const int nA = ee ? 2 : 1;
-    const int ss[2] = {sa < A.S_dyn ? sa : -1, sb < A.S_dyn ? sb : -1};
-    // exact low-rank projection: PSD(H) = B PSD(K) B^T, J^T PSD(H) J = P_s K+ P_t^T
-    T K[25], wh[4], chat[2][4], rh[3];
-    const int n = pair_hessian_lowrank<T>(ee, Xd, PG, T(d), T(kB), K, wh, chat, rh);
-    psd_small<T>(K, n);
-    for (int i = 0; i < 25; ++i) F.K[i] = K[i];
-    for (int k = 0; k < 3; ++k) F.rh[k] = rh[k];
-    F.n = n;
-    F.w = T(w);
-    for (int sd = 0; sd < 2; ++sd)
-        for (int a = 0; a < 4; ++a) {
-            T om = T(0), g0 = T(0), g1 = T(0);
-            for (int v = sd ? nA : 0; v < (sd ? 4 : nA); ++v) {
-                om += wh[v] * xi[v][a];
-                g0 += chat[0][v] * xi[v][a];
-                g1 += chat[1][v] * xi[v][a];
-            }
-            F.om[sd][a] = om; F.ga[sd][0][a] = g0; F.ga[sd][1][a] = g1;
-        }
-    for (int blk = 0; blk < 3; ++blk) {
-        const int bi = blk == 2 ? 1 : 0, bj = blk == 0 ? 0 : 1;
-        const int s1 = ss[bi], s2 = ss[bj];
-        F.dst[blk] = nullptr;
-        F.tr[blk] = 0;
-        if (s1 < 0 || s2 < 0) continue;
-        if (bi == bj) {
-            F.dst[blk] = diag + 144 * (int64_t)s1;
-        } else {
-            const int2 lp = l1[r.l1];
-            F.dst[blk] = off + 144 * (int64_t)r.l1;
-            F.tr[blk] = lp.x != s1;
-            if (atomicExch(&offflag[r.l1], 1) == 0) {
-                atomicAdd(&A.rowcnt[lp.x], 1);
-                atomicAdd(&A.rowcnt[lp.y], 1);
-            }
-        }
-    }
-    return true;
-}
-
-// Gradient entry t (0..47: vertex, component, xi index) of a pair.
-template <class T>
-__device__ __forceinline__ void scatter_grad(const AsmArgs &A, const PairScat<T> &F, int t) {
-    const int v = t / 12, k = (t / 4) % 3, a = t % 4;
-    if (F.sl[v] >= 0) atomicAdd(A.g + 12 * (int64_t)F.sl[v] + qidx(k, a), F.g[3 * v + k] * F.xb[v][a]);
-}
-
-// Column `col` of block `blk` of a pair's J^T PSD(H) J: m = K P_t^T e_col,
-// then its 12 rows P_s m.
-template <class T>
-__device__ __forceinline__ void scatter_col(const PairScat<T> &F, int blk, int col) {
-    T *dst = F.dst[blk];
-    if (!dst) return;
-    const int bi = blk == 2 ? 1 : 0, bj = blk == 0 ? 0 : 1, n = F.n;
-    const int l = col < 3 ? col : (col - 3) / 3, be = col < 3 ? 0 : 1 + (col - 3) % 3;
-    const bool tr = F.tr[blk];
-    T mc[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-        T acc = c < n ? F.K[c * 5 + l] * F.om[bj][be] : T(0);
-#pragma unroll
-        for (int j = 0; j < 2; ++j)
-            if (3 + j < n && c < n) acc += F.K[c * 5 + 3 + j] * F.rh[l] * F.ga[bj][j][be];
-        mc[c] = acc;
-    }
-#pragma unroll
-    for (int kk = 0; kk < 3; ++kk)
-#pragma unroll
-        for (int al = 0; al < 4; ++al) {
-            const int row = qidx(kk, al);
-            T v = F.om[bi][al] * mc[kk];
-#pragma unroll
-            for (int j = 0; j < 2; ++j)
-                if (3 + j < n) v += F.rh[kk] * F.ga[bi][j][al] * mc[3 + j];
-            v *= F.w;
-            if (v != T(0)) atomic_addT(dst + (tr ? col * 12 + row : row * 12 + col), v);
-        }
-}
-
 // Per active pair: barrier gradient and projected Hessian scattered to slots.
 // Edge-edge pairs whose mollifier is on (ee_cross2 < eps_x) are skipped: they
 // belong to k_pair_moll (full 12x12 projection), which runs beside this kernel
 // and picks them out with the same test.
-//
-// A pair's scatter (48 gradient entries, 3 blocks x 12 columns) is split over
-// G lanes: one lane forms the pair's factors (pair_factors, FP64-bound), then
-// the G lanes share its entries.  G follows the count n read on the device:
-// 8 while n <= 2432 and 4 while n <= 4864 (at most one warp per SM
-// sub-partition on 152 SMs), else 1 (one pair per lane).  An FP64 instruction
-// costs a warp the same however few lanes run it, so a warp's factor phase
-// takes as long for 4 pairs as for 32; only the scatter shrinks with G.
-template <class T, int G>
-__device__ __forceinline__ void pair_assemble_g(const AsmArgs &A, const PairRec *__restrict__ act, int64_t n,
-                                                const int2 *__restrict__ l1, T *__restrict__ diag,
-                                                T *__restrict__ off, int *__restrict__ offflag, PairScat<T> *sbuf) {
-    constexpr int P = 32 / G;  // pairs per warp
-    const int lane = threadIdx.x & 31, sub = lane % G, grp = lane / G;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t base = spread_slot() * P; base < n; base += nwarps * P) {
-        const int64_t i = base + grp;
-        if (G == 1) {
-            PairScat<T> F;
-            if (i < n && pair_factors(A, act[i], l1, diag, off, offflag, F)) {
-                for (int t = 0; t < 48; ++t) scatter_grad(A, F, t);
-#pragma unroll 1
-                for (int it = 0; it < 36; ++it) scatter_col(F, it / 12, it % 12);
-            }
-        } else {
-            PairScat<T> &F = sbuf[(threadIdx.x >> 5) * P + grp];
-            bool ok = false;
-            if (sub == 0 && i < n) ok = pair_factors(A, act[i], l1, diag, off, offflag, F);
-            ok = __shfl_sync(0xffffffffu, ok, lane - sub);
-            __syncwarp();
-            if (ok) {
-                for (int t = sub; t < 48; t += G) scatter_grad(A, F, t);
-#pragma unroll 1
-                for (int it = sub; it < 36; it += G) scatter_col(F, it / 12, it % 12);
-            }
-            __syncwarp();  // the group's record is rewritten by the next pair
+template <class T>
+__global__ void k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int64_t n, const int2 *__restrict__ l1,
+                                T *__restrict__ diag, T *__restrict__ off, int *__restrict__ offflag,
+                                const unsigned long long *__restrict__ n_dev) {
+    if (n_dev) n = min((int64_t)*n_dev, n);
+    for (int64_t ib = spread_base(); ib < n; ib += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ii = ib + (threadIdx.x & 31);
+        if (ii >= n) continue;
+        const int64_t i = ii;
+        PairRec r = act[i];
+        int sa, sb;
+        pair_slots(r, A.sv_slot, sa, sb);
+        int part = pair_part(sa, sb, A.S_dyn, A.slot_part);
+        if (!A.part[part].active) continue;
+        bool ee = r.flags & 1;
+        // pair-local coordinates in FP64; gradient in FP64, Hessian in T
+        double Xd[12];
+        for (int v = 0; v < 4; ++v)
+            for (int k = 0; k < 3; ++k) Xd[3 * v + k] = A.x[3 * (int64_t)r.v[v] + k] - A.x[3 * (int64_t)r.v[0] + k];
+        if (ee && ee_cross2(Xd) < r.eps) continue;  // mollified: k_pair_moll
+        PairGrad PG;
+        double gx[12];
+        const double kB = A.part[part].kB;  // the barrier stiffness of the pair's partition
+        double d = pair_gradient(ee, Xd, A.dhat, kB, r.eps, PG, gx);
+        if (!(d < A.dhat) || !(d > 0.0)) continue;
+        double w = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
+        int sl[4];
+        T xi[4][4];
+        double xbv[4][4];
+        for (int v = 0; v < 4; ++v) {
+            int s = A.sv_slot[r.v[v]];
+            sl[v] = s < A.S_dyn ? s : -1;
+            int b = A.slot_body[s];
+            const double *xb = A.xbar + 3 * ((int64_t)A.voff[b] + (r.v[v] - A.slot_voff[s]));
+            xbv[v][0] = 1.0; xbv[v][1] = xb[0]; xbv[v][2] = xb[1]; xbv[v][3] = xb[2];
+            for (int a = 0; a < 4; ++a) xi[v][a] = T(xbv[v][a]);
+        }
+        for (int v = 0; v < 4; ++v) {
+            if (sl[v] < 0) continue;
+            for (int k = 0; k < 3; ++k)
+                for (int a = 0; a < 4; ++a)
+                    atomicAdd(A.g + 12 * (int64_t)sl[v] + qidx(k, a), w * gx[3 * v + k] * xbv[v][a]);
+        }
+        // slot sides: PT = {point} | {triangle}, EE = {edge a} | {edge b}
+        const int nA = ee ? 2 : 1;
+        int ss[2] = {sa < A.S_dyn ? sa : -1, sb < A.S_dyn ? sb : -1};
+        {
+            // exact low-rank projection: PSD(H) = B PSD(K) B^T, J^T PSD(H) J = P_s K+ P_t^T
+            T K[25], wh[4], chat[2][4], rh[3];
+            int n = pair_hessian_lowrank<T>(ee, Xd, PG, T(d), T(kB), K, wh, chat, rh);
+            psd_small<T>(K, n);
+            // pull-backs of the basis to each side: om[a] = sum_v w^_v xi_v, ga[j] = sum_v c^_jv xi_v
+            T om[2][4], ga[2][2][4];
+            for (int sd = 0; sd < 2; ++sd)
+                for (int a = 0; a < 4; ++a) {
+                    om[sd][a] = T(0); ga[sd][0][a] = T(0); ga[sd][1][a] = T(0);
+                    for (int v = sd ? nA : 0; v < (sd ? 4 : nA); ++v) {
+                        om[sd][a] += wh[v] * xi[v][a];
+                        ga[sd][0][a] += chat[0][v] * xi[v][a];
+                        ga[sd][1][a] += chat[1][v] * xi[v][a];
+                    }
+                }
+            for (int bi = 0; bi < 2; ++bi)
+                for (int bj = bi; bj < 2; ++bj) {
+                    int s1 = ss[bi], s2 = ss[bj];
+                    if (s1 < 0 || s2 < 0) continue;
+                    T *dst;
+                    bool tr = false;
+                    if (bi == bj) dst = diag + 144 * (int64_t)s1;
+                    else {
+                        int2 lp = l1[r.l1];
+                        dst = off + 144 * (int64_t)r.l1;
+                        tr = (lp.x != s1);
+                        if (atomicExch(&offflag[r.l1], 1) == 0) {
+                            atomicAdd(&A.rowcnt[lp.x], 1);
+                            atomicAdd(&A.rowcnt[lp.y], 1);
+                        }
+                    }
+                    // column by column: m = K P_t^T e_col, then the 12 rows P_s m
+                    for (int l = 0; l < 3; ++l)
+                        for (int be = 0; be < 4; ++be) {
+                            int col = qidx(l, be);
+                            T mc[5];
+                            for (int c = 0; c < 5; ++c) {
+                                T acc = c < n ? K[c * 5 + l] * om[bj][be] : T(0);
+                                for (int j = 0; j < 2; ++j)
+                                    if (3 + j < n && c < n) acc += K[c * 5 + 3 + j] * rh[l] * ga[bj][j][be];
+                                mc[c] = acc;
+                            }
+                            for (int kk = 0; kk < 3; ++kk)
+                                for (int al = 0; al < 4; ++al) {
+                                    int row = qidx(kk, al);
+                                    T v = om[bi][al] * mc[kk];
+                                    for (int j = 0; j < 2; ++j)
+                                        if (3 + j < n) v += rh[kk] * ga[bi][j][al] * mc[3 + j];
+                                    v *= T(w);
+                                    if (v != T(0)) atomic_addT(dst + (tr ? col * 12 + row : row * 12 + col), v);
+                                }
+                        }
+                }
         }
     }
-}
-
-template <class T>
-__global__ void __launch_bounds__(128) k_pair_assemble(AsmArgs A, const PairRec *__restrict__ act, int64_t n,
-                                                       const int2 *__restrict__ l1, T *__restrict__ diag,
-                                                       T *__restrict__ off, int *__restrict__ offflag,
-                                                       const unsigned long long *__restrict__ n_dev) {
-    __shared__ PairScat<T> sbuf[32];  // 4 warps x 8 groups (G = 4)
-    if (n_dev) n = min((int64_t)*n_dev, n);
-    if (n <= 2432) pair_assemble_g<T, 8>(A, act, n, l1, diag, off, offflag, sbuf);
-    else if (n <= 4864) pair_assemble_g<T, 4>(A, act, n, l1, diag, off, offflag, sbuf);
-    else pair_assemble_g<T, 1>(A, act, n, l1, diag, off, offflag, sbuf);
 }
 
 // Pair k (0..5) of round rd (0..10) of the round-robin ordering on 12

@@ -860,26 +860,50 @@ __device__ double slot_energy(const EnArgs &A, int s, double al) {
     return E;
 }
 
-// The line-search energy kernels give every (item, trial step j) its own lane:
-// the items are padded to whole warps for each j, t in [0, (kLS + 1) npad),
-// j = t / npad, item t - j npad, so the lanes of a warp share j (add_energy
-// sums a warp into one partition's E[j]) and a warp carries one FP64 chain
-// instead of kLS + 1 in a row.
+// The line-search energy kernels give every (item, trial step j) its own lane
+// when the list is short: the items are padded to whole warps for each j,
+// t in [0, (kLS + 1) npad), j = t / npad, item t - j npad, so the lanes of a
+// warp share j (add_energy sums a warp into one partition's E[j]) and a warp
+// carries one FP64 chain instead of kLS + 1 in a row.  A long list (more
+// than about two warps per SM sub-partition that way) keeps one lane per
+// item looping over j, which loads each item once.  ls_range gives the
+// iteration space and, per warp, the item offset and the steps [j0, j1).
+constexpr int64_t kLsSplitItems = 32 * 152 * 8;
 __device__ __forceinline__ int64_t ls_pad(int64_t n) { return (n + 31) & ~(int64_t)31; }
+__device__ __forceinline__ int64_t ls_total(int64_t n) {
+    const int64_t npad = ls_pad(n);
+    return (kLS + 1) * npad <= kLsSplitItems ? (kLS + 1) * npad : npad;
+}
+__device__ __forceinline__ void ls_range(int64_t n, int64_t base, int64_t &first, int &j0, int &j1) {
+    const int64_t npad = ls_pad(n);
+    if ((kLS + 1) * npad <= kLsSplitItems) {
+        j0 = (int)(base / npad);
+        j1 = j0 + 1;
+        first = base - (int64_t)j0 * npad;
+    } else {
+        j0 = 0;
+        j1 = kLS + 1;
+        first = base;
+    }
+}
 
 __global__ void k_energy_slots(EnArgs A) {
     if (!*A.live) return;
-    const int64_t npad = ls_pad(A.S_dyn);
-    for (int64_t base = spread_base(); base < (kLS + 1) * npad; base += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(base / npad);
-        const int s = (int)(base - j * npad + (threadIdx.x & 31));
+    const int64_t total = ls_total(A.S_dyn);
+    for (int64_t base = spread_base(); base < total; base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t first;
+        int j0, j1;
+        ls_range(A.S_dyn, base, first, j0, j1);
+        const int s = (int)(first + (threadIdx.x & 31));
         int p = s < A.S_dyn ? A.slot_part[s] : -1;
         if (p >= 0 && !A.part[p].active) p = -1;
         if (p >= 0 && A.alphas[(kLS + 1) * p] < 0.0) p = -1;  // partition already decided
-        const double al = p >= 0 ? A.alphas[(kLS + 1) * p + j] : -1.0;
-        const bool use = p >= 0 && (j == 0 || al >= 0.0);
-        const double v = use ? slot_energy(A, s, al) : 0.0;
-        add_energy(A.part, use ? p : -1, j, v);
+        for (int j = j0; j < j1; ++j) {
+            const double al = p >= 0 ? A.alphas[(kLS + 1) * p + j] : -1.0;
+            const bool use = p >= 0 && (j == 0 || al >= 0.0);
+            const double v = use ? slot_energy(A, s, al) : 0.0;
+            add_energy(A.part, use ? p : -1, j, v);
+        }
     }
 }
 
@@ -887,43 +911,52 @@ __global__ void k_energy_pairs(EnArgs A, const PairRec *__restrict__ ls, int64_t
                                const unsigned long long *__restrict__ n_dev) {
     if (!*A.live) return;
     if (n_dev) n = min((int64_t)*n_dev, n);
-    const int64_t npad = ls_pad(n);
-    for (int64_t base = spread_base(); base < (kLS + 1) * npad; base += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(base / npad);
-        const int64_t i = base - j * npad + (threadIdx.x & 31);
+    const int64_t total = ls_total(n);
+    for (int64_t base = spread_base(); base < total; base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t first;
+        int j0, j1;
+        ls_range(n, base, first, j0, j1);
+        const int64_t i = first + (threadIdx.x & 31);
         int p = -1;
-        double e = 0.0;
+        PairRec r;
+        double w = 0.0, kB = 0.0, X0[12], DX[12];
         if (i < n) {
-            const PairRec r = ls[i];
+            r = ls[i];
             int sa, sb;
             pair_slots(r, A.sv_slot, sa, sb);
             p = pair_part(sa, sb, A.S_dyn, A.slot_part);
-            const double kB = A.part[p].kB;
+            kB = A.part[p].kB;
             if (!A.part[p].active || A.alphas[(kLS + 1) * p] < 0.0) p = -1;
-            const double al = p >= 0 ? A.alphas[(kLS + 1) * p + j] : -1.0;
-            if (p >= 0 && (j == 0 || al >= 0.0)) {
-                const double w = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
-                double X[12], d;
-                for (int v = 0; v < 4; ++v)
-                    for (int k = 0; k < 3; ++k) {
-                        const double a = A.x0[3 * (int64_t)r.v[v] + k];
-                        X[3 * v + k] = a + al * (A.x1[3 * (int64_t)r.v[v] + k] - a);
-                    }
-                e = w * pair_energy(r.flags & 1, X, A.dhat, kB, r.eps, d);
-            } else {
-                p = -1;
-            }
+            w = A.h * A.h / pair_kappa(sa, sb, A.S_dyn, A.slot_mask);
+            for (int v = 0; v < 4; ++v)
+                for (int k = 0; k < 3; ++k) {
+                    double a = A.x0[3 * (int64_t)r.v[v] + k];
+                    X0[3 * v + k] = a;
+                    DX[3 * v + k] = A.x1[3 * (int64_t)r.v[v] + k] - a;
+                }
         }
-        add_energy(A.part, p, j, e);
+        for (int j = j0; j < j1; ++j) {
+            double al = p >= 0 ? A.alphas[(kLS + 1) * p + j] : -1.0;
+            bool use = p >= 0 && (j == 0 || al >= 0.0);
+            double e = 0.0;
+            if (use) {
+                double X[12], d;
+                for (int q = 0; q < 12; ++q) X[q] = X0[q] + al * DX[q];
+                e = w * pair_energy(r.flags & 1, X, A.dhat, kB, r.eps, d);
+            }
+            add_energy(A.part, use ? p : -1, j, e);
+        }
     }
 }
 
 __global__ void k_energy_vp(EnArgs A, int64_t SVd) {
     if (!*A.live) return;
-    const int64_t npad = ls_pad(SVd);
-    for (int64_t base = spread_base(); base < (kLS + 1) * npad; base += (int64_t)gridDim.x * blockDim.x) {
-        const int j = (int)(base / npad);
-        const int64_t i = base - j * npad + (threadIdx.x & 31);
+    const int64_t total = ls_total(SVd);
+    for (int64_t base = spread_base(); base < total; base += (int64_t)gridDim.x * blockDim.x) {
+        int64_t first;
+        int j0, j1;
+        ls_range(SVd, base, first, j0, j1);
+        const int64_t i = first + (threadIdx.x & 31);
         int p = -1, s = 0;
         if (i < SVd) {
             s = A.sv_slot[i];
@@ -931,22 +964,24 @@ __global__ void k_energy_vp(EnArgs A, int64_t SVd) {
             if (!A.part[p].active || A.alphas[(kLS + 1) * p] < 0.0) p = -1;
         }
         const double w = p >= 0 ? A.h * A.h / (double)__popcll(A.slot_mask[s]) * A.part[p].kB : 0.0;
-        const double al = p >= 0 ? A.alphas[(kLS + 1) * p + j] : -1.0;
-        const bool use = p >= 0 && (j == 0 || al >= 0.0);
-        double e = 0.0;
-        if (use)
-            for (int k = 0; k < A.planes.n; ++k) {
-                const int ax = A.planes.axis[k];
-                const double xa = A.x0[3 * i + ax] + al * (A.x1[3 * i + ax] - A.x0[3 * i + ax]);
-                const double d = A.planes.sign[k] * xa - A.planes.offset[k];
-                if (!(d > 0.0)) e += 1.0 / 0.0;
-                else if (d < A.dhat) {
-                    double bb, b1, b2;
-                    barrier3<double>(d, A.dhat, bb, b1, b2);
-                    e += w * bb;
+        for (int j = j0; j < j1; ++j) {
+            const double al = p >= 0 ? A.alphas[(kLS + 1) * p + j] : -1.0;
+            const bool use = p >= 0 && (j == 0 || al >= 0.0);
+            double e = 0.0;
+            if (use)
+                for (int k = 0; k < A.planes.n; ++k) {
+                    const int ax = A.planes.axis[k];
+                    const double xa = A.x0[3 * i + ax] + al * (A.x1[3 * i + ax] - A.x0[3 * i + ax]);
+                    const double d = A.planes.sign[k] * xa - A.planes.offset[k];
+                    if (!(d > 0.0)) e += 1.0 / 0.0;
+                    else if (d < A.dhat) {
+                        double bb, b1, b2;
+                        barrier3<double>(d, A.dhat, bb, b1, b2);
+                        e += w * bb;
+                    }
                 }
-            }
-        add_energy(A.part, use && e != 0.0 ? p : -1, j, e);
+            add_energy(A.part, use && e != 0.0 ? p : -1, j, e);
+        }
     }
 }
 
